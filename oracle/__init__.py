@@ -1,0 +1,252 @@
+"""CPU oracle for level-synchronous breadth-first search.
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by ``__graft_entry__.smoke()``
+and by the CPU-baseline leg of ``bench.py``; never by the library.  It shares no
+code with the CUDA path (``paper_1705_04590_gb300``), and neither imports the
+other.  The only module both sides use is ``graphgen`` (seeded inputs).
+
+Contents (each cites the passage of Bulu\\c{c} et al. 2015 it follows):
+
+* :func:`build_csr`       -- "Graph Representation" + "Data Sets" (numpy sort/unique)
+* :func:`bfs_topdown`     -- Algorithm 1, serial FIFO (C)
+* :func:`bfs_bottomup`    -- Algorithm 2, serial (C)
+* :func:`min_parent`      -- (select2nd, min) semiring of the parallel top-down local discovery (C)
+* :func:`components`      -- union-find, to pin "reached set = component of the root" (C)
+* :func:`certify`         -- BFS invariants, valid at any size (C)
+* :func:`do_schedule`     -- per-level direction and work counts of the
+                             direction-optimizing search ("Parallel Direction-Optimizing BFS") (C)
+* :func:`brute_force_levels` -- all-pairs unit-weight relaxation to a fixpoint
+                             (Bellman-Ford style), numpy, tiny graphs only
+
+Every function is pinned by ``tests/test_oracle.py`` against something other
+than itself (brute force, closed forms, the hand-derived Figure 3 fixture,
+invariants, direction invariance).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+CERT_CODES = {1: "root", 2: "parent edge / parent level", 3: "edge spans > 1 level",
+              4: "edge to unreached vertex", 5: "reached set != component of root"}
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so (gcc -O2; plain C, single thread)."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", _SRC, "-o", tmp])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB_PATH)
+        vp = ctypes.c_void_p
+        i64, i32 = ctypes.c_int64, ctypes.c_int32
+        L.or_bfs_topdown.argtypes = [i64, vp, vp, i32, vp, vp, vp]
+        L.or_bfs_topdown.restype = i32
+        L.or_bfs_bottomup.argtypes = [i64, vp, vp, i32, vp, vp, vp, vp]
+        L.or_bfs_bottomup.restype = i32
+        L.or_min_parent.argtypes = [i64, vp, vp, vp, vp]
+        L.or_min_parent.restype = None
+        L.or_components.argtypes = [i64, vp, vp, vp]
+        L.or_components.restype = None
+        L.or_certify.argtypes = [i64, vp, vp, i32, vp, vp, vp]
+        L.or_certify.restype = i64
+        L.or_do_schedule.argtypes = [i64, vp, vp, vp, i32, i64, i64, i32] + [vp] * 7
+        L.or_do_schedule.restype = i32
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+@dataclass
+class CSR:
+    """Undirected, de-duplicated, self-loop-free CSR built by the oracle."""
+    n: int
+    offsets: np.ndarray  # int64[n+1]
+    cols: np.ndarray     # int32[nnz], each row sorted ascending
+
+    @property
+    def nnz(self) -> int:
+        return int(self.offsets[-1])
+
+    def degree(self) -> np.ndarray:
+        return np.diff(self.offsets)
+
+
+def build_csr(n: int, src: np.ndarray, dst: np.ndarray, chunk: int = 1 << 26) -> CSR:
+    """CSR of the undirected graph ("Graph Representation": sorted adjacencies,
+    each undirected edge stored in both rows, an n+1 row-pointer array; "Data
+    Sets": duplicate edges pruned).  Self-loops are dropped.
+
+    Written as the definition: the set {(u, v), (v, u) : {u, v} an input edge,
+    u != v} as 64-bit keys u*2^32 + v, sorted (numpy's sort, a library
+    primitive), repeats removed; the low halves are the column ids and the
+    row lengths are counts of the high halves.  Chunked only to bound host
+    memory (about 8 bytes per directed entry plus the 4-byte result)."""
+    src = np.asarray(src)
+    dst = np.asarray(dst)
+    m = int(src.shape[0])
+    if m and (min(int(src.min()), int(dst.min())) < 0 or max(int(src.max()), int(dst.max())) >= n):
+        raise ValueError("edge list holds ids outside [0, n)")
+    keep_total = 0
+    for a in range(0, m, chunk):
+        keep_total += int(np.count_nonzero(src[a:a + chunk] != dst[a:a + chunk]))
+    keys = np.empty(2 * keep_total, np.uint64)
+    w = 0
+    for a in range(0, m, chunk):
+        u = src[a:a + chunk].astype(np.uint64)
+        v = dst[a:a + chunk].astype(np.uint64)
+        k = u != v
+        u, v = u[k], v[k]
+        c = u.shape[0]
+        keys[w:w + c] = (u << np.uint64(32)) | v
+        keys[keep_total + w:keep_total + w + c] = (v << np.uint64(32)) | u
+        w += c
+    keys.sort()
+    # drop repeats in place (the write cursor never passes the read cursor)
+    nnz = 0
+    total = keys.shape[0]
+    prev = None
+    for a in range(0, total, chunk):
+        blk = keys[a:a + chunk]
+        first = np.empty(blk.shape[0], bool)
+        first[1:] = blk[1:] != blk[:-1]
+        if blk.shape[0]:
+            first[0] = prev is None or blk[0] != prev
+            prev = blk[-1]
+        sel = blk[first]
+        keys[nnz:nnz + sel.shape[0]] = sel
+        nnz += sel.shape[0]
+    cols = np.empty(nnz, np.int32)
+    counts = np.zeros(n, np.int64)
+    for a in range(0, nnz, chunk):
+        blk = keys[a:min(a + chunk, nnz)]
+        cols[a:a + blk.shape[0]] = (blk & np.uint64(0xFFFFFFFF)).astype(np.int32)
+        counts += np.bincount((blk >> np.uint64(32)).astype(np.int64), minlength=n)
+    del keys
+    off = np.zeros(n + 1, np.int64)
+    np.cumsum(counts, out=off[1:])
+    return CSR(n, off, cols)
+
+
+def csr_from_edges(g) -> CSR:
+    return build_csr(g.n, g.src, g.dst)
+
+
+def bfs_topdown(g: CSR, root: int):
+    """Algorithm 1. Returns (parent, level, num_levels)."""
+    parent = np.empty(g.n, np.int32)
+    level = np.empty(g.n, np.int32)
+    queue = np.empty(max(g.n, 1), np.int32)
+    L = _load().or_bfs_topdown(g.n, _ptr(g.offsets), _ptr(g.cols), int(root), _ptr(parent), _ptr(level), _ptr(queue))
+    return parent, level, int(L)
+
+
+def bfs_bottomup(g: CSR, root: int):
+    """Algorithm 2. Returns (parent, level, num_levels)."""
+    parent = np.empty(g.n, np.int32)
+    level = np.empty(g.n, np.int32)
+    f = np.empty(g.n, np.uint8)
+    nx = np.empty(g.n, np.uint8)
+    L = _load().or_bfs_bottomup(g.n, _ptr(g.offsets), _ptr(g.cols), int(root), _ptr(parent), _ptr(level),
+                                _ptr(f), _ptr(nx))
+    return parent, level, int(L)
+
+
+def levels(g: CSR, root: int) -> np.ndarray:
+    return bfs_topdown(g, root)[1]
+
+
+def min_parent(g: CSR, level: np.ndarray) -> np.ndarray:
+    level = np.ascontiguousarray(level, np.int32)
+    out = np.empty(g.n, np.int32)
+    _load().or_min_parent(g.n, _ptr(g.offsets), _ptr(g.cols), _ptr(level), _ptr(out))
+    return out
+
+
+def components(g: CSR) -> np.ndarray:
+    lab = np.empty(g.n, np.int32)
+    _load().or_components(g.n, _ptr(g.offsets), _ptr(g.cols), _ptr(lab))
+    return lab
+
+
+def certify(g: CSR, root: int, level: np.ndarray, parent: np.ndarray | None = None,
+            labels: np.ndarray | None = None) -> tuple[int, int]:
+    """(0, -1) if valid, else (failed invariant code, vertex).  See oracle.c."""
+    if labels is None:
+        labels = components(g)
+    level = np.ascontiguousarray(level, np.int32)
+    if parent is not None:
+        parent = np.ascontiguousarray(parent, np.int32)
+    r = _load().or_certify(g.n, _ptr(g.offsets), _ptr(g.cols), int(root), _ptr(parent), _ptr(level),
+                           _ptr(np.ascontiguousarray(labels, np.int32)))
+    if r == 0:
+        return 0, -1
+    return int(r >> 40), int(r & ((1 << 40) - 1))
+
+
+MODE_DO, MODE_TD, MODE_BU = 0, 1, 2
+
+
+@dataclass
+class Schedule:
+    dir: np.ndarray       # int32 per level: 0 top-down, 1 bottom-up
+    nf: np.ndarray
+    mf: np.ndarray
+    nnext: np.ndarray
+    mnext: np.ndarray
+    scanned: np.ndarray
+    examined: np.ndarray
+
+    @property
+    def num_levels(self) -> int:
+        return int(self.dir.shape[0])
+
+
+def do_schedule(g: CSR, level: np.ndarray, mode: int = MODE_DO, alpha: int = 14, beta: int = 24) -> Schedule:
+    level = np.ascontiguousarray(level, np.int32)
+    cap = int(level.max()) + 2 if level.size else 2
+    arrs = [np.zeros(cap, np.int32)] + [np.zeros(cap, np.int64) for _ in range(6)]
+    L = _load().or_do_schedule(g.n, _ptr(g.offsets), _ptr(g.cols), _ptr(level), mode, alpha, beta, cap,
+                               *[_ptr(a) for a in arrs])
+    if L < 0:
+        raise RuntimeError("schedule capacity")
+    return Schedule(*[a[:L].copy() for a in arrs])
+
+
+def brute_force_levels(n: int, src: np.ndarray, dst: np.ndarray, root: int) -> np.ndarray:
+    """Unit-weight relaxation d[v] = min(d[v], d[u] + 1) over every edge, both
+    directions, until nothing changes (Bellman-Ford style).  Self-loops and
+    duplicates are harmless here.  O(n * m): tiny graphs only."""
+    INF = np.iinfo(np.int64).max // 4
+    d = np.full(n, INF, np.int64)
+    d[root] = 0
+    s = np.concatenate([np.asarray(src, np.int64), np.asarray(dst, np.int64)])
+    t = np.concatenate([np.asarray(dst, np.int64), np.asarray(src, np.int64)])
+    for _ in range(n + 1):
+        cand = d[s] + 1
+        new = d.copy()
+        np.minimum.at(new, t, cand)
+        if np.array_equal(new, d):
+            break
+        d = new
+    out = np.where(d >= INF, -1, d)
+    return out.astype(np.int32)

@@ -1,0 +1,283 @@
+/*
+ * oracle.c -- serial CPU oracle for level-synchronous breadth-first search.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the package smoke check and
+ * the benchmark's CPU-baseline leg may load this library.  It shares no code,
+ * header or table with the CUDA path, and the CUDA path never calls it.
+ *
+ * Plain, slow, obviously correct C.  Each routine cites the passage of
+ * Bulu\c{c}, Beamer, Madduri, Asanovic, Patterson, "Distributed-Memory
+ * Breadth-First Search on Massive Graphs" (2015) that it follows:
+ *
+ *  (the CSR itself is built by the Python side of the oracle with numpy's
+ *  sort, as the set definition of "Graph Representation" / "Data Sets")
+ *  or_bfs_topdown    Algorithm 1 (sequential top-down BFS), FIFO queue, with
+ *                    the hop count d of the "Breadth-First Search" section
+ *                    recorded alongside the parent.
+ *  or_bfs_bottomup   Algorithm 2 (sequential bottom-up BFS): every unvisited
+ *                    vertex scans its neighbours for one in the *current*
+ *                    frontier and stops at the first; the next frontier is
+ *                    separate and swapped in at the end of the level.
+ *  or_min_parent     the (select2nd, min) semiring of the parallel top-down
+ *                    algorithm's local discovery: among the valid parents the
+ *                    minimum id.
+ *  or_components     union-find connected components (independent of BFS),
+ *                    used to check that the reached set is the component of
+ *                    the root ("examines the whole connected component").
+ *  or_certify        the invariants that make a level/parent pair a BFS:
+ *                    see the function comment.
+ *  or_do_schedule    the direction-optimizing schedule ("Parallel
+ *                    Direction-Optimizing BFS"): per level the direction chosen
+ *                    by the edges-out-of-frontier / frontier-size heuristics,
+ *                    and the per-level work counts that the byte model uses.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------ Algorithm 1 */
+
+/*
+ * Sequential top-down BFS (Algorithm 1).  parent[v] = -1 unless reached,
+ * parent[root] = root; level[v] = hop distance (-1 if unreachable).
+ * `queue` is scratch of n entries.  Returns the number of levels (the
+ * largest level + 1).  Ties among parents go to the first discoverer in FIFO
+ * order.
+ */
+int32_t or_bfs_topdown(int64_t n, const int64_t* off, const int32_t* cols, int32_t root,
+                       int32_t* parent, int32_t* level, int32_t* queue) {
+    for (int64_t v = 0; v < n; v++) { parent[v] = -1; level[v] = -1; }
+    parent[root] = root;
+    level[root] = 0;
+    /* frontier = queue[head, mid), next = queue[mid, tail): one FIFO holds both */
+    int64_t head = 0, tail = 0;
+    queue[tail++] = root;
+    int32_t d = 0;
+    while (head < tail) {                      /* while frontier != empty */
+        int64_t mid = tail;
+        for (; head < mid; head++) {           /* for each u in frontier */
+            int32_t u = queue[head];
+            for (int64_t k = off[u]; k < off[u + 1]; k++) {  /* each neighbour v */
+                int32_t v = cols[k];
+                if (parent[v] == -1) {         /* unvisited */
+                    queue[tail++] = v;         /* next <- next + {v} */
+                    parent[v] = u;
+                    level[v] = d + 1;
+                }
+            }
+        }
+        d++;                                   /* frontier <- next */
+    }
+    return d;
+}
+
+/* ------------------------------------------------------------------ Algorithm 2 */
+
+/*
+ * Sequential bottom-up BFS (Algorithm 2).  Same outputs as or_bfs_topdown.
+ * frontier/next are scratch byte arrays of n entries.  Membership is tested
+ * against the current frontier only; `next` becomes the frontier after the
+ * whole level.  Returns the number of levels.
+ */
+int32_t or_bfs_bottomup(int64_t n, const int64_t* off, const int32_t* cols, int32_t root,
+                        int32_t* parent, int32_t* level, uint8_t* frontier, uint8_t* next) {
+    for (int64_t v = 0; v < n; v++) { parent[v] = -1; level[v] = -1; frontier[v] = 0; next[v] = 0; }
+    parent[root] = root;
+    level[root] = 0;
+    frontier[root] = 1;
+    int64_t fsize = 1;
+    int32_t d = 0;
+    while (fsize > 0) {
+        int64_t nsize = 0;
+        for (int64_t u = 0; u < n; u++) {
+            if (parent[u] != -1) continue;     /* only unvisited vertices search */
+            for (int64_t k = off[u]; k < off[u + 1]; k++) {
+                int32_t v = cols[k];
+                if (frontier[v]) {
+                    next[u] = 1;
+                    parent[u] = v;
+                    level[u] = d + 1;
+                    nsize++;
+                    break;                     /* early exit */
+                }
+            }
+        }
+        uint8_t* t = frontier; frontier = next; next = t;   /* frontier <- next */
+        memset(next, 0, (size_t)n);
+        fsize = nsize;
+        d++;
+    }
+    return d;
+}
+
+/* ------------------------------------------------------------------ min-id parent */
+
+/* parent[v] = min{u in adj(v) : level[u] = level[v]-1}; parent[root] = root; -1 if unreached. */
+void or_min_parent(int64_t n, const int64_t* off, const int32_t* cols, const int32_t* level,
+                   int32_t* parent) {
+    for (int64_t v = 0; v < n; v++) {
+        parent[v] = -1;
+        if (level[v] == 0) { parent[v] = (int32_t)v; continue; }
+        if (level[v] < 0) continue;
+        for (int64_t k = off[v]; k < off[v + 1]; k++) {
+            int32_t u = cols[k];
+            if (level[u] == level[v] - 1 && (parent[v] == -1 || u < parent[v])) parent[v] = u;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ union-find */
+
+static int32_t or_find(int32_t* p, int32_t x) {
+    while (p[x] != x) { p[x] = p[p[x]]; x = p[x]; }   /* path halving */
+    return x;
+}
+
+/* label[v] = smallest vertex id of v's connected component. */
+void or_components(int64_t n, const int64_t* off, const int32_t* cols, int32_t* label) {
+    for (int64_t v = 0; v < n; v++) label[v] = (int32_t)v;
+    for (int64_t u = 0; u < n; u++)
+        for (int64_t k = off[u]; k < off[u + 1]; k++) {
+            int32_t a = or_find(label, (int32_t)u), b = or_find(label, cols[k]);
+            if (a != b) { if (a < b) label[b] = a; else label[a] = b; }
+        }
+    for (int64_t v = 0; v < n; v++) label[v] = or_find(label, (int32_t)v);
+}
+
+/* ------------------------------------------------------------------ certificate */
+
+/* binary search for v in the sorted row u */
+static int or_has_edge(const int64_t* off, const int32_t* cols, int32_t u, int32_t v) {
+    int64_t lo = off[u], hi = off[u + 1];
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (cols[mid] < v) lo = mid + 1; else hi = mid;
+    }
+    return lo < off[u + 1] && cols[lo] == v;
+}
+
+/*
+ * Check that (level, parent) is a breadth-first search from `root`:
+ *   1 level[root] = 0 and parent[root] = root (when parent is given)
+ *   2 for every reached v != root: level[v] >= 1, (parent[v], v) is an edge,
+ *     level[parent[v]] = level[v] - 1
+ *   3 every edge {u, v} with both ends reached spans at most one level
+ *   4 an edge never joins a reached and an unreached vertex
+ *   5 the reached set is exactly the connected component of root (label[]
+ *     from or_components) and unreached vertices carry parent = level = -1.
+ * 2 gives dist <= level along the parent chain; 3 gives level <= dist along a
+ * shortest path; together level = dist.  `parent` may be NULL (skips 2's
+ * parent clauses).  Returns 0 if valid, else (code << 40) | vertex where code
+ * is the failed invariant.
+ */
+int64_t or_certify(int64_t n, const int64_t* off, const int32_t* cols, int32_t root,
+                   const int32_t* parent, const int32_t* level, const int32_t* label) {
+    if (root < 0 || root >= n) return (int64_t)1 << 40;
+    if (level[root] != 0) return ((int64_t)1 << 40) | root;
+    if (parent && parent[root] != root) return ((int64_t)1 << 40) | root;
+    for (int64_t v = 0; v < n; v++) {
+        int reached = level[v] >= 0;
+        int in_comp = label[v] == label[root];
+        if (reached != in_comp) return ((int64_t)5 << 40) | v;
+        if (!reached) {
+            if (level[v] != -1 || (parent && parent[v] != -1)) return ((int64_t)5 << 40) | v;
+            continue;
+        }
+        if (v != root) {
+            if (level[v] < 1) return ((int64_t)2 << 40) | v;
+            if (parent) {
+                int32_t p = parent[v];
+                if (p < 0 || p >= n) return ((int64_t)2 << 40) | v;
+                if (!or_has_edge(off, cols, p, (int32_t)v)) return ((int64_t)2 << 40) | v;
+                if (level[p] != level[v] - 1) return ((int64_t)2 << 40) | v;
+            }
+        }
+        for (int64_t k = off[v]; k < off[v + 1]; k++) {
+            int32_t u = cols[k];
+            if (level[u] < 0) return ((int64_t)4 << 40) | v;
+            int32_t diff = level[u] - level[v];
+            if (diff > 1 || diff < -1) return ((int64_t)3 << 40) | v;
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ DO schedule */
+
+/*
+ * Direction-optimizing schedule from the exact levels.  The paper chooses,
+ * per level, top-down or bottom-up by "the number of edges originating in the
+ * frontier while top-down and the size of the frontier while bottom-up".  With
+ * the thresholds alpha, beta the rule read here is:
+ *   in top-down:  go bottom-up when m_f * alpha > m_u
+ *   in bottom-up: go top-down  when n_f * beta  < n
+ * where, at the start of level d, n_f = |frontier| = |{v : level[v] = d}|,
+ * m_f = sum of degrees over the frontier, m_u = sum of degrees over vertices
+ * not yet reached (level > d or unreachable).  The first level starts from
+ * top-down and is itself subject to the rule.  mode: 0 = direction-optimizing,
+ * 1 = top-down only, 2 = bottom-up only.
+ *
+ * Per level d (d < num_levels) the arrays receive:
+ *   dir[d]      0 top-down, 1 bottom-up
+ *   nf[d], mf[d]       frontier size and degree sum
+ *   nnext[d]    vertices discovered (|{v : level[v] = d+1}|)
+ *   mnext[d]    their degree sum
+ *   scanned[d]  bottom-up only: unvisited vertices with degree > 0 that search
+ *   examined[d] top-down: m_f; bottom-up: sum over searching vertices of the
+ *               1-based position of the first frontier neighbour in sorted
+ *               order, or the degree if none (the serial early-exit count)
+ * Returns num_levels, or -1 if cap is too small.
+ */
+int32_t or_do_schedule(int64_t n, const int64_t* off, const int32_t* cols, const int32_t* level,
+                       int32_t mode, int64_t alpha, int64_t beta, int32_t cap,
+                       int32_t* dir, int64_t* nf, int64_t* mf, int64_t* nnext, int64_t* mnext,
+                       int64_t* scanned, int64_t* examined) {
+    int32_t L = 0;
+    for (int64_t v = 0; v < n; v++) if (level[v] + 1 > L) L = level[v] + 1;
+    if (L > cap) return -1;
+    int64_t* cnt = (int64_t*)calloc((size_t)L + 1, sizeof(int64_t));
+    int64_t* deg = (int64_t*)calloc((size_t)L + 1, sizeof(int64_t));
+    int64_t total_deg_unreached = 0, nnz = off[n];
+    for (int64_t v = 0; v < n; v++) {
+        int64_t dv = off[v + 1] - off[v];
+        if (level[v] >= 0) { cnt[level[v]]++; deg[level[v]] += dv; }
+        else total_deg_unreached += dv;
+    }
+    (void)total_deg_unreached;
+    int64_t m_u = nnz - deg[0];     /* degree sum of vertices not in levels 0..d */
+    int32_t cur = 0;                /* start top-down */
+    for (int32_t d = 0; d < L; d++) {
+        int64_t n_f = cnt[d], m_f = deg[d];
+        if (mode == 1) cur = 0;
+        else if (mode == 2) cur = 1;
+        else if (cur == 0 && m_f * alpha > m_u) cur = 1;
+        else if (cur == 1 && n_f * beta < n) cur = 0;
+        dir[d] = cur;
+        nf[d] = n_f;
+        mf[d] = m_f;
+        nnext[d] = cnt[d + 1];
+        mnext[d] = deg[d + 1];
+        if (cur == 0) {
+            scanned[d] = 0;
+            examined[d] = m_f;
+        } else {
+            int64_t sc = 0, ex = 0;
+            for (int64_t u = 0; u < n; u++) {
+                if (level[u] >= 0 && level[u] <= d) continue;   /* already visited */
+                int64_t b = off[u], e = off[u + 1];
+                if (e == b) continue;                          /* degree 0 never searches */
+                sc++;
+                int64_t pos = e - b;
+                for (int64_t k = b; k < e; k++)
+                    if (level[cols[k]] == d) { pos = k - b + 1; break; }
+                ex += pos;
+            }
+            scanned[d] = sc;
+            examined[d] = ex;
+        }
+        m_u -= deg[d + 1];
+    }
+    free(cnt);
+    free(deg);
+    return L;
+}

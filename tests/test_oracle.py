@@ -1,0 +1,283 @@
+"""Pins of the CPU oracle against things other than itself (CPU only).
+
+* Figure 3 fixture (hand-derived, tests/golden/fig3.txt)
+* brute-force unit-weight relaxation on tiny graphs
+* networkx shortest paths / components (an independent library), where installed
+* closed forms: path, star, complete graph, torus
+* Algorithm 1 and Algorithm 2 give the same levels (direction invariance)
+* planted mistakes are rejected by the certificate
+* the direction-optimizing schedule against hand-derived cases and a literal
+  Python walk of Algorithm 2 on tiny graphs
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+from tests.golden import fixtures
+
+
+def csr(g):
+    return oracle.build_csr(g.n, g.src, g.dst)
+
+
+# ------------------------------------------------------------------ CSR build
+
+def _set_csr(n, src, dst):
+    adj = [set() for _ in range(n)]
+    for u, v in zip(src.tolist(), dst.tolist()):
+        if u != v:
+            adj[u].add(v)
+            adj[v].add(u)
+    return [sorted(a) for a in adj]
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_build_csr_matches_set_definition(seed):
+    g = graphgen.random_small(40, 120, seed)
+    c = csr(g)
+    want = _set_csr(g.n, g.src, g.dst)
+    assert c.offsets[0] == 0 and len(c.offsets) == g.n + 1
+    for v in range(g.n):
+        assert c.cols[c.offsets[v]:c.offsets[v + 1]].tolist() == want[v]
+
+
+def test_build_csr_fig3():
+    f = fixtures.fig3()
+    pairs = [(r, c) for r, cs in f["rows"].items() for c in cs]
+    g = graphgen.from_pairs(6, pairs)
+    c = csr(g)
+    edges = {(u, int(v)) for u in range(6) for v in c.cols[c.offsets[u]:c.offsets[u + 1]]}
+    tree = {(0, 1), (0, 3), (1, 4), (2, 3), (2, 5)}
+    assert edges == tree | {(b, a) for a, b in tree}
+
+
+def test_build_csr_rejects_bad_ids():
+    with pytest.raises(ValueError):
+        oracle.build_csr(3, np.array([0, 5], np.int32), np.array([1, 1], np.int32))
+
+
+# ------------------------------------------------------------------ BFS pins
+
+def test_fig3_levels_and_parents():
+    f = fixtures.fig3()
+    pairs = [(r, c) for r, cs in f["rows"].items() for c in cs]
+    c = csr(graphgen.from_pairs(6, pairs))
+    for fn in (oracle.bfs_topdown, oracle.bfs_bottomup):
+        parent, level, L = fn(c, f["root"])
+        assert level.tolist() == f["level"]
+        assert parent.tolist() == f["parent"]
+        assert L == 4
+
+
+def _tiny_graphs():
+    gs = [graphgen.random_small(n, m, s) for n, m, s in
+          [(1, 0, 0), (2, 1, 1), (5, 3, 2), (16, 10, 3), (16, 40, 4), (33, 20, 5), (64, 64, 6), (64, 300, 7),
+           (100, 90, 8), (128, 128, 9), (200, 400, 10), (256, 256, 11)]]
+    gs += [graphgen.path(17), graphgen.cycle(12), graphgen.star(20), graphgen.complete(9)]
+    two, _ = graphgen.disjoint_union([graphgen.path(5), graphgen.complete(4), graphgen.from_pairs(3, [])])
+    gs.append(two)
+    return gs
+
+
+@pytest.mark.parametrize("gi", range(17))
+def test_topdown_matches_brute_force(gi):
+    g = _tiny_graphs()[gi]
+    c = csr(g)
+    for root in range(g.n):
+        bf = oracle.brute_force_levels(g.n, g.src, g.dst, root)
+        p, lv, L = oracle.bfs_topdown(c, root)
+        assert np.array_equal(lv, bf), (g.name, root)
+        assert L == bf.max() + 1
+        assert oracle.certify(c, root, lv, p) == (0, -1)
+
+
+@pytest.mark.parametrize("gi", range(17))
+def test_bottomup_equals_topdown(gi):
+    g = _tiny_graphs()[gi]
+    c = csr(g)
+    for root in range(0, g.n, max(1, g.n // 13)):
+        _, l1, L1 = oracle.bfs_topdown(c, root)
+        p2, l2, L2 = oracle.bfs_bottomup(c, root)
+        assert np.array_equal(l1, l2) and L1 == L2
+        # in-order early exit over sorted rows yields the minimum-id parent
+        assert np.array_equal(p2, oracle.min_parent(c, l2))
+
+
+def test_against_networkx():
+    nx = pytest.importorskip("networkx")
+    g = graphgen.rmat(10, seed=1010)
+    c = csr(g)
+    G = nx.Graph()
+    G.add_nodes_from(range(g.n))
+    G.add_edges_from((u, v) for u, v in zip(g.src.tolist(), g.dst.tolist()) if u != v)
+    for root in graphgen.pick_roots(g, 4, 99).tolist():
+        lv = oracle.levels(c, root)
+        d = nx.single_source_shortest_path_length(G, root)
+        want = np.full(g.n, -1, np.int32)
+        for k, v in d.items():
+            want[k] = v
+        assert np.array_equal(lv, want)
+    lab = oracle.components(c)
+    comps = list(nx.connected_components(G))
+    assert len(set(lab.tolist())) == len(comps)
+    for comp in comps:
+        assert len({int(lab[v]) for v in comp}) == 1
+        assert int(lab[next(iter(comp))]) == min(comp)
+
+
+def test_closed_forms_path_star_complete():
+    n = 50
+    c = csr(graphgen.path(n))
+    for r in (0, 17, 49):
+        assert np.array_equal(oracle.levels(c, r), np.abs(np.arange(n) - r))
+    c = csr(graphgen.star(30, center=4))
+    lv = oracle.levels(c, 4)
+    assert lv[4] == 0 and np.all(np.delete(lv, 4) == 1)
+    lv = oracle.levels(c, 7)
+    assert lv[7] == 0 and lv[4] == 1 and np.all(np.delete(lv, [4, 7]) == 2)
+    c = csr(graphgen.complete(12))
+    lv = oracle.levels(c, 3)
+    assert lv[3] == 0 and np.all(np.delete(lv, 3) == 1)
+
+
+@pytest.mark.parametrize("side", [5, 16, 33])
+def test_torus_closed_form(side):
+    g = graphgen.torus(side, seed=3000)
+    inv = graphgen.torus_coordinates(side, seed=3000)
+    c = csr(g)
+    x, y = inv % side, inv // side
+    for root in [0, 7, side * side - 1]:
+        lv = oracle.levels(c, root)
+        dx = np.abs(x - x[root])
+        dy = np.abs(y - y[root])
+        want = np.minimum(dx, side - dx) + np.minimum(dy, side - dy)
+        assert np.array_equal(lv, want)
+        assert lv.max() == 2 * (side // 2)
+
+
+def test_isolated_root_and_degree_zero():
+    g = graphgen.from_pairs(5, [(0, 1), (1, 2), (3, 3)])
+    c = csr(g)
+    p, lv, L = oracle.bfs_topdown(c, 3)          # only a self-loop: degree 0
+    assert lv.tolist() == [-1, -1, -1, 0, -1] and p.tolist() == [-1, -1, -1, 3, -1] and L == 1
+    p, lv, L = oracle.bfs_topdown(c, 4)
+    assert lv.tolist() == [-1, -1, -1, -1, 0] and L == 1
+
+
+# ------------------------------------------------------------------ certificate
+
+def test_certificate_rejects_planted_mistakes():
+    g = graphgen.rmat(9, seed=1009)
+    c = csr(g)
+    root = int(graphgen.pick_roots(g, 1, 5)[0])
+    p, lv, _ = oracle.bfs_topdown(c, root)
+    lab = oracle.components(c)
+    assert oracle.certify(c, root, lv, p, lab) == (0, -1)
+    reached = np.flatnonzero((lv > 1))
+    v = int(reached[0])
+    # level off by one
+    bad = lv.copy(); bad[v] += 1
+    assert oracle.certify(c, root, bad, p, lab)[0] in (2, 3)
+    # all levels shifted by +1 except root: parent levels break
+    bad = np.where(lv > 0, lv + 1, lv).astype(np.int32)
+    assert oracle.certify(c, root, bad, p, lab)[0] in (2, 3)
+    assert oracle.certify(c, root, bad, None, lab)[0] == 3
+    # parent that is not a neighbour
+    badp = p.copy(); badp[v] = root
+    if not np.any(c.cols[c.offsets[root]:c.offsets[root + 1]] == v):
+        assert oracle.certify(c, root, lv, badp, lab) == (2, v)
+    # parent at the same level
+    same = [int(u) for u in c.cols[c.offsets[v]:c.offsets[v + 1]] if lv[u] == lv[v]]
+    if same:
+        badp = p.copy(); badp[v] = same[0]
+        assert oracle.certify(c, root, lv, badp, lab) == (2, v)
+    # a reached vertex reported unreachable
+    bad = lv.copy(); bad[v] = -1
+    badp = p.copy(); badp[v] = -1
+    assert oracle.certify(c, root, bad, badp, lab)[0] in (4, 5)
+    # wrong root
+    bad = lv.copy(); bad[root] = 1
+    assert oracle.certify(c, root, bad, p, lab)[0] == 1
+    # an unreachable vertex (other component) reported at some level
+    unreached = np.flatnonzero(lv < 0)
+    if unreached.size:
+        bad = lv.copy(); bad[unreached[0]] = 3
+        assert oracle.certify(c, root, bad, None, lab)[0] in (3, 4, 5)
+
+
+# ------------------------------------------------------------------ DO schedule
+
+def _alg2_walk(c, level, d):
+    """Literal Algorithm 2 step at level d in Python: for each unvisited vertex
+    with neighbours, count neighbour examinations up to the first one in the
+    frontier (inclusive)."""
+    scanned = examined = 0
+    for u in range(c.n):
+        if 0 <= level[u] <= d:
+            continue
+        row = c.cols[c.offsets[u]:c.offsets[u + 1]].tolist()
+        if not row:
+            continue
+        scanned += 1
+        for k, v in enumerate(row):
+            examined += 1
+            if level[v] == d:
+                break
+    return scanned, examined
+
+
+def test_schedule_star_hand_derived():
+    n = 100
+    c = csr(graphgen.star(n, center=0))
+    s = oracle.do_schedule(c, oracle.levels(c, 0))
+    # level 0: m_f = 99, m_u = 99 -> 99*14 > 99 -> bottom-up; level 1: n_f = 99, 99*24 >= 100 stays
+    assert s.dir.tolist() == [1, 1]
+    assert s.nf.tolist() == [1, 99] and s.mf.tolist() == [99, 99]
+    assert s.scanned.tolist() == [99, 0] and s.examined.tolist() == [99, 0]
+    s = oracle.do_schedule(c, oracle.levels(c, 5))
+    # level 0 (leaf 5): m_f = 1, m_u = 197 -> top-down; level 1 (centre): 99*14 > 98 -> bottom-up
+    assert s.dir.tolist() == [0, 1, 1]
+    assert s.nf.tolist() == [1, 1, 98] and s.mf.tolist() == [1, 99, 98]
+    assert s.nnext.tolist() == [1, 98, 0]
+
+
+def test_schedule_path_switches_back():
+    n = 100
+    c = csr(graphgen.path(n))
+    s = oracle.do_schedule(c, oracle.levels(c, 0))
+    # level d frontier {d}: m_f = 2, m_u = 197 - 2d; bottom-up from d = 85, then n_f*24 < 100
+    # sends it back to top-down on the next level, alternating.
+    assert s.dir[:85].tolist() == [0] * 85
+    assert s.dir[85] == 1 and s.dir[86] == 0 and s.dir[87] == 1
+    td = oracle.do_schedule(c, oracle.levels(c, 0), mode=oracle.MODE_TD)
+    assert td.dir.tolist() == [0] * n
+    bu = oracle.do_schedule(c, oracle.levels(c, 0), mode=oracle.MODE_BU)
+    assert bu.dir.tolist() == [1] * n
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_schedule_counts_match_literal_walk(seed):
+    g = graphgen.rmat(8, seed=300 + seed)
+    c = csr(g)
+    root = int(graphgen.pick_roots(g, 1, seed)[0])
+    lv = oracle.levels(c, root)
+    s = oracle.do_schedule(c, lv, mode=oracle.MODE_BU)
+    deg = np.diff(c.offsets)
+    for d in range(s.num_levels):
+        assert s.nf[d] == np.sum(lv == d)
+        assert s.mf[d] == deg[lv == d].sum()
+        assert s.nnext[d] == np.sum(lv == d + 1)
+        assert (s.scanned[d], s.examined[d]) == _alg2_walk(c, lv, d)
+    sd = oracle.do_schedule(c, lv, mode=oracle.MODE_DO)
+    # re-derive each direction from the rule with m_u recomputed from scratch
+    cur = 0
+    for d in range(sd.num_levels):
+        m_u = deg[(lv > d) | (lv < 0)].sum()
+        if cur == 0 and sd.mf[d] * 14 > m_u:
+            cur = 1
+        elif cur == 1 and sd.nf[d] * 24 < c.n:
+            cur = 0
+        assert sd.dir[d] == cur
