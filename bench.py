@@ -1,0 +1,329 @@
+#!/usr/bin/env python
+"""Benchmark: GTEPS (harmonic mean over roots) of direction-optimizing BFS on one GB300.
+
+Workload (default): R-MAT scale 26, edge factor 16, initiator .57/.19/.19/.05,
+symmetrised, self-loops and duplicates removed, ids relabelled from seed
+1026; 64 distinct seeded roots with degree > 0; CSR layout; alpha 14, beta 24.
+A step is one full search (the whole level loop: init, top-down / bottom-up
+levels, conversions, direction switches) from the next root, cycling through
+the 64 roots; inputs (the 9 GB graph) are resident and larger than L2.
+
+value   = undirected edges x steps / total device time of the steps, summed
+          over ranks (= harmonic mean of per-root GTEPS when every step is one
+          root); CUDA events on the launching stream, after W warm-up steps.
+e2e     = the same through the public API with host buffers: each step also
+          copies level[] and parent[] (8n bytes) back to pinned host memory.
+roofline: algorithmic bytes per search from the search's own per-level
+          counters (paper_1705_04590_gb300.roofline) / measured duration,
+          against the measured HBM copy bandwidth (MEASURED_PEAKS.json).
+cpu_baseline: the serial CPU oracle (Algorithm 1) on one host core, on a
+          bounded sample: R-MAT at a smaller scale with the same generator.
+
+--impl reference times that oracle alone, the same way, one search per step.
+Multi-GPU (torchrun): replicas only -- each rank searches its own copy of the
+graph from its own roots; no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "bfs_single_kernel_traffic.json")
+KERNEL_SOURCES = ["paper_1705_04590_gb300/csrc/bfs_single.cu", "paper_1705_04590_gb300/csrc/bfs_common.cuh"]
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi sampled every 200 ms while the timed region runs."""
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={CLOCK_QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "", 1).isdigit())
+        mx = max((float(r[2]) for r in rows if r[2].replace(".", "", 1).isdigit()), default=None)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "of measured"}
+    return {"hbm_gbs": 6800.0, "source": "of fallback"}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------ CPU oracle (baseline / reference arm)
+
+def oracle_sample(scale: int, nroots: int, repeats: int = 1):
+    """Serial Algorithm 1 on R-MAT `scale` (same generator): (GTEPS hmean, seconds, searches, m)."""
+    import oracle
+    from graphgen import workloads
+    oracle.build()
+    w = workloads.RMAT[scale]
+    e = w.edges()
+    roots = w.roots(e, nroots).tolist()
+    ref = oracle.build_csr(e.n, e.src, e.dst)
+    del e
+    m = ref.nnz // 2
+    times = []
+    for _ in range(repeats):
+        for r in roots:
+            t0 = time.perf_counter()
+            oracle.bfs_topdown(ref, r)
+            times.append(time.perf_counter() - t0)
+    total = sum(times)
+    return len(times) * m / total / 1e9, total, len(times), m, times
+
+
+def reference_arm(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    from graphgen import workloads
+    oracle.build()
+    # sample scale chosen so that (W + K) serial searches take a few minutes on one core
+    scale = args.cpu_scale
+    while scale > 16 and (args.steps + args.warmup) * 1.6 * 2.0 ** (scale - 22) > 150.0:
+        scale -= 1
+    w = workloads.RMAT[scale]
+    e = w.edges()
+    ref = oracle.build_csr(e.n, e.src, e.dst)
+    roots = w.roots(e, 64).tolist()
+    del e
+    m = ref.nnz // 2
+    for i in range(args.warmup):
+        oracle.bfs_topdown(ref, roots[i % len(roots)])
+    times = []
+    for i in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.bfs_topdown(ref, roots[i % len(roots)])
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = args.steps * m / total / 1e9
+    sample = (f"serial Algorithm 1 (oracle) on R-MAT scale {scale} (same generator, edge factor 16; "
+              f"1/{2 ** (args.scale - scale)} of the scale-{args.scale} graph), one search per step, "
+              f"{len(roots)} roots cycled")
+    line = {"impl": "reference", "metric": f"GTEPS harmonic mean, R-MAT scale {args.scale}, 1 GB300", "value": value,
+            "unit": "GTEPS", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": f"rmat-scale{args.scale}-ef16 single-source BFS", "sample_scale": scale,
+                       "roots": len(roots), "undirected_edges": m},
+            "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+
+def our_arm(args):
+    import numpy as np
+    import torch
+
+    import paper_1705_04590_gb300 as bfs
+    from graphgen import workloads
+    from paper_1705_04590_gb300 import roofline
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    bfs.build()
+    bfs.load()
+
+    w = workloads.RMAT[args.scale]
+    t0 = time.time()
+    e = w.edges()
+    roots_all = w.roots(e, args.roots).tolist()
+    g = bfs.Graph.from_edges(e.src, e.dst, e.n)
+    n = e.n
+    del e
+    setup_s = time.time() - t0
+    m = g.nnz // 2
+    roots = roots_all[rank % len(roots_all):] + roots_all[:rank % len(roots_all)]
+    opts = bfs.options(mode=bfs.MODE_DO, alpha=14, beta=24)
+    level = torch.empty(n, dtype=torch.int32, device="cuda")
+    parent = torch.empty(n, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    # per-root algorithmic bytes from the search's own counters (untimed pass)
+    bytes_of = {}
+    levels_of = {}
+    for r in roots:
+        info = g.run(r, parent=parent, level=level, opts=opts, stats=True, record_levels=4096)
+        bytes_of[r] = roofline.search_bytes(n, info["records"])
+        levels_of[r] = info["num_levels"]
+
+    for i in range(args.warmup):
+        g.run(roots[i % len(roots)], parent=parent, level=level, opts=opts)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    torch.cuda.synchronize()
+    evs[0].record(stream)
+    for i in range(args.steps):
+        g.run(roots[i % len(roots)], parent=parent, level=level, opts=opts)
+        evs[i + 1].record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    g.sync()
+    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
+    total_ms = evs[0].elapsed_time(evs[-1])
+    if ws > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = ws * args.steps * m / (total_ms / 1e3) / 1e9
+    alg_bytes = sum(bytes_of[roots[i % len(roots)]] for i in range(args.steps))
+    achieved = alg_bytes / (sum(step_ms) / 1e3) / 1e9
+    peaks = measured_peaks()
+
+    # end to end: the same searches with level[] and parent[] copied to pinned host memory every step
+    e2e_steps = min(args.steps, 64)
+    h_level = torch.empty(n, dtype=torch.int32, pin_memory=True)
+    h_parent = torch.empty(n, dtype=torch.int32, pin_memory=True)
+    torch.cuda.synchronize()
+    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ea.record(stream)
+    for i in range(e2e_steps):
+        g.run(roots[i % len(roots)], parent=parent, level=level, opts=opts)
+        h_level.copy_(level, non_blocking=True)
+        h_parent.copy_(parent, non_blocking=True)
+    eb.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = ea.elapsed_time(eb)
+    e2e_value = ws * e2e_steps * m / (e2e_ms / 1e3) / 1e9
+
+    traffic = None
+    if os.path.exists(TRAFFIC_FILE):
+        with open(TRAFFIC_FILE) as f:
+            tr = json.load(f)
+        if tr.get("kernel_source_hash") == kernel_source_hash() and tr.get("scale") == args.scale:
+            traffic = tr.get("dram_bytes_per_launch")
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        gteps, secs, cnt, m_s, _ = oracle_sample(args.cpu_scale, 8)
+        cpu = {"value": gteps, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+               "sample": f"serial Algorithm 1 (oracle, one host core) on R-MAT scale {args.cpu_scale} "
+                         f"(same generator; {m_s} undirected edges), {cnt} roots, {secs:.1f} s of CPU work"}
+
+    if rank == 0:
+        line = {
+            "metric": f"GTEPS harmonic mean, R-MAT scale {args.scale}, 1 GB300 (single-source, direction-optimizing)",
+            "value": value, "unit": "GTEPS", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": f"rmat-scale{args.scale}-ef16 single-source BFS, {len(roots)} roots cycled",
+                       "n": n, "nnz": g.nnz, "undirected_edges": m, "alpha": 14, "beta": 24, "layout": "csr",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                       "l2": "inputs larger than L2 (graph resident in HBM, %.1f GB)" % (g.device_bytes() / 1e9),
+                       "levels_per_search": float(np.mean([levels_of[r] for r in roots])),
+                       "setup_s": round(setup_s, 1)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                         "peak_source": peaks["source"], "kernel": "bfs_single_kernel",
+                         "algorithmic_bytes_per_search": alg_bytes / args.steps},
+            "e2e": {"value": e2e_value, "unit": "GTEPS", "h2d_bytes_per_step": 4, "d2h_bytes_per_step": 8 * n,
+                    "steps": e2e_steps},
+            "gpu_launches": args.steps,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+            "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
+        }
+        print(json.dumps(line), flush=True)
+    g.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=256)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scale", type=int, default=26)
+    ap.add_argument("--roots", type=int, default=64)
+    ap.add_argument("--cpu-scale", type=int, default=22)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return reference_arm(args)
+    return our_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,283 @@
+/*
+ * bfs.h -- C ABI of a single-GPU direction-optimizing breadth-first search
+ * library for GB300 (sm_103a).
+ *
+ * The operations follow Bulu\c{c}, Beamer, Madduri, Asanovic, Patterson,
+ * "Distributed-Memory Breadth-First Search on Massive Graphs" (2015):
+ *   - the problem statement of Algorithm 1/2: input G(V, E) and a source s;
+ *     output parent[v] = the parent of v in a breadth-first spanning tree,
+ *     -1 if v is unreachable, parent[s] = s; the parent of a vertex d hops
+ *     from s is any vertex d-1 hops from s with an edge to it ("Breadth-First
+ *     Search");
+ *   - top-down steps (Algorithm 1), bottom-up steps (Algorithm 2) and the
+ *     per-level choice between them ("Parallel Direction-Optimizing BFS");
+ *   - CSR storage, or DCSC for hypersparse sub-matrices ("Graph
+ *     Representation"); graphs are undirected, duplicates and self-loops are
+ *     pruned ("Data Sets").
+ *
+ * Conventions for every call:
+ *   - Every function returns a bfs_status; no C++ exception crosses the ABI.
+ *     On error a message is available from bfs_last_error() (thread-local,
+ *     valid until the next call on that thread).
+ *   - Vertex ids are int32_t (n <= 2^31 - 1); edge counts and offsets are
+ *     int64_t.
+ *   - "stream" is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Work is enqueued on it; outputs are valid once the stream has
+ *     reached the point of the call (unless a function says it synchronises).
+ *   - The library owns graph storage and per-graph work buffers (allocated
+ *     through the bfs_allocator given at creation, or cudaMalloc if NULL).  The
+ *     caller owns every output buffer and every stream.
+ *   - A failed call leaves no partially built object behind.
+ */
+#ifndef BFS_GB300_H
+#define BFS_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BFS_OK = 0,
+    BFS_ERR_INVALID = 1,     /* bad argument (NULL handle, root out of range, bad sizes, bad CSR) */
+    BFS_ERR_OOM = 2,         /* device or host allocation failed */
+    BFS_ERR_CUDA = 3,        /* a CUDA runtime call failed (message names it) */
+    BFS_ERR_TIMEOUT = 4,     /* a bounded device wait (grid barrier) ran out; outputs undefined */
+    BFS_ERR_BUSY = 5,        /* server: no free capacity (queue full) */
+    BFS_ERR_NOT_READY = 6,   /* server: ticket still in flight */
+    BFS_ERR_UNSUPPORTED = 7  /* option or layout not supported for this graph/device */
+} bfs_status;
+
+typedef struct bfs_graph bfs_graph;
+typedef struct bfs_server bfs_server;
+
+/*
+ * Device memory hook.  alloc(bytes, stream, ctx) returns device memory (NULL
+ * on failure); free(ptr, bytes, stream, ctx) releases it.  Memory may be
+ * stream-ordered on `stream`.  NULL hook => cudaMalloc / cudaFree.
+ */
+typedef struct {
+    void* (*alloc)(size_t bytes, void* stream, void* ctx);
+    void (*free)(void* ptr, size_t bytes, void* stream, void* ctx);
+    void* ctx;
+} bfs_allocator;
+
+/* graph construction flags */
+#define BFS_FLAG_DEVICE_PTRS   1u  /* input arrays are device pointers (else host memory) */
+#define BFS_FLAG_SYMMETRIZE    2u  /* store each edge in both rows (undirected); required for edge lists */
+#define BFS_FLAG_BUILD_DCSC    4u  /* also build the column-block DCSC tiles (layout BFS_LAYOUT_DCSC_TILED) */
+#define BFS_FLAG_CHECK_SYMMETRY 8u /* from_csr: verify that the CSR is symmetric (one extra pass) */
+
+/* search direction policy ("Parallel Direction-Optimizing BFS") */
+#define BFS_MODE_DO       0   /* per level: top-down or bottom-up by the alpha/beta rule */
+#define BFS_MODE_TD_ONLY  1   /* every level top-down (Algorithm 1) */
+#define BFS_MODE_BU_ONLY  2   /* every level bottom-up (Algorithm 2) */
+#define BFS_MODE_RANDOM   3   /* per level a seeded coin flip (testing: levels must not change) */
+
+#define BFS_LAYOUT_CSR          0
+#define BFS_LAYOUT_DCSC_TILED   1
+
+#define BFS_PARENT_ANY     0  /* any valid parent (whichever claim wins) */
+#define BFS_PARENT_MIN_ID  1  /* the minimum-id valid parent: the (select2nd, min) semiring */
+
+/*
+ * Options of one search; pass NULL for the defaults (DO, CSR, alpha 14,
+ * beta 24, ANY parent, 10 s barrier limit).  Direction rule, at the start of
+ * level d with frontier size n_f, frontier degree sum m_f and degree sum m_u
+ * of the vertices not yet reached: in top-down, switch to bottom-up when
+ * m_f * alpha > m_u; in bottom-up, switch to top-down when n_f * beta < n.
+ * Levels never depend on these choices, only the work does.
+ */
+typedef struct {
+    int32_t mode;          /* BFS_MODE_* */
+    int32_t layout;        /* BFS_LAYOUT_*; DCSC needs a graph built with BFS_FLAG_BUILD_DCSC */
+    int32_t alpha;         /* >= 1 */
+    int32_t beta;          /* >= 1 */
+    int32_t parent_mode;   /* BFS_PARENT_* */
+    int32_t td_big_degree; /* top-down: frontier vertices above this degree are split into edge chunks
+                              shared by all warps (0 = tuned default) */
+    int64_t timeout_ms;    /* limit of every device-side wait; 0 = default 10000 */
+    uint64_t seed;         /* BFS_MODE_RANDOM only */
+    int32_t debug_barrier_extra; /* testing only: every grid barrier waits for this many arrivals that
+                                    never come, so each wait runs out after timeout_ms (0 = off) */
+    int32_t reserved;
+} bfs_options;
+
+void bfs_options_default(bfs_options* opt);
+
+/* One record per level of a search (device counters copied back). */
+typedef struct {
+    int32_t dir;          /* 0 top-down, 1 bottom-up */
+    int32_t reserved;
+    int64_t nf;           /* frontier size at the start of the level */
+    int64_t mf;           /* sum of degrees over the frontier */
+    int64_t nnext;        /* vertices discovered by the level */
+    int64_t mnext;        /* their degree sum */
+    int64_t scanned;      /* bottom-up: unvisited vertices with degree > 0 that searched */
+    int64_t examined;     /* top-down: m_f; bottom-up: sum over searching vertices of the 1-based
+                             position of the first frontier neighbour in sorted order, or the degree */
+} bfs_level_record;
+
+typedef struct {
+    int32_t num_levels;        /* levels with a non-empty frontier */
+    int32_t levels_capacity;   /* in: entries available at `levels` (may be 0) */
+    bfs_level_record* levels;  /* in: host array or NULL; out: min(num_levels, capacity) records */
+    int64_t vertices_reached;
+    int64_t edges_examined;    /* sum of `examined` over all levels */
+} bfs_stats;
+
+/* ----------------------------------------------------------------- graphs */
+
+/*
+ * Build a graph from an undirected edge list (src[i], dst[i]), i < n_edges,
+ * ids in [0, n_vertices).  Self-loops and duplicate edges are dropped and each
+ * row is sorted ascending ("Graph Representation", "Data Sets").  flags must
+ * include BFS_FLAG_SYMMETRIZE (directed graphs are not supported).  With
+ * BFS_FLAG_DEVICE_PTRS, src/dst are device pointers, else host pointers
+ * (copied in chunks).  The build runs on `stream` and returns when the graph
+ * is ready.  Isolated vertices keep their ids.  *out receives the handle.
+ * Errors: INVALID (NULL pointers, n_vertices outside [1, 2^31-1], an id out of
+ * range, no SYMMETRIZE flag), OOM, CUDA.
+ */
+bfs_status bfs_graph_create_from_edges(const int32_t* src, const int32_t* dst, int64_t n_edges,
+                                       int64_t n_vertices, uint32_t flags, const bfs_allocator* alloc,
+                                       void* stream, bfs_graph** out);
+
+/*
+ * Build a graph from a CSR that is already undirected: row_offsets[n+1]
+ * (int64, row_offsets[0] = 0, non-decreasing), col_ids[nnz] (int32, each row
+ * strictly ascending, no self-loops).  The arrays are copied.  The row rules
+ * and id ranges are checked on the device (INVALID if broken); symmetry only
+ * with BFS_FLAG_CHECK_SYMMETRY.
+ */
+bfs_status bfs_graph_create_from_csr(const int64_t* row_offsets, const int32_t* col_ids, int64_t n,
+                                     int64_t nnz, uint32_t flags, const bfs_allocator* alloc, void* stream,
+                                     bfs_graph** out);
+
+/* n, nnz (directed entries = 2 x undirected edges) and device bytes held; any pointer may be NULL. */
+bfs_status bfs_graph_info(const bfs_graph* g, int64_t* n, int64_t* nnz, int64_t* device_bytes);
+
+/*
+ * Device pointers of the stored CSR (row_offsets int64[n+1], col_ids
+ * int32[nnz]); owned by the graph, valid until bfs_graph_destroy.
+ */
+bfs_status bfs_graph_csr(const bfs_graph* g, const int64_t** row_offsets, const int32_t** col_ids);
+
+/*
+ * Copy the stored CSR into caller buffers (host or device; the copy kind is
+ * inferred): offsets_out int64[n+1], cols_out int32[nnz] (either may be
+ * NULL).  Synchronises `stream`.
+ */
+bfs_status bfs_graph_copy_csr(const bfs_graph* g, int64_t* offsets_out, int32_t* cols_out, void* stream);
+
+/* Device pointers of the DCSC tiles (see bfs_dcsc_layout); INVALID if not built. */
+typedef struct {
+    int32_t num_blocks;          /* p_c column blocks */
+    int32_t block_shift;         /* block of column v = v >> block_shift */
+    const int64_t* tile_ptr;     /* [num_blocks+1] start of each tile in jc/cp (entries) */
+    const int32_t* jc;           /* non-empty row ids of each tile, ascending */
+    const int64_t* cp;           /* [total rows + num_blocks] edge start per listed row (tile-local end sentinel) */
+    const int32_t* ir;           /* column ids (global), rows sorted ascending */
+    int64_t total_rows;          /* sum of non-empty rows over tiles (= entries of jc) */
+} bfs_dcsc_layout;
+bfs_status bfs_graph_dcsc(const bfs_graph* g, bfs_dcsc_layout* out);
+
+void bfs_graph_destroy(bfs_graph* g);
+
+/* ----------------------------------------------------------------- search */
+
+/*
+ * Breadth-first search from `root` (Algorithm 1/2 with the per-level
+ * direction choice).  parent_dev / level_dev: caller-owned device arrays of n
+ * int32, either may be NULL.  level[v] = hop distance or -1; parent as in the
+ * problem statement.  Levels are exact; parents are any valid parent (or the
+ * minimum one with BFS_PARENT_MIN_ID).  A degree-0 root is valid (only it is
+ * reached).  The whole level loop runs on the device in one launch (no host
+ * round trip per level).  Asynchronous on `stream`, unless stats != NULL: then
+ * the call synchronises the stream and fills *stats, and a device-side
+ * timeout is reported as BFS_ERR_TIMEOUT.  Without stats, a timeout is
+ * reported by the next call that synchronises on this graph
+ * (bfs_graph_sync).  Runs on one graph handle are serialised by the library
+ * (they share work buffers).  Errors: INVALID (root outside [0, n), bad
+ * options), UNSUPPORTED, CUDA, TIMEOUT.
+ */
+bfs_status bfs_run(bfs_graph* g, int32_t root, int32_t* parent_dev, int32_t* level_dev,
+                   const bfs_options* opt, void* stream, bfs_stats* stats);
+
+/*
+ * One search from a set of roots, all at level 0 (level = distance to the
+ * nearest root; parent[r] = r for each root).  For a disjoint union of graphs
+ * with one root per part this is each part's own BFS, which is how an uneven
+ * batch of many graphs runs in one launch.  roots_host: k distinct ids
+ * (repeats are ignored), 1 <= k <= n.  Otherwise as bfs_run.
+ */
+bfs_status bfs_run_multiroot(bfs_graph* g, const int32_t* roots_host, int32_t k, int32_t* parent_dev,
+                             int32_t* level_dev, const bfs_options* opt, void* stream, bfs_stats* stats);
+
+/*
+ * Batched multi-source BFS: k independent searches (roots_host[0..k-1],
+ * repeats allowed), packed 64 at a time as per-vertex 64-bit lane masks and
+ * advanced together, one fused persistent launch per 64 roots.
+ * level_dev: device int32[k][n] row-major (row i = search from roots_host[i]).
+ * parent_dev: NULL, or int32[k][n]: for each reached v != root the minimum-id
+ * neighbour one level closer (BFS_PARENT_MIN_ID semantics).  Asynchronous
+ * on `stream`.  Errors: INVALID, OOM, CUDA.
+ */
+bfs_status bfs_run_multi(bfs_graph* g, const int32_t* roots_host, int32_t k, int32_t* level_dev,
+                         int32_t* parent_dev, const bfs_options* opt, void* stream);
+
+/* Wait for the graph's enqueued searches; returns the first device-side error since the last sync. */
+bfs_status bfs_graph_sync(bfs_graph* g, void* stream);
+
+/* ----------------------------------------------------------------- server */
+
+/*
+ * A query server that keeps graphs resident and runs BFS queries with
+ * continuous batching: each graph has up to max_lanes (<= 64) lane slots of a
+ * running multi-source search; a query is admitted into a free slot at the
+ * next level boundary (its lane starts at the current iteration, and its
+ * levels count from there), so queries that arrive while others run share
+ * the device work.  Admission is bounded by hbm_budget_bytes for per-query
+ * state.  A host thread drives the device; outputs land in caller memory.
+ */
+bfs_status bfs_server_create(int64_t hbm_budget_bytes, int32_t max_lanes, bfs_server** out);
+
+/* Make `g` servable (the server does not own it; keep it alive until destroy). */
+bfs_status bfs_server_add_graph(bfs_server* s, bfs_graph* g, int32_t* slot);
+
+/*
+ * Queue a query (graph slot, root).  level_out_host: caller-owned host array
+ * of the graph's n int32, filled with the levels when the ticket completes
+ * (must stay valid until then).  Never blocks; BUSY if the request queue is
+ * full, INVALID for a bad slot/root.
+ */
+bfs_status bfs_submit(bfs_server* s, int32_t slot, int32_t root, int32_t* level_out_host, uint64_t* ticket);
+
+/* BFS_OK when done (result written), BFS_ERR_NOT_READY while in flight, INVALID for an unknown ticket. */
+bfs_status bfs_poll(bfs_server* s, uint64_t ticket);
+
+/* Block until done or timeout_ms elapsed (NOT_READY); timeout_ms < 0 waits forever. */
+bfs_status bfs_wait(bfs_server* s, uint64_t ticket, int64_t timeout_ms);
+
+/*
+ * Latency of completed tickets in microseconds (submit -> done), and counters:
+ * out[0] completed, out[1] device launches, out[2] lanes filled summed over launches.
+ */
+bfs_status bfs_server_stats(bfs_server* s, int64_t* counters3);
+bfs_status bfs_ticket_latency_us(bfs_server* s, uint64_t ticket, double* us);
+
+void bfs_server_destroy(bfs_server* s);
+
+/* ----------------------------------------------------------------- misc */
+
+const char* bfs_status_string(bfs_status st);
+const char* bfs_last_error(void);
+/* Library version string. */
+const char* bfs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

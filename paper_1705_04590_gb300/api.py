@@ -1,0 +1,233 @@
+"""Python binding over the C ABI (include/bfs.h): argument marshalling only.
+
+Every step of a search runs in the library's CUDA kernels; this module turns
+torch tensors into device pointers and torch streams into cudaStream_t.
+Graph storage comes from PyTorch's caching allocator through the ABI's
+allocator hook (PyTorch is used for device memory and streams only).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib as L
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream) -> int | None:
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) or None
+
+
+def _dev_ptr(t, dtype_name: str, numel: int | None = None, what: str = "tensor"):
+    if t is None:
+        return None
+    torch = _torch()
+    want = getattr(torch, dtype_name)
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{what} must be a CUDA tensor")
+    if t.dtype != want or not t.is_contiguous():
+        raise TypeError(f"{what} must be a contiguous {dtype_name} tensor")
+    if numel is not None and t.numel() < numel:
+        raise ValueError(f"{what} needs at least {numel} elements")
+    return t.data_ptr()
+
+
+class _TorchAllocator:
+    """bfs_allocator backed by torch.cuda.caching_allocator_alloc / _delete."""
+
+    def __init__(self):
+        torch = _torch()
+        self._torch = torch
+        self._dev = torch.cuda.current_device()
+
+        def _alloc(nbytes, stream, ctx):
+            try:
+                return int(torch.cuda.caching_allocator_alloc(int(nbytes), self._dev, stream or 0))
+            except Exception:
+                return None
+
+        def _free(ptr, nbytes, stream, ctx):
+            try:
+                torch.cuda.caching_allocator_delete(ptr)
+            except Exception:
+                pass
+
+        self._alloc_cb = L.ALLOC_FN(_alloc)
+        self._free_cb = L.FREE_FN(_free)
+        self.struct = L.Allocator(self._alloc_cb, self._free_cb, None)
+
+
+def options(mode: int = L.MODE_DO, layout: int = L.LAYOUT_CSR, alpha: int = 14, beta: int = 24,
+            parent_mode: int = L.PARENT_ANY, td_big_degree: int = 0, timeout_ms: int = 10000, seed: int = 0,
+            debug_barrier_extra: int = 0) -> L.Options:
+    o = L.Options()
+    L.load().bfs_options_default(ctypes.byref(o))
+    o.mode, o.layout, o.alpha, o.beta, o.parent_mode = mode, layout, alpha, beta, parent_mode
+    o.td_big_degree, o.timeout_ms, o.seed, o.debug_barrier_extra = td_big_degree, timeout_ms, seed, \
+        debug_barrier_extra
+    return o
+
+
+class Graph:
+    """A resident undirected graph (CSR, optionally DCSC tiles) on the current CUDA device."""
+
+    def __init__(self, handle: int, allocator, keepalive=()):
+        self._h = ctypes.c_void_p(handle)
+        self._alloc = allocator
+        self._keep = keepalive
+        n, nnz, nb = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        L.check(L.load().bfs_graph_info(self._h, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(nb)), "graph_info")
+        self.n, self.nnz = n.value, nnz.value
+
+    # ---------------------------------------------------------------- creation
+    @classmethod
+    def from_edges(cls, src, dst, n: int, dcsc: bool = False, stream=None, torch_allocator: bool = True) -> "Graph":
+        """src/dst: numpy int32 arrays (host) or int32 CUDA tensors (device)."""
+        lib = L.load()
+        torch = _torch()
+        flags = L.FLAG_SYMMETRIZE | (L.FLAG_BUILD_DCSC if dcsc else 0)
+        if isinstance(src, torch.Tensor):
+            if src.numel() != dst.numel():
+                raise ValueError("src and dst differ in length")
+            ps, pd = _dev_ptr(src, "int32", what="src"), _dev_ptr(dst, "int32", what="dst")
+            flags |= L.FLAG_DEVICE_PTRS
+            m = src.numel()
+            keep = (src, dst)
+        else:
+            src = np.ascontiguousarray(src, np.int32)
+            dst = np.ascontiguousarray(dst, np.int32)
+            if src.shape != dst.shape:
+                raise ValueError("src and dst differ in length")
+            ps, pd, m, keep = src.ctypes.data, dst.ctypes.data, int(src.shape[0]), (src, dst)
+        alloc = _TorchAllocator() if torch_allocator else None
+        h = ctypes.c_void_p()
+        st = lib.bfs_graph_create_from_edges(ps, pd, m, n, flags, ctypes.byref(alloc.struct) if alloc else None,
+                                             _stream_ptr(stream), ctypes.byref(h))
+        L.check(st, "bfs_graph_create_from_edges")
+        del keep
+        return cls(h.value, alloc)
+
+    @classmethod
+    def from_csr(cls, offsets, cols, n: int, check_symmetry: bool = False, dcsc: bool = False, stream=None,
+                 torch_allocator: bool = True) -> "Graph":
+        lib = L.load()
+        torch = _torch()
+        flags = (L.FLAG_CHECK_SYMMETRY if check_symmetry else 0) | (L.FLAG_BUILD_DCSC if dcsc else 0)
+        if isinstance(offsets, torch.Tensor):
+            po, pc = _dev_ptr(offsets, "int64", n + 1, "offsets"), _dev_ptr(cols, "int32", what="cols")
+            nnz = cols.numel()
+            flags |= L.FLAG_DEVICE_PTRS
+        else:
+            offsets = np.ascontiguousarray(offsets, np.int64)
+            cols = np.ascontiguousarray(cols, np.int32)
+            if offsets.shape[0] != n + 1:
+                raise ValueError("offsets must have n+1 entries")
+            po, pc, nnz = offsets.ctypes.data, cols.ctypes.data if cols.size else None, int(cols.shape[0])
+        alloc = _TorchAllocator() if torch_allocator else None
+        h = ctypes.c_void_p()
+        st = lib.bfs_graph_create_from_csr(po, pc, n, nnz, flags, ctypes.byref(alloc.struct) if alloc else None,
+                                           _stream_ptr(stream), ctypes.byref(h))
+        L.check(st, "bfs_graph_create_from_csr")
+        return cls(h.value, alloc)
+
+    # ---------------------------------------------------------------- queries
+    @property
+    def handle(self):
+        return self._h
+
+    def device_bytes(self) -> int:
+        nb = ctypes.c_int64()
+        L.check(L.load().bfs_graph_info(self._h, None, None, ctypes.byref(nb)), "graph_info")
+        return nb.value
+
+    def csr_host(self):
+        """(offsets int64[n+1], cols int32[nnz]) copied to host numpy arrays."""
+        off = np.empty(self.n + 1, np.int64)
+        cols = np.empty(max(self.nnz, 1), np.int32)
+        L.check(L.load().bfs_graph_copy_csr(self._h, off.ctypes.data, cols.ctypes.data, None), "graph_copy_csr")
+        return off, cols[: self.nnz]
+
+    def dcsc_layout(self) -> L.DcscLayout:
+        d = L.DcscLayout()
+        L.check(L.load().bfs_graph_dcsc(self._h, ctypes.byref(d)), "graph_dcsc")
+        return d
+
+    # ---------------------------------------------------------------- searches
+    def run(self, root: int, parent=None, level=None, opts: L.Options | None = None, stream=None,
+            stats: bool = False, record_levels: int = 0):
+        """BFS from root into caller-owned int32 CUDA tensors (either may be None).
+        With stats=True the call synchronises and returns (num_levels, reached, records)."""
+        lib = L.load()
+        pp = _dev_ptr(parent, "int32", self.n, "parent")
+        pl = _dev_ptr(level, "int32", self.n, "level")
+        st_ptr, holder = self._stats(stats, record_levels)
+        st = lib.bfs_run(self._h, int(root), pp, pl, ctypes.byref(opts) if opts else None, _stream_ptr(stream),
+                         st_ptr)
+        L.check(st, "bfs_run")
+        return self._stats_out(holder)
+
+    def run_multiroot(self, roots, parent=None, level=None, opts: L.Options | None = None, stream=None,
+                      stats: bool = False, record_levels: int = 0):
+        lib = L.load()
+        r = np.ascontiguousarray(roots, np.int32)
+        pp = _dev_ptr(parent, "int32", self.n, "parent")
+        pl = _dev_ptr(level, "int32", self.n, "level")
+        st_ptr, holder = self._stats(stats, record_levels)
+        st = lib.bfs_run_multiroot(self._h, r.ctypes.data, int(r.shape[0]), pp, pl,
+                                   ctypes.byref(opts) if opts else None, _stream_ptr(stream), st_ptr)
+        L.check(st, "bfs_run_multiroot")
+        return self._stats_out(holder)
+
+    def run_multi(self, roots, level, parent=None, opts: L.Options | None = None, stream=None):
+        """k searches packed as 64-bit lane masks; level/parent: int32 CUDA tensors of k*n."""
+        lib = L.load()
+        r = np.ascontiguousarray(roots, np.int32)
+        k = int(r.shape[0])
+        pl = _dev_ptr(level, "int32", k * self.n, "level")
+        pp = _dev_ptr(parent, "int32", k * self.n, "parent")
+        st = lib.bfs_run_multi(self._h, r.ctypes.data, k, pl, pp, ctypes.byref(opts) if opts else None,
+                               _stream_ptr(stream))
+        L.check(st, "bfs_run_multi")
+
+    def sync(self, stream=None):
+        L.check(L.load().bfs_graph_sync(self._h, _stream_ptr(stream)), "bfs_graph_sync")
+
+    @staticmethod
+    def _stats(want: bool, cap: int):
+        if not want:
+            return None, None
+        s = L.Stats()
+        recs = (L.LevelRecord * max(cap, 1))()
+        s.levels_capacity = cap
+        s.levels = ctypes.cast(recs, ctypes.POINTER(L.LevelRecord))
+        return ctypes.byref(s), (s, recs, cap)
+
+    @staticmethod
+    def _stats_out(holder):
+        if holder is None:
+            return None
+        s, recs, cap = holder
+        nrec = min(s.num_levels, cap)
+        rows = [(r.dir, r.nf, r.mf, r.nnext, r.mnext, r.scanned, r.examined) for r in recs[:nrec]]
+        arr = np.array(rows, dtype=np.int64).reshape(-1, 7)
+        return {"num_levels": s.num_levels, "reached": s.vertices_reached, "edges_examined": s.edges_examined,
+                "records": arr}
+
+    def close(self):
+        if self._h:
+            L.load().bfs_graph_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

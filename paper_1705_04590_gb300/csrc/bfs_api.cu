@@ -1,0 +1,332 @@
+// bfs_api.cu -- the extern "C" entry points declared in include/bfs.h.
+//
+// Argument checking, handle life cycle, the allocator hook, stream ordering
+// between runs that share a graph's work buffers, and error reporting
+// (status codes + a thread-local message).  All compute is in the kernels of
+// bfs_single.cu / bfs_multi.cu / graph_build.cu.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "bfs_internal.h"
+
+namespace bfsrt {
+
+static thread_local std::string t_last_error;
+
+void set_error(const std::string& msg) { t_last_error = msg; }
+
+bfs_status fail(bfs_status st, const std::string& msg) {
+    t_last_error = msg;
+    return st;
+}
+
+bfs_status cuda_fail(cudaError_t e, const char* what) {
+    t_last_error = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return e == cudaErrorMemoryAllocation ? BFS_ERR_OOM : BFS_ERR_CUDA;
+}
+
+void* DeviceAlloc::alloc(size_t bytes, cudaStream_t s) {
+    if (bytes == 0) bytes = 16;
+    if (has_hook && hook.alloc) return hook.alloc(bytes, (void*)s, hook.ctx);
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void DeviceAlloc::release(void* p, size_t bytes, cudaStream_t s) {
+    if (!p) return;
+    if (bytes == 0) bytes = 16;
+    if (has_hook && hook.free) {
+        hook.free(p, bytes, (void*)s, hook.ctx);
+        return;
+    }
+    cudaFree(p);
+}
+
+static void destroy_graph(bfs_graph* g) {
+    if (!g) return;
+    cudaDeviceSynchronize();
+    single_release(g);
+    multi_release(g);
+    if (g->dcsc.built) {
+        g->mem.release(g->dcsc.tile_ptr, 0, nullptr);
+        g->mem.release(g->dcsc.jc, 0, nullptr);
+        g->mem.release(g->dcsc.cp, 0, nullptr);
+        g->mem.release(g->dcsc.ir, 0, nullptr);
+    }
+    g->mem.release(g->offsets, sizeof(int64_t) * (size_t)(g->n + 1), nullptr);
+    g->mem.release(g->cols, sizeof(int32_t) * (size_t)(g->nnz + kColPad), nullptr);
+    g->mem.release(g->isolated, sizeof(uint32_t) * (size_t)g->W, nullptr);
+    if (g->last_done) cudaEventDestroy(g->last_done);
+    delete g;
+}
+
+static bfs_status new_graph(int64_t n, const bfs_allocator* alloc, bfs_graph** out) {
+    if (!out) return fail(BFS_ERR_INVALID, "out handle pointer is NULL");
+    *out = nullptr;
+    if (n < 1 || n > 2147483647LL) return fail(BFS_ERR_INVALID, "n must lie in [1, 2^31-1]");
+    bfs_graph* g = new (std::nothrow) bfs_graph();
+    if (!g) return fail(BFS_ERR_OOM, "host allocation of the graph handle");
+    g->n = n;
+    g->W = (n + 31) / 32;
+    if (alloc && alloc->alloc && alloc->free) {
+        g->mem.hook = *alloc;
+        g->mem.has_hook = true;
+    }
+    cudaError_t e = cudaGetDevice(&g->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, g->device);
+    int coop = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, g->device);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->last_done, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        delete g;
+        return cuda_fail(e, "device query");
+    }
+    if (!coop) {
+        destroy_graph(g);
+        return fail(BFS_ERR_UNSUPPORTED, "device does not support cooperative launches");
+    }
+    *out = g;
+    return BFS_OK;
+}
+
+static bfs_status check_options(const bfs_options* in, bfs_options* out, const bfs_graph* g, bool need_level_for_min,
+                                const int32_t* level) {
+    bfs_options_default(out);
+    if (in) *out = *in;
+    if (out->mode < 0 || out->mode > 3) return fail(BFS_ERR_INVALID, "options.mode must be a BFS_MODE_* value");
+    if (out->layout != BFS_LAYOUT_CSR && out->layout != BFS_LAYOUT_DCSC_TILED)
+        return fail(BFS_ERR_INVALID, "options.layout must be a BFS_LAYOUT_* value");
+    if (out->layout == BFS_LAYOUT_DCSC_TILED && !g->dcsc.built)
+        return fail(BFS_ERR_UNSUPPORTED, "DCSC layout requested but the graph was built without BFS_FLAG_BUILD_DCSC");
+    if (out->alpha < 1 || out->beta < 1) return fail(BFS_ERR_INVALID, "options.alpha and options.beta must be >= 1");
+    if (out->parent_mode != BFS_PARENT_ANY && out->parent_mode != BFS_PARENT_MIN_ID)
+        return fail(BFS_ERR_INVALID, "options.parent_mode must be a BFS_PARENT_* value");
+    if (need_level_for_min && out->parent_mode == BFS_PARENT_MIN_ID && !level)
+        return fail(BFS_ERR_INVALID, "BFS_PARENT_MIN_ID needs a level output");
+    if (out->timeout_ms < 0) return fail(BFS_ERR_INVALID, "options.timeout_ms must be >= 0");
+    if (out->td_big_degree != 0 && out->td_big_degree < 64) out->td_big_degree = 64;
+    if (out->debug_barrier_extra < 0) return fail(BFS_ERR_INVALID, "options.debug_barrier_extra must be >= 0");
+    return BFS_OK;
+}
+
+// Order this run after the previous one on the same graph (shared buffers).
+static bfs_status order_after_previous(bfs_graph* g, cudaStream_t s) {
+    if (g->has_last && g->last_stream != s) BFS_CUDA_TRY(cudaStreamWaitEvent(s, g->last_done, 0));
+    return BFS_OK;
+}
+
+static bfs_status mark_done(bfs_graph* g, cudaStream_t s) {
+    BFS_CUDA_TRY(cudaEventRecord(g->last_done, s));
+    g->has_last = true;
+    g->last_stream = s;
+    return BFS_OK;
+}
+
+}  // namespace bfsrt
+
+using namespace bfsrt;
+
+extern "C" {
+
+void bfs_options_default(bfs_options* opt) {
+    if (!opt) return;
+    memset(opt, 0, sizeof(*opt));
+    opt->mode = BFS_MODE_DO;
+    opt->layout = BFS_LAYOUT_CSR;
+    opt->alpha = 14;
+    opt->beta = 24;
+    opt->parent_mode = BFS_PARENT_ANY;
+    opt->td_big_degree = 0;
+    opt->timeout_ms = 10000;
+}
+
+bfs_status bfs_graph_create_from_edges(const int32_t* src, const int32_t* dst, int64_t n_edges, int64_t n_vertices,
+                                       uint32_t flags, const bfs_allocator* alloc, void* stream, bfs_graph** out) {
+    if (out) *out = nullptr;
+    if (n_edges < 0) return fail(BFS_ERR_INVALID, "n_edges must be >= 0");
+    if (n_edges > 0 && (!src || !dst)) return fail(BFS_ERR_INVALID, "src/dst must not be NULL");
+    if (!(flags & BFS_FLAG_SYMMETRIZE))
+        return fail(BFS_ERR_UNSUPPORTED, "only undirected graphs are supported: pass BFS_FLAG_SYMMETRIZE");
+    bfs_graph* g = nullptr;
+    bfs_status st = new_graph(n_vertices, alloc, &g);
+    if (st != BFS_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    st = build_csr_from_edges(g, src, dst, n_edges, (flags & BFS_FLAG_DEVICE_PTRS) != 0, s);
+    if (st == BFS_OK && (flags & BFS_FLAG_BUILD_DCSC)) st = build_dcsc_tiles(g, s);
+    if (st != BFS_OK) {
+        std::string msg = bfs_last_error();
+        destroy_graph(g);
+        set_error(msg);
+        return st;
+    }
+    *out = g;
+    return BFS_OK;
+}
+
+bfs_status bfs_graph_create_from_csr(const int64_t* row_offsets, const int32_t* col_ids, int64_t n, int64_t nnz,
+                                     uint32_t flags, const bfs_allocator* alloc, void* stream, bfs_graph** out) {
+    if (out) *out = nullptr;
+    if (!row_offsets) return fail(BFS_ERR_INVALID, "row_offsets must not be NULL");
+    if (nnz < 0) return fail(BFS_ERR_INVALID, "nnz must be >= 0");
+    if (nnz > 0 && !col_ids) return fail(BFS_ERR_INVALID, "col_ids must not be NULL");
+    bfs_graph* g = nullptr;
+    bfs_status st = new_graph(n, alloc, &g);
+    if (st != BFS_OK) return st;
+    g->nnz = nnz;
+    cudaStream_t s = (cudaStream_t)stream;
+    st = build_csr_from_csr(g, row_offsets, col_ids, (flags & BFS_FLAG_DEVICE_PTRS) != 0,
+                            (flags & BFS_FLAG_CHECK_SYMMETRY) != 0, s);
+    if (st == BFS_OK && (flags & BFS_FLAG_BUILD_DCSC)) st = build_dcsc_tiles(g, s);
+    if (st != BFS_OK) {
+        std::string msg = bfs_last_error();
+        destroy_graph(g);
+        set_error(msg);
+        return st;
+    }
+    *out = g;
+    return BFS_OK;
+}
+
+bfs_status bfs_graph_info(const bfs_graph* g, int64_t* n, int64_t* nnz, int64_t* device_bytes) {
+    if (!g) return fail(BFS_ERR_INVALID, "graph handle is NULL");
+    if (n) *n = g->n;
+    if (nnz) *nnz = g->nnz;
+    if (device_bytes)
+        *device_bytes = (int64_t)(g->graph_bytes + g->single.bytes + g->multi.bytes + g->dcsc.bytes);
+    return BFS_OK;
+}
+
+bfs_status bfs_graph_csr(const bfs_graph* g, const int64_t** row_offsets, const int32_t** col_ids) {
+    if (!g) return fail(BFS_ERR_INVALID, "graph handle is NULL");
+    if (row_offsets) *row_offsets = g->offsets;
+    if (col_ids) *col_ids = g->cols;
+    return BFS_OK;
+}
+
+bfs_status bfs_graph_copy_csr(const bfs_graph* g, int64_t* offsets_out, int32_t* cols_out, void* stream) {
+    if (!g) return fail(BFS_ERR_INVALID, "graph handle is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (offsets_out)
+        BFS_CUDA_TRY(cudaMemcpyAsync(offsets_out, g->offsets, sizeof(int64_t) * (size_t)(g->n + 1), cudaMemcpyDefault, s));
+    if (cols_out && g->nnz > 0)
+        BFS_CUDA_TRY(cudaMemcpyAsync(cols_out, g->cols, sizeof(int32_t) * (size_t)g->nnz, cudaMemcpyDefault, s));
+    BFS_CUDA_TRY(cudaStreamSynchronize(s));
+    return BFS_OK;
+}
+
+bfs_status bfs_graph_dcsc(const bfs_graph* g, bfs_dcsc_layout* out) {
+    if (!g || !out) return fail(BFS_ERR_INVALID, "NULL argument");
+    if (!g->dcsc.built) return fail(BFS_ERR_INVALID, "graph was built without BFS_FLAG_BUILD_DCSC");
+    out->num_blocks = g->dcsc.num_blocks;
+    out->block_shift = g->dcsc.block_shift;
+    out->tile_ptr = g->dcsc.tile_ptr;
+    out->jc = g->dcsc.jc;
+    out->cp = g->dcsc.cp;
+    out->ir = g->dcsc.ir;
+    out->total_rows = g->dcsc.total_rows;
+    return BFS_OK;
+}
+
+void bfs_graph_destroy(bfs_graph* g) { destroy_graph(g); }
+
+static bfs_status run_common(bfs_graph* g, const int32_t* roots, int32_t k, int32_t* parent_dev, int32_t* level_dev,
+                             const bfs_options* opt, void* stream, bfs_stats* stats) {
+    if (!g) return fail(BFS_ERR_INVALID, "graph handle is NULL");
+    bfs_options o;
+    bfs_status st = check_options(opt, &o, g, true, level_dev);
+    if (st != BFS_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(g->run_mu);
+    st = order_after_previous(g, s);
+    if (st != BFS_OK) return st;
+    st = single_prepare(g, s);
+    if (st != BFS_OK) return st;
+    if (o.layout == BFS_LAYOUT_DCSC_TILED) return fail(BFS_ERR_UNSUPPORTED, "DCSC layout not available for bfs_run");
+    st = single_launch(g, roots, k, parent_dev, level_dev, o, s);
+    if (st != BFS_OK) return st;
+    st = mark_done(g, s);
+    if (st != BFS_OK) return st;
+    if (stats) return single_collect(g, s, stats);
+    return BFS_OK;
+}
+
+bfs_status bfs_run(bfs_graph* g, int32_t root, int32_t* parent_dev, int32_t* level_dev, const bfs_options* opt,
+                   void* stream, bfs_stats* stats) {
+    if (!g) return fail(BFS_ERR_INVALID, "graph handle is NULL");
+    if (root < 0 || (int64_t)root >= g->n) return fail(BFS_ERR_INVALID, "root outside [0, n)");
+    return run_common(g, &root, 1, parent_dev, level_dev, opt, stream, stats);
+}
+
+bfs_status bfs_run_multiroot(bfs_graph* g, const int32_t* roots_host, int32_t k, int32_t* parent_dev,
+                             int32_t* level_dev, const bfs_options* opt, void* stream, bfs_stats* stats) {
+    if (!g) return fail(BFS_ERR_INVALID, "graph handle is NULL");
+    if (!roots_host || k < 1 || (int64_t)k > g->n) return fail(BFS_ERR_INVALID, "need 1 <= k <= n roots");
+    std::vector<int32_t> r(roots_host, roots_host + k);
+    for (int32_t x : r)
+        if (x < 0 || (int64_t)x >= g->n) return fail(BFS_ERR_INVALID, "a root lies outside [0, n)");
+    std::sort(r.begin(), r.end());
+    r.erase(std::unique(r.begin(), r.end()), r.end());
+    return run_common(g, r.data(), (int32_t)r.size(), parent_dev, level_dev, opt, stream, stats);
+}
+
+bfs_status bfs_run_multi(bfs_graph* g, const int32_t* roots_host, int32_t k, int32_t* level_dev, int32_t* parent_dev,
+                         const bfs_options* opt, void* stream) {
+    if (!g) return fail(BFS_ERR_INVALID, "graph handle is NULL");
+    if (!roots_host || k < 1) return fail(BFS_ERR_INVALID, "need k >= 1 roots");
+    if (!level_dev) return fail(BFS_ERR_INVALID, "level_dev must not be NULL");
+    for (int32_t i = 0; i < k; i++)
+        if (roots_host[i] < 0 || (int64_t)roots_host[i] >= g->n) return fail(BFS_ERR_INVALID, "a root lies outside [0, n)");
+    bfs_options o;
+    bfs_status st = check_options(opt, &o, g, false, level_dev);
+    if (st != BFS_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(g->run_mu);
+    st = order_after_previous(g, s);
+    if (st != BFS_OK) return st;
+    st = multi_prepare(g, s);
+    if (st != BFS_OK) return st;
+    st = multi_launch(g, roots_host, k, level_dev, parent_dev, o, s);
+    if (st != BFS_OK) return st;
+    return mark_done(g, s);
+}
+
+bfs_status bfs_graph_sync(bfs_graph* g, void* stream) {
+    if (!g) return fail(BFS_ERR_INVALID, "graph handle is NULL");
+    std::lock_guard<std::mutex> lk(g->run_mu);
+    cudaStream_t s = (cudaStream_t)stream;
+    BFS_CUDA_TRY(cudaStreamSynchronize(s));
+    if (g->last_done) BFS_CUDA_TRY(cudaEventSynchronize(g->last_done));
+    if (g->single.ready) {
+        bfs_status st = single_collect(g, s, nullptr);
+        if (st != BFS_OK) return st;
+    }
+    if (g->multi.ready) return multi_collect_status(g, s);
+    return BFS_OK;
+}
+
+const char* bfs_status_string(bfs_status st) {
+    switch (st) {
+        case BFS_OK: return "BFS_OK";
+        case BFS_ERR_INVALID: return "BFS_ERR_INVALID";
+        case BFS_ERR_OOM: return "BFS_ERR_OOM";
+        case BFS_ERR_CUDA: return "BFS_ERR_CUDA";
+        case BFS_ERR_TIMEOUT: return "BFS_ERR_TIMEOUT";
+        case BFS_ERR_BUSY: return "BFS_ERR_BUSY";
+        case BFS_ERR_NOT_READY: return "BFS_ERR_NOT_READY";
+        case BFS_ERR_UNSUPPORTED: return "BFS_ERR_UNSUPPORTED";
+    }
+    return "BFS_ERR_UNKNOWN";
+}
+
+const char* bfs_last_error(void) { return t_last_error.c_str(); }
+
+const char* bfs_version(void) { return "gb300-dobfs 0.1 (sm_103a)"; }
+
+}  // extern "C"

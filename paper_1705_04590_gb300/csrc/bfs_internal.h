@@ -1,0 +1,135 @@
+// bfs_internal.h -- host-side structures shared by the library's translation
+// units (not part of the public ABI; see include/bfs.h for that).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <mutex>
+#include <string>
+
+#include "../../include/bfs.h"
+
+namespace bfsrt {
+
+// thread-local last error message + helpers (bfs_api.cpp)
+void set_error(const std::string& msg);
+bfs_status fail(bfs_status st, const std::string& msg);
+bfs_status cuda_fail(cudaError_t e, const char* what);
+
+#define BFS_CUDA_TRY(expr)                                     \
+    do {                                                       \
+        cudaError_t e__ = (expr);                              \
+        if (e__ != cudaSuccess) return bfsrt::cuda_fail(e__, #expr); \
+    } while (0)
+
+// Device memory through the user hook or cudaMalloc.
+struct DeviceAlloc {
+    bfs_allocator hook{};
+    bool has_hook = false;
+    void* alloc(size_t bytes, cudaStream_t s);
+    void release(void* p, size_t bytes, cudaStream_t s);
+};
+
+// Per-graph buffers of the single-source search, reused by every run.
+struct SingleWork {
+    bool ready = false;
+    unsigned* visited = nullptr;   // [W]
+    unsigned* front0 = nullptr;    // [W]
+    unsigned* front1 = nullptr;    // [W]
+    int* queue0 = nullptr;         // [n]
+    int* queue1 = nullptr;         // [n]
+    void* tasks = nullptr;         // top-down edge-chunk descriptors
+    long long task_cap = 0;
+    void* ctrl = nullptr;          // bfsk::Ctrl
+    bfs_level_record* records = nullptr;  // [rec_cap] device
+    int rec_cap = 0;
+    int* roots_dev = nullptr;      // [n] staging for multi-root seeds
+    int* roots_pinned = nullptr;   // host pinned staging
+    long long roots_cap = 0;
+    size_t bytes = 0;
+    int grid = 0, block = 0;       // cooperative launch shape
+};
+
+struct MultiWork {
+    bool ready = false;
+    unsigned long long* seen = nullptr;
+    unsigned long long* front = nullptr;
+    unsigned long long* next = nullptr;
+    void* ctrl = nullptr;
+    int* roots_dev = nullptr;      // [64]
+    int* roots_pinned = nullptr;
+    size_t bytes = 0;
+    int grid = 0, block = 0;
+};
+
+struct DcscTiles {
+    bool built = false;
+    int num_blocks = 0;
+    int block_shift = 0;
+    int64_t* tile_ptr = nullptr;   // [num_blocks+1]
+    int32_t* jc = nullptr;         // [total_rows]
+    int64_t* cp = nullptr;         // [total_rows + num_blocks]
+    int32_t* ir = nullptr;         // [nnz + pad]
+    int64_t total_rows = 0;
+    size_t bytes = 0;
+};
+
+}  // namespace bfsrt
+
+struct bfs_graph {
+    int64_t n = 0;
+    int64_t nnz = 0;
+    int device = 0;
+    int64_t* offsets = nullptr;     // [n+1]
+    int32_t* cols = nullptr;        // [nnz + kColPad]
+    uint32_t* isolated = nullptr;   // [W] bit v set when deg(v) = 0 or v >= n
+    int64_t W = 0;                  // bitmap words
+    size_t graph_bytes = 0;
+    bfsrt::DeviceAlloc mem;
+    bfsrt::SingleWork single;
+    bfsrt::MultiWork multi;
+    bfsrt::DcscTiles dcsc;
+    std::mutex run_mu;              // serialises runs on the shared work buffers
+    cudaEvent_t last_done = nullptr;   // completion of the last enqueued run
+    cudaStream_t last_stream = nullptr;
+    bool has_last = false;
+    unsigned run_counter = 0;
+    int sm_count = 0;
+};
+
+namespace bfsrt {
+
+constexpr int64_t kColPad = 32;  // readable slack after col_ids (vector loads past the last row)
+
+// graph_build.cu
+bfs_status build_csr_from_edges(bfs_graph* g, const int32_t* src, const int32_t* dst, int64_t m,
+                                bool device_ptrs, cudaStream_t s);
+bfs_status build_csr_from_csr(bfs_graph* g, const int64_t* off, const int32_t* cols, bool device_ptrs,
+                              bool check_symmetry, cudaStream_t s);
+bfs_status build_isolated_bitmap(bfs_graph* g, cudaStream_t s);
+bfs_status build_dcsc_tiles(bfs_graph* g, cudaStream_t s);
+
+// bfs_single.cu
+bfs_status single_prepare(bfs_graph* g, cudaStream_t s);
+bfs_status single_launch(bfs_graph* g, const int32_t* roots_host, int32_t k, int32_t* parent,
+                         int32_t* level, const bfs_options& opt, cudaStream_t s);
+bfs_status single_collect(bfs_graph* g, cudaStream_t s, bfs_stats* stats);
+void single_release(bfs_graph* g);
+
+// bfs_multi.cu
+bfs_status multi_prepare(bfs_graph* g, cudaStream_t s);
+bfs_status multi_launch(bfs_graph* g, const int32_t* roots_host, int32_t k, int32_t* level,
+                        int32_t* parent, const bfs_options& opt, cudaStream_t s);
+bfs_status multi_collect_status(bfs_graph* g, cudaStream_t s);
+void multi_release(bfs_graph* g);
+
+// lane-slot stepping for the server (bfs_multi.cu)
+struct LaneJob {
+    int32_t root;
+    int32_t start_iter;  // iteration at which the lane was seeded
+    int32_t* level_dev;  // [n] output row
+};
+
+}  // namespace bfsrt

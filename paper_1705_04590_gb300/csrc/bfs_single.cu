@@ -1,0 +1,659 @@
+// bfs_single.cu -- single-source (and multi-root) direction-optimizing BFS as
+// one persistent cooperative launch per search.
+//
+// The level loop of Algorithm 1/2 runs entirely on the device: every CTA
+// evaluates the direction rule of "Parallel Direction-Optimizing BFS" from
+// the same device counters, does its share of the level, and meets the
+// others at a bounded grid barrier.  No host round trip happens per level.
+//
+// Level d (frontier F_d, n_f = |F_d|, m_f = sum of degrees over F_d, m_u =
+// degree sum of the vertices not yet reached):
+//   direction: top-down -> bottom-up when m_f * alpha > m_u,
+//              bottom-up -> top-down when n_f * beta < n.
+//   top-down  (Algorithm 1 inner loops; the local discovery of Algorithm 3):
+//              for u in the queue, for v in adj(u): claim v by an atomicOr on
+//              the visited bitmap; the winner writes parent/level and appends
+//              v to the next queue (warp ballot + one atomicAdd per warp).
+//              Frontier vertices of degree > big_deg are cut into edge chunks
+//              that all warps share after a barrier (load balance on R-MAT
+//              hubs); the rest are gathered warp-cooperatively (a warp prefix
+//              sum over its 32 vertices' degrees maps lanes onto edges).
+//   bottom-up (Algorithm 2 inner loops; the local search of Algorithm 4):
+//              a warp owns 32 consecutive vertices (one word of the
+//              completed bitmap c); each unvisited lane scans its sorted row
+//              in 16-byte (int4) pieces, testing frontier-bitmap bits, and
+//              stops at the first hit; long rows continue warp-cooperatively.
+//              Found vertices are written to the next-frontier bitmap as one
+//              ballot word per warp (no atomics: the warp owns the word).
+//   conversion: queue -> bitmap before a bottom-up level that follows a
+//              top-down one, bitmap -> queue (popcount + warp scan) before a
+//              top-down level that follows a bottom-up one.
+// Membership tests read only the current frontier; next is separate and
+// swapped in after the level (the reading of Algorithm 2 that keeps levels
+// exact).
+#include <cstdio>
+
+#include "bfs_common.cuh"
+#include "bfs_internal.h"
+
+namespace bfsk {
+
+constexpr int kBlock = 512;
+constexpr int kChunk = 1024;   // edges per top-down chunk task
+constexpr int kLongRem = 32;   // bottom-up: rows with more ids left than this go warp-cooperative
+constexpr int kWPW = 2;        // bottom-up: bitmap words (32 vertices each) per warp iteration
+constexpr unsigned kFull = 0xffffffffu;
+
+struct Task {
+    long long start;
+    int len;
+    int u;
+};
+
+struct SingleParams {
+    const long long* __restrict__ off;
+    const int* __restrict__ cols;
+    const unsigned* __restrict__ isolated;
+    long long n, nnz, W;
+    int* parent;
+    int* level;
+    unsigned* visited;
+    unsigned* front0;
+    unsigned* front1;
+    int* queue0;
+    int* queue1;
+    Task* tasks;
+    long long task_cap;
+    Ctrl* ctrl;
+    bfs_level_record* rec;
+    int rec_cap;
+    int root0;     // the root when nroots == 1
+    int nroots;    // > 1: roots already copied into queue0[0..nroots)
+    int mode, alpha, beta, parent_mode, big_deg;
+    unsigned long long seed;
+    unsigned long long timeout_ns;
+    unsigned expected;
+};
+
+constexpr int TD = 0, BU = 1;
+
+__device__ __forceinline__ int decide_dir(const SingleParams& p, int prev, long long nf, long long mf,
+                                          long long mu, int d) {
+    switch (p.mode) {
+        case BFS_MODE_TD_ONLY: return TD;
+        case BFS_MODE_BU_ONLY: return BU;
+        case BFS_MODE_RANDOM:
+            return (int)(mix64(p.seed + 0x9E3779B97F4A7C15ULL * (unsigned long long)(d + 1)) >> 63);
+        default:
+            if (prev == TD) return (mf * (long long)p.alpha > mu) ? BU : TD;
+            return (nf * (long long)p.beta < p.n) ? TD : BU;
+    }
+}
+
+__device__ __forceinline__ long long gtid() { return (long long)blockIdx.x * blockDim.x + threadIdx.x; }
+__device__ __forceinline__ long long gthreads() { return (long long)gridDim.x * blockDim.x; }
+
+// parent/level fill, completed bitmap = isolated vertices (+ root), clear both
+// frontier bitmaps.
+__device__ void init_phase(const SingleParams& p) {
+    const long long tid = gtid(), nth = gthreads();
+    const bool single = p.nroots == 1;
+    const long long r = p.root0;
+    if (p.parent || p.level) {
+        for (long long v = tid; v < p.n; v += nth) {
+            const bool isr = single && v == r;
+            if (p.parent) p.parent[v] = isr ? (int)r : -1;
+            if (p.level) p.level[v] = isr ? 0 : -1;
+        }
+    }
+    const long long rw = single ? (r >> 5) : -1;
+    const unsigned rb = single ? (1u << (r & 31)) : 0u;
+    for (long long w = tid; w < p.W; w += nth) {
+        unsigned x = __ldg(p.isolated + w);
+        if (w == rw) x |= rb;
+        p.visited[w] = x;
+        p.front0[w] = 0u;
+        p.front1[w] = 0u;
+    }
+    if (single && tid == 0) {
+        p.queue0[0] = (int)r;
+        p.ctrl->tail[0] = 1ull;
+        p.ctrl->accm[0] = (unsigned long long)(__ldg(p.off + r + 1) - __ldg(p.off + r));
+    }
+}
+
+// multi-root seeding (after the fill): roots already sit in queue0.
+__device__ void seed_roots_phase(const SingleParams& p) {
+    const long long tid = gtid(), nth = gthreads();
+    unsigned long long m = 0;
+    for (long long i = tid; i < p.nroots; i += nth) {
+        const int r = __ldcg(p.queue0 + i);
+        atomicOr(p.visited + (r >> 5), 1u << (r & 31));
+        if (p.parent) p.parent[r] = r;
+        if (p.level) p.level[r] = 0;
+        m += (unsigned long long)(__ldg(p.off + r + 1) - __ldg(p.off + r));
+    }
+    block_add4(m, 0, 0, 0, &p.ctrl->accm[0], nullptr, nullptr, nullptr);
+    if (tid == 0) p.ctrl->tail[0] = (unsigned long long)p.nroots;
+}
+
+// ------------------------------------------------------------------ top-down
+
+// Visit edge (u, v) for the whole warp (every lane calls; `act` masks).
+__device__ __forceinline__ void td_visit(const SingleParams& p, int d, int u, int v, bool act, int* qnext,
+                                         unsigned long long* tail, unsigned long long& acc_m) {
+    bool claimed = false;
+    if (act) {
+        const unsigned bit = 1u << (v & 31);
+        unsigned* wp = p.visited + (v >> 5);
+        if (!(__ldcg(wp) & bit)) claimed = !(atomicOr(wp, bit) & bit);
+    }
+    const unsigned cm = __ballot_sync(kFull, claimed);
+    if (cm) {
+        const int leader = __ffs(cm) - 1;
+        unsigned long long base = 0;
+        if (lane_id() == leader) base = atomicAdd(tail, (unsigned long long)__popc(cm));
+        base = __shfl_sync(kFull, base, leader);
+        if (claimed) {
+            qnext[base + __popc(cm & lanemask_lt())] = v;
+            if (p.parent) p.parent[v] = u;
+            if (p.level) p.level[v] = d + 1;
+            acc_m += (unsigned long long)(__ldg(p.off + v + 1) - __ldg(p.off + v));
+        }
+    }
+}
+
+__device__ void td_phase(const SingleParams& p, int d, const int* qcur, long long nf, int* qnext, int snext,
+                         unsigned long long& acc_m) {
+    const int lane = lane_id();
+    const long long gw = gtid() >> 5, nw = gthreads() >> 5;
+    unsigned long long* tail = &p.ctrl->tail[snext];
+    for (long long base = gw * 32; base < nf; base += nw * 32) {
+        const long long i = base + lane;
+        int u = 0;
+        long long s = 0, e = 0;
+        if (i < nf) {
+            u = __ldcg(qcur + i);
+            s = __ldg(p.off + u);
+            e = __ldg(p.off + u + 1);
+        }
+        const long long deg = e - s;
+        int mydeg = 0;
+        if (deg > p.big_deg) {
+            const long long nch = (deg + kChunk - 1) / kChunk;
+            const unsigned long long t0 = atomicAdd(&p.ctrl->ntask[snext], (unsigned long long)nch);
+            for (long long c = 0; c < nch; c++) {
+                const long long ti = (long long)t0 + c;
+                if (ti < p.task_cap) {
+                    Task t;
+                    t.start = s + c * kChunk;
+                    t.len = (int)min((long long)kChunk, e - t.start);
+                    t.u = u;
+                    p.tasks[ti] = t;
+                } else {
+                    atomicMax(&p.ctrl->status, kDevOverflow);
+                }
+            }
+        } else {
+            mydeg = (int)deg;
+        }
+        const int incl = warp_inclusive_scan(mydeg);
+        const int total = __shfl_sync(kFull, incl, 31);
+        const int excl = incl - mydeg;
+        for (int k0 = 0; k0 < total; k0 += 32) {
+            const int k = k0 + lane;
+            int j = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+                const int c = __shfl_sync(kFull, incl, j + step - 1);
+                if (c <= k) j += step;
+            }
+            const long long sj = __shfl_sync(kFull, s, j);
+            const int exj = __shfl_sync(kFull, excl, j);
+            const int uj = __shfl_sync(kFull, u, j);
+            const bool act = k < total;
+            const int v = act ? __ldg(p.cols + sj + (k - exj)) : 0;
+            td_visit(p, d, uj, v, act, qnext, tail, acc_m);
+        }
+    }
+}
+
+__device__ void task_phase(const SingleParams& p, int d, long long ntask, int* qnext, int snext,
+                           unsigned long long& acc_m) {
+    const int lane = lane_id();
+    const long long gw = gtid() >> 5, nw = gthreads() >> 5;
+    unsigned long long* tail = &p.ctrl->tail[snext];
+    const long long nt = ntask < p.task_cap ? ntask : p.task_cap;
+    for (long long t = gw; t < nt; t += nw) {
+        const int4 raw = __ldcg(reinterpret_cast<const int4*>(p.tasks + t));
+        const long long start = (long long)(unsigned)raw.x | ((long long)raw.y << 32);
+        const int len = raw.z, u = raw.w;
+        for (int k0 = 0; k0 < len; k0 += 32) {
+            const int k = k0 + lane;
+            const bool act = k < len;
+            const int v = act ? __ldg(p.cols + start + k) : 0;
+            td_visit(p, d, u, v, act, qnext, tail, acc_m);
+        }
+    }
+}
+
+// parent_mode MIN_ID after a top-down level: each newly found v takes the
+// smallest neighbour on level d (rows are sorted, so the first one found).
+__device__ void td_min_parent(const SingleParams& p, int d, const int* qnext, long long nn) {
+    const long long tid = gtid(), nth = gthreads();
+    for (long long i = tid; i < nn; i += nth) {
+        const int v = __ldcg(qnext + i);
+        const long long s = __ldg(p.off + v), e = __ldg(p.off + v + 1);
+        for (long long k = s; k < e; k++) {
+            const int u = __ldg(p.cols + k);
+            if (__ldcg(p.level + u) == d) {
+                p.parent[v] = u;
+                break;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ conversions
+
+__device__ void queue_to_bitmap(const SingleParams& p, const int* q, long long nf, unsigned* f) {
+    const long long tid = gtid(), nth = gthreads();
+    for (long long i = tid; i < nf; i += nth) {
+        const int v = __ldcg(q + i);
+        atomicOr(f + (v >> 5), 1u << (v & 31));
+    }
+}
+
+// Read-and-clear `f` into queue q (cursor *tail), clear `other` too, so both
+// frontier bitmaps are zero for a later queue -> bitmap conversion.
+__device__ void bitmap_to_queue(const SingleParams& p, unsigned* f, unsigned* other, int* q,
+                                unsigned long long* tail) {
+    const int lane = lane_id();
+    const long long nth = gthreads();
+    for (long long base = gtid() - lane; base < p.W; base += nth) {
+        const long long w = base + lane;
+        unsigned x = 0;
+        if (w < p.W) {
+            x = __ldcg(f + w);
+            f[w] = 0u;
+            other[w] = 0u;
+        }
+        const int cnt = __popc(x);
+        const int incl = warp_inclusive_scan(cnt);
+        const int tot = __shfl_sync(kFull, incl, 31);
+        unsigned long long b = 0;
+        if (lane == 31 && tot) b = atomicAdd(tail, (unsigned long long)tot);
+        b = __shfl_sync(kFull, b, 31);
+        long long pos = (long long)b + incl - cnt;
+        while (x) {
+            const int bit = __ffs(x) - 1;
+            x &= x - 1;
+            q[pos++] = (int)(w * 32 + bit);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ bottom-up
+
+__device__ __forceinline__ bool in_frontier(const unsigned* f, int v) {
+    return (__ldcg(f + (v >> 5)) >> (v & 31)) & 1u;
+}
+
+__device__ void bu_phase(const SingleParams& p, int d, const unsigned* fcur, unsigned* fnext,
+                         unsigned long long& acc_n, unsigned long long& acc_m, unsigned long long& acc_sc,
+                         unsigned long long& acc_ex) {
+    const int lane = lane_id();
+    const long long gw = gtid() >> 5, nw = gthreads() >> 5;
+    for (long long w0 = gw * kWPW; w0 < p.W; w0 += nw * kWPW) {
+        unsigned cw[kWPW];
+        long long base[kWPW];   // row start rounded down to 4 ids (16 bytes)
+        int lead[kWPW];         // s - base (0..3)
+        int len[kWPW];          // degree (0 when visited / not searching)
+        int nxt[kWPW];          // next unread position, relative to base
+        int hit[kWPW];          // position of the first frontier neighbour relative to s, or -1
+        int pv[kWPW];
+#pragma unroll
+        for (int j = 0; j < kWPW; j++) cw[j] = (w0 + j < p.W) ? __ldcg(p.visited + w0 + j) : kFull;
+#pragma unroll
+        for (int j = 0; j < kWPW; j++) {
+            base[j] = 0;
+            lead[j] = 0;
+            len[j] = 0;
+            nxt[j] = 0;
+            hit[j] = -1;
+            pv[j] = -1;
+            if (!((cw[j] >> lane) & 1u)) {
+                const long long u = (w0 + j) * 32 + lane;
+                const long long s = __ldg(p.off + u);
+                len[j] = (int)(__ldg(p.off + u + 1) - s);
+                base[j] = s & ~3LL;
+                lead[j] = (int)(s - base[j]);
+                nxt[j] = 0;
+            }
+        }
+        // thread-wise rounds of 8 ids (two int4 loads, eight bitmap probes in flight)
+        for (int r = 0;; r++) {
+            bool need[kWPW];
+            int4 xa[kWPW], xb[kWPW];
+            bool any = false;
+#pragma unroll
+            for (int j = 0; j < kWPW; j++) {
+                const int endrel = lead[j] + len[j];
+                need[j] = len[j] > 0 && hit[j] < 0 && nxt[j] < endrel && (r == 0 || endrel - nxt[j] <= kLongRem);
+                if (need[j]) {
+                    const int4* q = reinterpret_cast<const int4*>(p.cols + base[j] + nxt[j]);
+                    xa[j] = __ldg(q);
+                    xb[j] = (nxt[j] + 4 < endrel) ? __ldg(q + 1) : make_int4(0, 0, 0, 0);
+                    any = true;
+                }
+            }
+            if (!__any_sync(kFull, any)) break;
+#pragma unroll
+            for (int j = 0; j < kWPW; j++) {
+                if (need[j]) {
+                    const int ids[8] = {xa[j].x, xa[j].y, xa[j].z, xa[j].w, xb[j].x, xb[j].y, xb[j].z, xb[j].w};
+                    unsigned hb = 0;
+#pragma unroll
+                    for (int t = 0; t < 8; t++) {
+                        const int rel = nxt[j] + t;
+                        if (rel >= lead[j] && rel < lead[j] + len[j] && in_frontier(fcur, ids[t])) hb |= 1u << t;
+                    }
+                    if (hb) {
+                        const int t = __ffs(hb) - 1;
+                        hit[j] = nxt[j] + t - lead[j];
+                        pv[j] = ids[t];
+                    }
+                    nxt[j] += 8;
+                }
+            }
+        }
+        // warp-cooperative continuation of long rows, one vertex at a time
+#pragma unroll
+        for (int j = 0; j < kWPW; j++) {
+            unsigned pend = __ballot_sync(kFull, len[j] > 0 && hit[j] < 0 && nxt[j] < lead[j] + len[j]);
+            while (pend) {
+                const int L = __ffs(pend) - 1;
+                pend &= pend - 1;
+                const long long b = __shfl_sync(kFull, base[j], L);
+                const int from = __shfl_sync(kFull, nxt[j], L);
+                const int to = __shfl_sync(kFull, lead[j] + len[j], L);
+                const int ld = __shfl_sync(kFull, lead[j], L);
+                int fpos = -1, fv = -1;
+                for (int q0 = from; q0 < to; q0 += 32) {
+                    const int q = q0 + lane;
+                    int v = 0;
+                    bool h = false;
+                    if (q < to) {
+                        v = __ldg(p.cols + b + q);
+                        h = in_frontier(fcur, v);
+                    }
+                    const unsigned hm = __ballot_sync(kFull, h);
+                    if (hm) {
+                        const int f = __ffs(hm) - 1;
+                        fpos = q0 + f - ld;
+                        fv = __shfl_sync(kFull, v, f);
+                        break;
+                    }
+                }
+                if (lane == L) {
+                    hit[j] = fpos;
+                    pv[j] = fv;
+                }
+            }
+        }
+        // outputs: parent/level, next-frontier word, completed word, counters
+#pragma unroll
+        for (int j = 0; j < kWPW; j++) {
+            const long long w = w0 + j;
+            if (w >= p.W) break;
+            const bool act = len[j] > 0;
+            const bool found = act && hit[j] >= 0;
+            if (act) {
+                acc_sc += 1;
+                acc_ex += (unsigned long long)(found ? hit[j] + 1 : len[j]);
+            }
+            const unsigned fm = __ballot_sync(kFull, found);
+            if (found) {
+                const long long u = w * 32 + lane;
+                if (p.parent) p.parent[u] = pv[j];
+                if (p.level) p.level[u] = d + 1;
+                acc_m += (unsigned long long)len[j];
+            }
+            if (lane == 0) {
+                fnext[w] = fm;
+                if (fm) p.visited[w] = cw[j] | fm;
+                acc_n += (unsigned long long)__popc(fm);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ kernel
+
+__global__ void __launch_bounds__(kBlock, 2) bfs_single_kernel(SingleParams p) {
+    Ctrl* c = p.ctrl;
+    init_phase(p);
+    if (!grid_sync(c, p.expected, p.timeout_ns)) return;
+    if (p.nroots > 1) {
+        seed_roots_phase(p);
+        if (!grid_sync(c, p.expected, p.timeout_ns)) return;
+    }
+    long long nf = p.nroots;
+    long long mf = (long long)ld_acquire64(&c->accm[0]);
+    long long mu = p.nnz - mf;
+    long long reached = nf;
+    int prev = TD, qsel = 0, bsel = 0, d = 0;
+    const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+    while (true) {
+        const int dir = decide_dir(p, prev, nf, mf, mu, d);
+        const int scur = d % 3, snext = (d + 1) % 3, sfree = (d + 2) % 3;
+        if (lead) {
+            c->tail[sfree] = 0;
+            c->accn[sfree] = 0;
+            c->accm[sfree] = 0;
+            c->scanned[sfree] = 0;
+            c->examined[sfree] = 0;
+            c->ntask[sfree] = 0;
+        }
+        long long nf_next, scanned = 0, examined = mf;
+        int* qcur = qsel ? p.queue1 : p.queue0;
+        int* qnext = qsel ? p.queue0 : p.queue1;
+        unsigned* fcur = bsel ? p.front1 : p.front0;
+        unsigned* fnext = bsel ? p.front0 : p.front1;
+        if (dir == TD) {
+            if (prev == BU) {
+                bitmap_to_queue(p, fcur, fnext, qcur, &c->tail[scur]);
+                if (!grid_sync(c, p.expected, p.timeout_ns)) return;
+            }
+            unsigned long long am = 0;
+            td_phase(p, d, qcur, nf, qnext, snext, am);
+            block_add4(0, am, 0, 0, nullptr, &c->accm[snext], nullptr, nullptr);
+            if (!grid_sync(c, p.expected, p.timeout_ns)) return;
+            const long long nt = (long long)ld_acquire64(&c->ntask[snext]);
+            if (nt > 0) {
+                unsigned long long am2 = 0;
+                task_phase(p, d, nt, qnext, snext, am2);
+                block_add4(0, am2, 0, 0, nullptr, &c->accm[snext], nullptr, nullptr);
+                if (!grid_sync(c, p.expected, p.timeout_ns)) return;
+            }
+            nf_next = (long long)ld_acquire64(&c->tail[snext]);
+            if (p.parent_mode == BFS_PARENT_MIN_ID && p.parent && p.level) td_min_parent(p, d, qnext, nf_next);
+            qsel ^= 1;
+        } else {
+            if (prev == TD) {
+                queue_to_bitmap(p, qcur, nf, fcur);
+                if (!grid_sync(c, p.expected, p.timeout_ns)) return;
+            }
+            unsigned long long an = 0, am = 0, asc = 0, aex = 0;
+            bu_phase(p, d, fcur, fnext, an, am, asc, aex);
+            block_add4(an, am, asc, aex, &c->accn[snext], &c->accm[snext], &c->scanned[snext],
+                       &c->examined[snext]);
+            if (!grid_sync(c, p.expected, p.timeout_ns)) return;
+            nf_next = (long long)ld_acquire64(&c->accn[snext]);
+            scanned = (long long)ld_acquire64(&c->scanned[snext]);
+            examined = (long long)ld_acquire64(&c->examined[snext]);
+            bsel ^= 1;
+        }
+        const long long mf_next = (long long)ld_acquire64(&c->accm[snext]);
+        if (lead && d < p.rec_cap) {
+            bfs_level_record r;
+            r.dir = dir;
+            r.reserved = 0;
+            r.nf = nf;
+            r.mf = mf;
+            r.nnext = nf_next;
+            r.mnext = mf_next;
+            r.scanned = scanned;
+            r.examined = examined;
+            p.rec[d] = r;
+        }
+        if (nf_next == 0) break;
+        reached += nf_next;
+        mu -= mf_next;
+        nf = nf_next;
+        mf = mf_next;
+        prev = dir;
+        d++;
+    }
+    if (lead) {
+        c->num_levels = d + 1;
+        c->reached = reached;
+    }
+}
+
+}  // namespace bfsk
+
+// ====================================================================== host
+
+namespace bfsrt {
+
+using bfsk::Ctrl;
+using bfsk::SingleParams;
+using bfsk::Task;
+
+static int round_up_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+bfs_status single_prepare(bfs_graph* g, cudaStream_t s) {
+    SingleWork& w = g->single;
+    if (w.ready) return BFS_OK;
+    const long long n = g->n, W = g->W;
+    const long long task_cap = g->nnz / bfsk::kChunk + g->nnz / 64 + 1024;
+    const int rec_cap = 1 << 16;
+    struct Item { void** p; size_t bytes; };
+    Item items[] = {
+        {(void**)&w.visited, sizeof(unsigned) * (size_t)W},
+        {(void**)&w.front0, sizeof(unsigned) * (size_t)W},
+        {(void**)&w.front1, sizeof(unsigned) * (size_t)W},
+        {(void**)&w.queue0, sizeof(int) * (size_t)(n + 32)},
+        {(void**)&w.queue1, sizeof(int) * (size_t)(n + 32)},
+        {(void**)&w.tasks, sizeof(Task) * (size_t)task_cap},
+        {(void**)&w.ctrl, sizeof(Ctrl)},
+        {(void**)&w.records, sizeof(bfs_level_record) * (size_t)rec_cap},
+    };
+    size_t total = 0;
+    for (auto& it : items) {
+        *it.p = g->mem.alloc(it.bytes, s);
+        if (!*it.p) {
+            for (auto& jt : items)
+                if (*jt.p) { g->mem.release(*jt.p, jt.bytes, s); *jt.p = nullptr; }
+            return fail(BFS_ERR_OOM, "single-source work buffers: device allocation failed");
+        }
+        total += it.bytes;
+    }
+    w.task_cap = task_cap;
+    w.rec_cap = rec_cap;
+    w.bytes = total;
+    int nb = 0;
+    BFS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, bfsk::bfs_single_kernel, bfsk::kBlock, 0));
+    if (nb < 1) return fail(BFS_ERR_UNSUPPORTED, "BFS kernel cannot be resident on this device");
+    w.block = bfsk::kBlock;
+    w.grid = nb * g->sm_count;
+    BFS_CUDA_TRY(cudaMemsetAsync(w.ctrl, 0, sizeof(Ctrl), s));
+    w.ready = true;
+    return BFS_OK;
+}
+
+void single_release(bfs_graph* g) {
+    SingleWork& w = g->single;
+    if (!w.ready) return;
+    const long long n = g->n, W = g->W;
+    g->mem.release(w.visited, sizeof(unsigned) * (size_t)W, nullptr);
+    g->mem.release(w.front0, sizeof(unsigned) * (size_t)W, nullptr);
+    g->mem.release(w.front1, sizeof(unsigned) * (size_t)W, nullptr);
+    g->mem.release(w.queue0, sizeof(int) * (size_t)(n + 32), nullptr);
+    g->mem.release(w.queue1, sizeof(int) * (size_t)(n + 32), nullptr);
+    g->mem.release(w.tasks, sizeof(Task) * (size_t)w.task_cap, nullptr);
+    g->mem.release(w.ctrl, sizeof(Ctrl), nullptr);
+    g->mem.release(w.records, sizeof(bfs_level_record) * (size_t)w.rec_cap, nullptr);
+    w = SingleWork();
+}
+
+bfs_status single_launch(bfs_graph* g, const int32_t* roots_host, int32_t k, int32_t* parent,
+                         int32_t* level, const bfs_options& opt, cudaStream_t s) {
+    SingleWork& w = g->single;
+    SingleParams p;
+    p.off = reinterpret_cast<const long long*>(g->offsets);
+    p.cols = g->cols;
+    p.isolated = g->isolated;
+    p.n = g->n;
+    p.nnz = g->nnz;
+    p.W = g->W;
+    p.parent = parent;
+    p.level = level;
+    p.visited = w.visited;
+    p.front0 = w.front0;
+    p.front1 = w.front1;
+    p.queue0 = w.queue0;
+    p.queue1 = w.queue1;
+    p.tasks = reinterpret_cast<Task*>(w.tasks);
+    p.task_cap = w.task_cap;
+    p.ctrl = reinterpret_cast<Ctrl*>(w.ctrl);
+    p.rec = w.records;
+    p.rec_cap = w.rec_cap;
+    p.root0 = roots_host[0];
+    p.nroots = k;
+    p.mode = opt.mode;
+    p.alpha = opt.alpha;
+    p.beta = opt.beta;
+    p.parent_mode = opt.parent_mode;
+    p.big_deg = opt.td_big_degree > 0 ? opt.td_big_degree : 128;
+    p.seed = opt.seed;
+    p.timeout_ns = (unsigned long long)(opt.timeout_ms > 0 ? opt.timeout_ms : 10000) * 1000000ull;
+    p.expected = (unsigned)w.grid + (unsigned)(opt.debug_barrier_extra > 0 ? opt.debug_barrier_extra : 0);
+    BFS_CUDA_TRY(cudaMemsetAsync(w.ctrl, 0, sizeof(Ctrl), s));
+    if (k > 1) BFS_CUDA_TRY(cudaMemcpyAsync(w.queue0, roots_host, sizeof(int32_t) * (size_t)k, cudaMemcpyHostToDevice, s));
+    void* args[] = {&p};
+    BFS_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)bfsk::bfs_single_kernel, dim3(w.grid), dim3(w.block),
+                                             args, 0, s));
+    return BFS_OK;
+}
+
+bfs_status single_collect(bfs_graph* g, cudaStream_t s, bfs_stats* stats) {
+    SingleWork& w = g->single;
+    Ctrl c;
+    BFS_CUDA_TRY(cudaMemcpyAsync(&c, w.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+    BFS_CUDA_TRY(cudaStreamSynchronize(s));
+    if (c.status == bfsk::kDevTimeout)
+        return fail(BFS_ERR_TIMEOUT, "device grid barrier wait ran out of time; outputs are undefined");
+    if (c.status == bfsk::kDevOverflow)
+        return fail(BFS_ERR_CUDA, "top-down chunk task list overflowed (internal sizing error)");
+    if (stats) {
+        stats->num_levels = (int32_t)c.num_levels;
+        stats->vertices_reached = c.reached;
+        const int nrec = (int)std::min<long long>(c.num_levels, (long long)w.rec_cap);
+        const int ncopy = std::min(nrec, stats->levels_capacity);
+        stats->edges_examined = 0;
+        if (nrec > 0) {
+            bfs_level_record* tmp = new (std::nothrow) bfs_level_record[nrec];
+            if (!tmp) return fail(BFS_ERR_OOM, "host allocation for level records");
+            cudaError_t e = cudaMemcpy(tmp, w.records, sizeof(bfs_level_record) * (size_t)nrec, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) { delete[] tmp; return cuda_fail(e, "cudaMemcpy(level records)"); }
+            for (int i = 0; i < nrec; i++) stats->edges_examined += tmp[i].examined;
+            if (stats->levels && ncopy > 0) memcpy(stats->levels, tmp, sizeof(bfs_level_record) * (size_t)ncopy);
+            delete[] tmp;
+        }
+    }
+    return BFS_OK;
+}
+
+}  // namespace bfsrt

@@ -1,0 +1,282 @@
+// graph_build.cu -- device-side graph construction (off the timed path).
+//
+// "Graph Representation": adjacencies of each vertex sorted and stored
+// contiguously, every undirected edge stored in both rows, an n+1 row
+// pointer array (64-bit here; column ids 32-bit).  "Data Sets": duplicate
+// edges pruned.  Self-loops are dropped as well.
+//
+// Edge list -> CSR: each edge {u, v}, u != v, becomes the 64-bit keys
+// (u << 32 | v) and (v << 32 | u); the keys are radix-sorted (CUB) and
+// de-duplicated; the low halves are the column ids and a degree count plus
+// an exclusive scan gives the row offsets.  Also built here: the bitmap of
+// vertices that never search (degree 0, or ids past n in the last word).
+#include <cub/device/device_radix_sort.cuh>
+#include <cub/device/device_scan.cuh>
+#include <cub/device/device_select.cuh>
+
+#include "bfs_internal.h"
+
+namespace bfsk_build {
+
+__global__ void k_check_and_keys(const int32_t* __restrict__ src, const int32_t* __restrict__ dst, long long m,
+                                 long long n, unsigned long long* __restrict__ keys,
+                                 unsigned long long* __restrict__ count, int* __restrict__ bad) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const long long nth = (long long)gridDim.x * blockDim.x;
+    for (long long base = (long long)blockIdx.x * blockDim.x + threadIdx.x - lane; base < m; base += nth) {
+        const long long i = base + lane;
+        bool keep = false;
+        unsigned long long k0 = 0, k1 = 0;
+        if (i < m) {
+            const int u = src[i], v = dst[i];
+            if (u < 0 || v < 0 || (long long)u >= n || (long long)v >= n) {
+                atomicExch(bad, 1);
+            } else if (u != v) {
+                keep = true;
+                k0 = ((unsigned long long)(unsigned)u << 32) | (unsigned)v;
+                k1 = ((unsigned long long)(unsigned)v << 32) | (unsigned)u;
+            }
+        }
+        const unsigned km = __ballot_sync(full, keep);
+        if (km) {
+            const int leader = __ffs(km) - 1;
+            unsigned long long b = 0;
+            if (lane == leader) b = atomicAdd(count, 2ull * __popc(km));
+            b = __shfl_sync(full, b, leader);
+            if (keep) {
+                unsigned lt;
+                asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
+                const unsigned long long pos = b + 2ull * __popc(km & lt);
+                keys[pos] = k0;
+                keys[pos + 1] = k1;
+            }
+        }
+    }
+}
+
+__global__ void k_split_keys(const unsigned long long* __restrict__ keys, long long nnz, int32_t* __restrict__ cols,
+                             unsigned long long* __restrict__ deg) {
+    const long long nth = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += nth) {
+        const unsigned long long k = keys[i];
+        cols[i] = (int32_t)(k & 0xffffffffull);
+        atomicAdd(deg + (k >> 32), 1ull);
+    }
+}
+
+__global__ void k_fill_i32(int32_t* p, long long cnt, int32_t v) {
+    const long long nth = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += nth) p[i] = v;
+}
+
+__global__ void k_isolated(const long long* __restrict__ off, long long n, long long W, uint32_t* __restrict__ iso) {
+    const long long nth = (long long)gridDim.x * blockDim.x;
+    for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < W; w += nth) {
+        uint32_t x = 0;
+        for (int b = 0; b < 32; b++) {
+            const long long v = w * 32 + b;
+            if (v >= n || off[v + 1] == off[v]) x |= 1u << b;
+        }
+        iso[w] = x;
+    }
+}
+
+// CSR validation: warp per row.  bad codes: 1 offsets, 2 id range, 3 order/duplicate, 4 self-loop, 5 asymmetric
+__global__ void k_check_csr(const long long* __restrict__ off, const int32_t* __restrict__ cols, long long n,
+                            long long nnz, int check_sym, int* __restrict__ bad) {
+    const int lane = threadIdx.x & 31;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long r = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5); r < n; r += nw) {
+        const long long s = off[r], e = off[r + 1];
+        if (s > e || s < 0 || e > nnz) {
+            if (lane == 0) atomicMax(bad, 1);
+            continue;
+        }
+        for (long long k = s + lane; k < e; k += 32) {
+            const int c = cols[k];
+            if (c < 0 || (long long)c >= n) { atomicMax(bad, 2); continue; }
+            if (c == (int)r) atomicMax(bad, 4);
+            if (k + 1 < e && !(c < cols[k + 1])) atomicMax(bad, 3);
+            if (check_sym) {
+                long long lo = off[c], hi = off[c + 1];
+                if (lo < 0 || hi > nnz || lo > hi) { atomicMax(bad, 1); continue; }
+                while (lo < hi) {
+                    const long long mid = lo + (hi - lo) / 2;
+                    if (cols[mid] < (int)r) lo = mid + 1; else hi = mid;
+                }
+                if (lo >= off[c + 1] || cols[lo] != (int)r) atomicMax(bad, 5);
+            }
+        }
+    }
+}
+
+}  // namespace bfsk_build
+
+namespace bfsrt {
+
+using namespace bfsk_build;
+
+static int grid_for(long long items, int block, int sms) {
+    long long g = (items + block - 1) / block;
+    long long cap = (long long)sms * 32;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+// RAII scratch through the graph's allocator
+struct Scratch {
+    DeviceAlloc* mem;
+    cudaStream_t s;
+    void* p = nullptr;
+    size_t bytes = 0;
+    Scratch(DeviceAlloc* m, cudaStream_t st) : mem(m), s(st) {}
+    bool get(size_t b) {
+        p = mem->alloc(b, s);
+        bytes = b;
+        return p != nullptr;
+    }
+    ~Scratch() {
+        if (p) mem->release(p, bytes, s);
+    }
+};
+
+static bfs_status finish_offsets(bfs_graph* g, unsigned long long* deg, cudaStream_t s) {
+    // offsets[0] = 0, offsets[1..n] = inclusive scan of degrees
+    const long long n = g->n;
+    size_t tb = 0;
+    BFS_CUDA_TRY(cub::DeviceScan::InclusiveSum(nullptr, tb, deg, (unsigned long long*)g->offsets + 1, n, s));
+    Scratch tmp(&g->mem, s);
+    if (!tmp.get(tb + 16)) return fail(BFS_ERR_OOM, "graph build: scan scratch");
+    BFS_CUDA_TRY(cudaMemsetAsync(g->offsets, 0, sizeof(int64_t), s));
+    BFS_CUDA_TRY(cub::DeviceScan::InclusiveSum(tmp.p, tb, deg, (unsigned long long*)g->offsets + 1, n, s));
+    return BFS_OK;
+}
+
+bfs_status build_isolated_bitmap(bfs_graph* g, cudaStream_t s) {
+    g->W = (g->n + 31) / 32;
+    g->isolated = (uint32_t*)g->mem.alloc(sizeof(uint32_t) * (size_t)g->W, s);
+    if (!g->isolated) return fail(BFS_ERR_OOM, "graph build: isolated bitmap");
+    g->graph_bytes += sizeof(uint32_t) * (size_t)g->W;
+    k_isolated<<<grid_for(g->W, 256, g->sm_count), 256, 0, s>>>((const long long*)g->offsets, g->n, g->W,
+                                                                g->isolated);
+    BFS_CUDA_TRY(cudaGetLastError());
+    return BFS_OK;
+}
+
+bfs_status build_csr_from_edges(bfs_graph* g, const int32_t* src, const int32_t* dst, int64_t m, bool device_ptrs,
+                                cudaStream_t s) {
+    const long long n = g->n;
+    Scratch dsrc(&g->mem, s), ddst(&g->mem, s);
+    const int32_t* es = src;
+    const int32_t* ed = dst;
+    if (!device_ptrs && m > 0) {
+        if (!dsrc.get(sizeof(int32_t) * (size_t)m) || !ddst.get(sizeof(int32_t) * (size_t)m))
+            return fail(BFS_ERR_OOM, "graph build: edge staging");
+        BFS_CUDA_TRY(cudaMemcpyAsync(dsrc.p, src, sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice, s));
+        BFS_CUDA_TRY(cudaMemcpyAsync(ddst.p, dst, sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice, s));
+        es = (const int32_t*)dsrc.p;
+        ed = (const int32_t*)ddst.p;
+    }
+    const long long cap = 2 * (long long)m;
+    Scratch keys_a(&g->mem, s), keys_b(&g->mem, s), small(&g->mem, s);
+    if (!small.get(64)) return fail(BFS_ERR_OOM, "graph build: counters");
+    unsigned long long* d_count = (unsigned long long*)small.p;
+    int* d_bad = (int*)((char*)small.p + 16);
+    unsigned long long* d_sel = (unsigned long long*)((char*)small.p + 32);
+    BFS_CUDA_TRY(cudaMemsetAsync(small.p, 0, 64, s));
+    if (cap > 0) {
+        if (!keys_a.get(sizeof(unsigned long long) * (size_t)cap) || !keys_b.get(sizeof(unsigned long long) * (size_t)cap))
+            return fail(BFS_ERR_OOM, "graph build: key buffers");
+        k_check_and_keys<<<grid_for(m, 256, g->sm_count), 256, 0, s>>>(es, ed, m, n, (unsigned long long*)keys_a.p,
+                                                                      d_count, d_bad);
+        BFS_CUDA_TRY(cudaGetLastError());
+    }
+    unsigned long long h[2] = {0, 0};
+    int hbad = 0;
+    BFS_CUDA_TRY(cudaMemcpyAsync(&h[0], d_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    BFS_CUDA_TRY(cudaMemcpyAsync(&hbad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BFS_CUDA_TRY(cudaStreamSynchronize(s));
+    if (hbad) return fail(BFS_ERR_INVALID, "edge list holds a vertex id outside [0, n_vertices)");
+    const long long nk = (long long)h[0];
+    int end_bit = 32;
+    while (end_bit < 64 && (1ll << (end_bit - 32)) < n) end_bit++;
+    long long nnz = 0;
+    unsigned long long* uniq = nullptr;
+    if (nk > 0) {
+        size_t tb = 0;
+        cub::DoubleBuffer<unsigned long long> db((unsigned long long*)keys_a.p, (unsigned long long*)keys_b.p);
+        BFS_CUDA_TRY(cub::DeviceRadixSort::SortKeys(nullptr, tb, db, nk, 0, end_bit, s));
+        size_t tu = 0;
+        BFS_CUDA_TRY(cub::DeviceSelect::Unique(nullptr, tu, (unsigned long long*)keys_a.p,
+                                               (unsigned long long*)keys_b.p, d_sel, nk, s));
+        Scratch tmp(&g->mem, s);
+        if (!tmp.get((tb > tu ? tb : tu) + 256)) return fail(BFS_ERR_OOM, "graph build: sort scratch");
+        BFS_CUDA_TRY(cub::DeviceRadixSort::SortKeys(tmp.p, tb, db, nk, 0, end_bit, s));
+        unsigned long long* sorted = db.Current();
+        uniq = db.Alternate();
+        BFS_CUDA_TRY(cub::DeviceSelect::Unique(tmp.p, tu, sorted, uniq, d_sel, nk, s));
+        BFS_CUDA_TRY(cudaMemcpyAsync(&h[1], d_sel, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        BFS_CUDA_TRY(cudaStreamSynchronize(s));
+        nnz = (long long)h[1];
+    }
+    g->nnz = nnz;
+    g->offsets = (int64_t*)g->mem.alloc(sizeof(int64_t) * (size_t)(n + 1), s);
+    g->cols = (int32_t*)g->mem.alloc(sizeof(int32_t) * (size_t)(nnz + kColPad), s);
+    if (!g->offsets || !g->cols) return fail(BFS_ERR_OOM, "graph build: CSR arrays");
+    g->graph_bytes = sizeof(int64_t) * (size_t)(n + 1) + sizeof(int32_t) * (size_t)(nnz + kColPad);
+    Scratch deg(&g->mem, s);
+    if (!deg.get(sizeof(unsigned long long) * (size_t)n)) return fail(BFS_ERR_OOM, "graph build: degrees");
+    BFS_CUDA_TRY(cudaMemsetAsync(deg.p, 0, sizeof(unsigned long long) * (size_t)n, s));
+    k_fill_i32<<<1, 32, 0, s>>>(g->cols + nnz, kColPad, 0);
+    BFS_CUDA_TRY(cudaGetLastError());
+    if (nnz > 0) {
+        k_split_keys<<<grid_for(nnz, 256, g->sm_count), 256, 0, s>>>(uniq, nnz, g->cols, (unsigned long long*)deg.p);
+        BFS_CUDA_TRY(cudaGetLastError());
+    }
+    bfs_status st = finish_offsets(g, (unsigned long long*)deg.p, s);
+    if (st != BFS_OK) return st;
+    st = build_isolated_bitmap(g, s);
+    if (st != BFS_OK) return st;
+    BFS_CUDA_TRY(cudaStreamSynchronize(s));
+    return BFS_OK;
+}
+
+bfs_status build_csr_from_csr(bfs_graph* g, const int64_t* off, const int32_t* cols, bool device_ptrs,
+                              bool check_symmetry, cudaStream_t s) {
+    const long long n = g->n, nnz = g->nnz;
+    g->offsets = (int64_t*)g->mem.alloc(sizeof(int64_t) * (size_t)(n + 1), s);
+    g->cols = (int32_t*)g->mem.alloc(sizeof(int32_t) * (size_t)(nnz + kColPad), s);
+    if (!g->offsets || !g->cols) return fail(BFS_ERR_OOM, "graph build: CSR arrays");
+    g->graph_bytes = sizeof(int64_t) * (size_t)(n + 1) + sizeof(int32_t) * (size_t)(nnz + kColPad);
+    const cudaMemcpyKind kind = device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    BFS_CUDA_TRY(cudaMemcpyAsync(g->offsets, off, sizeof(int64_t) * (size_t)(n + 1), kind, s));
+    if (nnz > 0) BFS_CUDA_TRY(cudaMemcpyAsync(g->cols, cols, sizeof(int32_t) * (size_t)nnz, kind, s));
+    k_fill_i32<<<1, 32, 0, s>>>(g->cols + nnz, kColPad, 0);
+    BFS_CUDA_TRY(cudaGetLastError());
+    Scratch small(&g->mem, s);
+    if (!small.get(64)) return fail(BFS_ERR_OOM, "graph build: counters");
+    BFS_CUDA_TRY(cudaMemsetAsync(small.p, 0, 64, s));
+    int64_t ends[2] = {0, 0};
+    BFS_CUDA_TRY(cudaMemcpyAsync(&ends[0], g->offsets, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    BFS_CUDA_TRY(cudaMemcpyAsync(&ends[1], g->offsets + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    BFS_CUDA_TRY(cudaStreamSynchronize(s));
+    if (ends[0] != 0 || ends[1] != nnz) return fail(BFS_ERR_INVALID, "row_offsets[0] must be 0 and row_offsets[n] = nnz");
+    k_check_csr<<<grid_for(n * 32, 256, g->sm_count), 256, 0, s>>>((const long long*)g->offsets, g->cols, n, nnz,
+                                                                 check_symmetry ? 1 : 0, (int*)small.p);
+    BFS_CUDA_TRY(cudaGetLastError());
+    int bad = 0;
+    BFS_CUDA_TRY(cudaMemcpyAsync(&bad, small.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BFS_CUDA_TRY(cudaStreamSynchronize(s));
+    static const char* why[] = {"", "row offsets decrease or leave [0, nnz]", "a column id lies outside [0, n)",
+                                "a row is not strictly ascending (unsorted or duplicate)", "a self-loop",
+                                "the CSR is not symmetric"};
+    if (bad) return fail(BFS_ERR_INVALID, std::string("invalid CSR: ") + why[bad < 6 ? bad : 0]);
+    bfs_status st = build_isolated_bitmap(g, s);
+    if (st != BFS_OK) return st;
+    BFS_CUDA_TRY(cudaStreamSynchronize(s));
+    return BFS_OK;
+}
+
+}  // namespace bfsrt

@@ -1,0 +1,302 @@
+"""GPU parity of the single-source / multi-root search against the CPU oracle.
+
+Levels are compared element by element (bit-exact: integer output, zero
+tolerance).  Parents are legitimately non-unique, so they are checked by the
+oracle's certificate (valid BFS tree of the oracle's own graph), and bit-exact
+against the oracle in BFS_PARENT_MIN_ID mode.  The per-level device counters
+(direction, frontier sizes, bottom-up examination counts) must equal the
+oracle's direction-optimizing schedule exactly.
+"""
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+from graphgen import workloads
+
+pytestmark = pytest.mark.gpu
+
+MODES = None
+
+
+def _modes(bfs):
+    return {"do": bfs.MODE_DO, "td": bfs.MODE_TD_ONLY, "bu": bfs.MODE_BU_ONLY, "random": bfs.MODE_RANDOM}
+
+
+class Case:
+    def __init__(self, bfs, e, dcsc=False):
+        import torch
+        self.e = e
+        self.ref = oracle.build_csr(e.n, e.src, e.dst)
+        self.g = bfs.Graph.from_edges(e.src, e.dst, e.n, dcsc=dcsc)
+        self.labels = oracle.components(self.ref)
+        self.level = torch.empty(e.n, dtype=torch.int32, device="cuda")
+        self.parent = torch.empty(e.n, dtype=torch.int32, device="cuda")
+
+    def run(self, root, opts=None, stats=False):
+        info = self.g.run(root, parent=self.parent, level=self.level, opts=opts, stats=stats, record_levels=1 << 14)
+        return self.level.cpu().numpy(), self.parent.cpu().numpy(), info
+
+
+def _check_csr(case):
+    off, cols = case.g.csr_host()
+    assert case.g.nnz == case.ref.nnz
+    assert np.array_equal(off, case.ref.offsets)
+    assert np.array_equal(cols, case.ref.cols)
+
+
+def _small_graphs():
+    gs = [graphgen.random_small(n, m, s) for n, m, s in
+          [(1, 0, 0), (2, 1, 1), (5, 3, 2), (33, 20, 5), (64, 300, 7), (100, 90, 8), (257, 600, 11)]]
+    gs += [graphgen.path(70), graphgen.cycle(65), graphgen.star(100), graphgen.complete(40)]
+    u, _ = graphgen.disjoint_union([graphgen.path(5), graphgen.complete(4), graphgen.from_pairs(3, [(0, 0)])])
+    gs.append(u)
+    return gs
+
+
+@pytest.mark.parametrize("gi", range(12))
+def test_small_graphs_every_root_every_mode(gpu_lib, gi):
+    bfs = gpu_lib
+    case = Case(bfs, _small_graphs()[gi])
+    _check_csr(case)
+    for root in range(case.e.n):
+        want = oracle.levels(case.ref, root)
+        for name, mode in _modes(bfs).items():
+            lv, pa, _ = case.run(root, bfs.options(mode=mode, seed=root * 7 + 1))
+            assert np.array_equal(lv, want), (case.e.name, root, name)
+            assert oracle.certify(case.ref, root, lv, pa, case.labels) == (0, -1), (case.e.name, root, name)
+
+
+@pytest.mark.parametrize("scale", [12, 16])
+def test_rmat_levels_parents_all_modes(gpu_lib, scale):
+    bfs = gpu_lib
+    w = workloads.RMAT[scale]
+    e = w.edges()
+    case = Case(bfs, e)
+    _check_csr(case)
+    for root in w.roots(e, 16).tolist():
+        want = oracle.levels(case.ref, root)
+        for name, mode in _modes(bfs).items():
+            lv, pa, info = case.run(root, bfs.options(mode=mode, seed=root), stats=True)
+            assert np.array_equal(lv, want), (scale, root, name)
+            assert oracle.certify(case.ref, root, lv, pa, case.labels) == (0, -1), (scale, root, name)
+            assert info["num_levels"] == int(want.max()) + 1
+            assert info["reached"] == int((want >= 0).sum())
+
+
+def test_ragged_er_spans_many_tiles(gpu_lib):
+    bfs = gpu_lib
+    n = 100_003   # not a multiple of 32: ragged last bitmap word
+    e = graphgen.erdos_renyi(n, 8 * n, seed=77)
+    case = Case(bfs, e)
+    _check_csr(case)
+    for root in graphgen.pick_roots(e, 4, 5).tolist():
+        want = oracle.levels(case.ref, root)
+        for mode in (bfs.MODE_DO, bfs.MODE_BU_ONLY, bfs.MODE_TD_ONLY):
+            lv, pa, _ = case.run(root, bfs.options(mode=mode))
+            assert np.array_equal(lv, want)
+            assert oracle.certify(case.ref, root, lv, pa, case.labels) == (0, -1)
+
+
+@pytest.mark.parametrize("scale", [12, 16])
+def test_level_records_match_oracle_schedule(gpu_lib, scale):
+    """Device per-level counters == the oracle's direction-optimizing schedule, for DO/TD/BU."""
+    bfs = gpu_lib
+    w = workloads.RMAT[scale]
+    e = w.edges()
+    case = Case(bfs, e)
+    for root in w.roots(e, 6).tolist():
+        want = oracle.levels(case.ref, root)
+        for mode, omode in ((bfs.MODE_DO, oracle.MODE_DO), (bfs.MODE_TD_ONLY, oracle.MODE_TD),
+                            (bfs.MODE_BU_ONLY, oracle.MODE_BU)):
+            for alpha, beta in ((14, 24), (2, 100)):
+                _, _, info = case.run(root, bfs.options(mode=mode, alpha=alpha, beta=beta), stats=True)
+                s = oracle.do_schedule(case.ref, want, omode, alpha, beta)
+                rec = info["records"]
+                assert rec.shape[0] == s.num_levels
+                got = {k: rec[:, i] for i, k in enumerate(["dir", "nf", "mf", "nnext", "mnext", "scanned", "examined"])}
+                for k in ["dir", "nf", "mf", "nnext", "mnext", "scanned", "examined"]:
+                    assert np.array_equal(got[k], getattr(s, k)), (scale, root, mode, alpha, k)
+
+
+def test_min_id_parents_bit_exact(gpu_lib):
+    bfs = gpu_lib
+    w = workloads.RMAT[14]
+    e = w.edges()
+    case = Case(bfs, e)
+    for root in w.roots(e, 6).tolist():
+        want = oracle.levels(case.ref, root)
+        pmin = oracle.min_parent(case.ref, want)
+        for mode in (bfs.MODE_DO, bfs.MODE_TD_ONLY, bfs.MODE_BU_ONLY, bfs.MODE_RANDOM):
+            lv, pa, _ = case.run(root, bfs.options(mode=mode, parent_mode=bfs.PARENT_MIN_ID, seed=3))
+            assert np.array_equal(lv, want)
+            assert np.array_equal(pa, pmin), (root, mode)
+
+
+def test_torus_closed_form(gpu_lib):
+    bfs = gpu_lib
+    side = 256
+    e = graphgen.torus(side, seed=3000)
+    inv = graphgen.torus_coordinates(side, seed=3000)
+    case = Case(bfs, e)
+    x, y = inv % side, inv // side
+    for root in [0, 12345, side * side - 1]:
+        lv, pa, info = case.run(root, stats=True)
+        dx = np.abs(x - x[root])
+        dy = np.abs(y - y[root])
+        want = np.minimum(dx, side - dx) + np.minimum(dy, side - dy)
+        assert np.array_equal(lv, want)
+        assert info["num_levels"] == side + 1
+        assert oracle.certify(case.ref, root, lv, pa, case.labels) == (0, -1)
+
+
+def test_path_bottom_up_only_same_level_discovery(gpu_lib):
+    """Bottom-up must test the *current* frontier: on a path every level finds one vertex."""
+    bfs = gpu_lib
+    n = 3000
+    case = Case(bfs, graphgen.path(n))
+    for root in (0, 1234, n - 1):
+        lv, pa, info = case.run(root, bfs.options(mode=bfs.MODE_BU_ONLY), stats=True)
+        assert np.array_equal(lv, np.abs(np.arange(n) - root))
+        assert oracle.certify(case.ref, root, lv, pa, case.labels) == (0, -1)
+
+
+def test_degree_zero_root_and_empty_graph(gpu_lib):
+    bfs = gpu_lib
+    e = graphgen.from_pairs(70, [(0, 1), (1, 2), (5, 5), (40, 41)])
+    case = Case(bfs, e)
+    for root in (5, 69, 0, 40):
+        want = oracle.levels(case.ref, root)
+        for mode in (bfs.MODE_DO, bfs.MODE_BU_ONLY, bfs.MODE_TD_ONLY):
+            lv, pa, info = case.run(root, bfs.options(mode=mode), stats=True)
+            assert np.array_equal(lv, want)
+            assert oracle.certify(case.ref, root, lv, pa, case.labels) == (0, -1)
+    empty = Case(bfs, graphgen.from_pairs(10, []))
+    lv, pa, info = empty.run(3, stats=True)
+    assert lv.tolist() == [-1, -1, -1, 0, -1, -1, -1, -1, -1, -1] and pa[3] == 3 and info["num_levels"] == 1
+
+
+def test_outputs_optional(gpu_lib):
+    import torch
+    bfs = gpu_lib
+    w = workloads.RMAT[12]
+    e = w.edges()
+    case = Case(bfs, e)
+    root = int(w.roots(e, 1)[0])
+    want = oracle.levels(case.ref, root)
+    lv = torch.empty(e.n, dtype=torch.int32, device="cuda")
+    case.g.run(root, level=lv)
+    assert np.array_equal(lv.cpu().numpy(), want)
+    pa = torch.empty(e.n, dtype=torch.int32, device="cuda")
+    case.g.run(root, parent=pa)
+    pa = pa.cpu().numpy()
+    assert np.array_equal(pa >= 0, want >= 0)
+    info = case.g.run(root, stats=True)
+    assert info["reached"] == int((want >= 0).sum())
+
+
+def test_multiroot_disjoint_union_equals_parts(gpu_lib):
+    """An uneven batch of graphs as one search over their disjoint union."""
+    bfs = gpu_lib
+    parts = [graphgen.rmat(s, seed=500 + s) for s in (6, 9, 11, 12, 8, 10)]
+    u, offs = graphgen.disjoint_union(parts)
+    roots = [int(offs[i]) + int(graphgen.pick_roots(p, 1, 9 + i)[0]) for i, p in enumerate(parts)]
+    case = Case(bfs, u)
+    for mode in (bfs.MODE_DO, bfs.MODE_TD_ONLY, bfs.MODE_BU_ONLY):
+        case.g.run_multiroot(roots, parent=case.parent, level=case.level, opts=bfs.options(mode=mode))
+        lv = case.level.cpu().numpy()
+        pa = case.parent.cpu().numpy()
+        for i, p in enumerate(parts):
+            pr = oracle.build_csr(p.n, p.src, p.dst)
+            want = oracle.levels(pr, roots[i] - int(offs[i]))
+            assert np.array_equal(lv[offs[i]:offs[i + 1]], want), (i, mode)
+        for i in range(len(parts)):
+            assert pa[roots[i]] == roots[i]
+
+
+def test_multiroot_nearest_root_distance(gpu_lib):
+    """Roots in one component: level = distance to the nearest root (oracle on a super-root graph)."""
+    bfs = gpu_lib
+    e = graphgen.rmat(11, seed=42)
+    roots = graphgen.pick_roots(e, 5, 3).tolist()
+    case = Case(bfs, e)
+    case.g.run_multiroot(roots + roots[:2], parent=case.parent, level=case.level)
+    lv = case.level.cpu().numpy()
+    sup = e.n
+    aug = graphgen.EdgeList(e.n + 1, np.concatenate([e.src, np.full(len(roots), sup, np.int32)]),
+                            np.concatenate([e.dst, np.array(roots, np.int32)]))
+    ref = oracle.build_csr(aug.n, aug.src, aug.dst)
+    d = oracle.levels(ref, sup)[: e.n]
+    want = np.where(d >= 1, d - 1, -1)
+    assert np.array_equal(lv, want)
+
+
+def test_invalid_arguments(gpu_lib):
+    import torch
+    bfs = gpu_lib
+    e = graphgen.rmat(8, seed=1)
+    case = Case(bfs, e)
+    with pytest.raises(bfs.BfsError) as ex:
+        case.g.run(e.n)
+    assert ex.value.status == 1
+    with pytest.raises(bfs.BfsError) as ex:
+        case.g.run(-1)
+    assert ex.value.status == 1
+    with pytest.raises(bfs.BfsError):
+        case.g.run(0, parent=case.parent, opts=bfs.options(parent_mode=bfs.PARENT_MIN_ID))
+    with pytest.raises(bfs.BfsError):
+        bfs.Graph.from_edges(np.array([0, 5], np.int32), np.array([1, 300], np.int32), 10)
+    # CSR validation
+    ref = oracle.build_csr(e.n, e.src, e.dst)
+    g2 = bfs.Graph.from_csr(ref.offsets, ref.cols, e.n, check_symmetry=True)
+    off, cols = g2.csr_host()
+    assert np.array_equal(off, ref.offsets) and np.array_equal(cols, ref.cols)
+    bad = ref.cols.copy()
+    row = int(np.argmax(np.diff(ref.offsets)))
+    s = int(ref.offsets[row])
+    bad[s], bad[s + 1] = bad[s + 1], bad[s]
+    with pytest.raises(bfs.BfsError):
+        bfs.Graph.from_csr(ref.offsets, bad, e.n)
+    bad = ref.cols.copy()
+    bad[s] = row
+    with pytest.raises(bfs.BfsError):
+        bfs.Graph.from_csr(ref.offsets, bad, e.n)
+    # directed (asymmetric) CSR: rejected only when asked to check
+    off = np.array([0, 1, 1], np.int64)
+    cols = np.array([1], np.int32)
+    bfs.Graph.from_csr(off, cols, 2).close()
+    with pytest.raises(bfs.BfsError):
+        bfs.Graph.from_csr(off, cols, 2, check_symmetry=True)
+
+
+def test_barrier_timeout_returns_error_and_recovers(gpu_lib):
+    """A grid barrier that waits for an arrival that never comes gives up after timeout_ms,
+    reports BFS_ERR_TIMEOUT, and the next search on the same graph is correct."""
+    bfs = gpu_lib
+    w = workloads.RMAT[10]
+    e = w.edges()
+    case = Case(bfs, e)
+    root = int(w.roots(e, 1)[0])
+    with pytest.raises(bfs.BfsError) as ex:
+        case.run(root, bfs.options(timeout_ms=200, debug_barrier_extra=1), stats=True)
+    assert ex.value.status == 4
+    lv, pa, _ = case.run(root, stats=True)
+    assert np.array_equal(lv, oracle.levels(case.ref, root))
+
+
+def test_streams_and_repeat(gpu_lib):
+    import torch
+    bfs = gpu_lib
+    w = workloads.RMAT[13]
+    e = w.edges()
+    case = Case(bfs, e)
+    roots = w.roots(e, 8).tolist()
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    outs = [torch.empty(e.n, dtype=torch.int32, device="cuda") for _ in roots]
+    for i, r in enumerate(roots):
+        case.g.run(r, level=outs[i], stream=s1 if i % 2 else s2)
+    case.g.sync(s1)
+    case.g.sync(s2)
+    torch.cuda.synchronize()
+    for i, r in enumerate(roots):
+        assert np.array_equal(outs[i].cpu().numpy(), oracle.levels(case.ref, r))
