@@ -118,6 +118,7 @@ typedef struct {
     int64_t scanned;      /* bottom-up: unvisited vertices with degree > 0 that searched */
     int64_t examined;     /* top-down: m_f; bottom-up: sum over searching vertices of the 1-based
                              position of the first frontier neighbour in sorted order, or the degree */
+    int64_t t_ns;         /* device time from the end of initialisation to the end of this level */
 } bfs_level_record;
 
 typedef struct {

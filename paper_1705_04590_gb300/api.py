@@ -216,8 +216,8 @@ class Graph:
             return None
         s, recs, cap = holder
         nrec = min(s.num_levels, cap)
-        rows = [(r.dir, r.nf, r.mf, r.nnext, r.mnext, r.scanned, r.examined) for r in recs[:nrec]]
-        arr = np.array(rows, dtype=np.int64).reshape(-1, 7)
+        rows = [(r.dir, r.nf, r.mf, r.nnext, r.mnext, r.scanned, r.examined, r.t_ns) for r in recs[:nrec]]
+        arr = np.array(rows, dtype=np.int64).reshape(-1, 8)
         return {"num_levels": s.num_levels, "reached": s.vertices_reached, "edges_examined": s.edges_examined,
                 "records": arr}
 

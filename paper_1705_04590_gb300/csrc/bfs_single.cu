@@ -444,6 +444,7 @@ __global__ void __launch_bounds__(kBlock, 2) bfs_single_kernel(SingleParams p) {
     long long reached = nf;
     int prev = TD, qsel = 0, bsel = 0, d = 0;
     const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+    const uint64_t t_start = lead ? globaltimer_ns() : 0;
     while (true) {
         const int dir = decide_dir(p, prev, nf, mf, mu, d);
         const int scur = d % 3, snext = (d + 1) % 3, sfree = (d + 2) % 3;
@@ -505,6 +506,7 @@ __global__ void __launch_bounds__(kBlock, 2) bfs_single_kernel(SingleParams p) {
             r.mnext = mf_next;
             r.scanned = scanned;
             r.examined = examined;
+            r.t_ns = (long long)(globaltimer_ns() - t_start);
             p.rec[d] = r;
         }
         if (nf_next == 0) break;

@@ -24,14 +24,14 @@ L2_BYTES = 126 * 1024 * 1024
 
 
 def search_bytes(n: int, records, want_parent: bool = True, want_level: bool = True) -> int:
-    """records: rows (dir, nf, mf, nnext, mnext, scanned, examined), one per level."""
+    """records: rows (dir, nf, mf, nnext, mnext, scanned, examined[, t_ns]), one per level."""
     W = (n + 7) // 8
     out = 4 * (int(want_parent) + int(want_level))
     probe = 0 if W <= L2_BYTES // 4 else 4
     total = out * n + W
     prev = 0
     for r in records:
-        d, nf, mf, nnext, _mnext, scanned, examined = (int(x) for x in r)
+        d, nf, mf, nnext, _mnext, scanned, examined = (int(x) for x in r[:7])
         if d == 1 and prev == 0:
             total += 4 * nf + W
         elif d == 0 and prev == 1:
