@@ -22,13 +22,19 @@ constexpr unsigned kDevOk = 0;
 constexpr unsigned kDevTimeout = 1;
 constexpr unsigned kDevOverflow = 2;
 
-// Control block of one launch: zeroed by the host (cudaMemsetAsync) before
-// every launch.  Counters indexed [slot] rotate over levels (slot = level % 3).
-struct Ctrl {
-    unsigned bar_count;
-    unsigned bar_gen;
+// Grid barrier + run status; the first member of every launch control block.
+struct BarrierState {
+    unsigned count;
+    unsigned gen;
     unsigned status;
-    unsigned pad0;
+    unsigned pad;
+};
+
+// Control block of one single-source launch: zeroed by the host
+// (cudaMemsetAsync) before every launch.  Counters indexed [slot] rotate over
+// levels (slot = level % 3).
+struct Ctrl {
+    BarrierState b;
     unsigned long long tail[3];      // length of the queue holding frontier `slot`
     unsigned long long accn[3];      // size of frontier `slot` (bottom-up producer)
     unsigned long long accm[3];      // degree sum of frontier `slot`
@@ -128,22 +134,22 @@ __device__ __forceinline__ void block_add4(unsigned long long a, unsigned long l
 // when the run has failed (this wait or another CTA's ran out of time); the
 // caller then leaves its loop.  `expected` is the number of CTAs (plus any
 // deliberately missing arrivals in the timeout test).
-__device__ __forceinline__ bool grid_sync(Ctrl* c, unsigned expected, uint64_t timeout_ns) {
+__device__ __forceinline__ bool grid_sync(BarrierState* c, unsigned expected, uint64_t timeout_ns) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        const unsigned g = ld_acquire(&c->bar_gen);
+        const unsigned g = ld_acquire(&c->gen);
         __threadfence();
-        const unsigned arrived = atomicAdd(&c->bar_count, 1u) + 1u;
+        const unsigned arrived = atomicAdd(&c->count, 1u) + 1u;
         if (arrived == expected) {
-            atomicExch(&c->bar_count, 0u);
+            atomicExch(&c->count, 0u);
             __threadfence();
-            st_release(&c->bar_gen, g + 1u);
+            st_release(&c->gen, g + 1u);
         } else {
             const uint64_t t0 = globaltimer_ns();
             unsigned spins = 0;
-            while (ld_acquire(&c->bar_gen) == g) {
+            while (ld_acquire(&c->gen) == g) {
                 if (++spins > 32u) {
                     __nanosleep(40);
                     if ((spins & 63u) == 0u) {

@@ -52,14 +52,17 @@ struct SingleWork {
     int grid = 0, block = 0;       // cooperative launch shape
 };
 
+// Buffers of one multi-source (64-lane) search state: bfs_run_multi's own,
+// and one per graph slot of a server.
 struct MultiWork {
     bool ready = false;
-    unsigned long long* seen = nullptr;
-    unsigned long long* front = nullptr;
-    unsigned long long* next = nullptr;
-    void* ctrl = nullptr;
-    int* roots_dev = nullptr;      // [64]
-    int* roots_pinned = nullptr;
+    unsigned long long* seen = nullptr;   // [n] lane masks
+    unsigned long long* front = nullptr;  // [n]
+    unsigned long long* next = nullptr;   // [n]
+    void* ctrl = nullptr;                 // bfsk::MCtrl
+    void* tasks = nullptr;                // bfsk::MTask[task_cap]
+    long long task_cap = 0;
+    void* lanes = nullptr;                // bfsk::LaneTable
     size_t bytes = 0;
     int grid = 0, block = 0;
 };
@@ -124,12 +127,19 @@ bfs_status multi_launch(bfs_graph* g, const int32_t* roots_host, int32_t k, int3
                         int32_t* parent, const bfs_options& opt, cudaStream_t s);
 bfs_status multi_collect_status(bfs_graph* g, cudaStream_t s);
 void multi_release(bfs_graph* g);
+bfs_status multi_alloc(bfs_graph* g, MultiWork& w, cudaStream_t s);
+void multi_free(bfs_graph* g, MultiWork& w);
 
-// lane-slot stepping for the server (bfs_multi.cu)
-struct LaneJob {
-    int32_t root;
-    int32_t start_iter;  // iteration at which the lane was seeded
-    int32_t* level_dev;  // [n] output row
-};
+// Stepped multi-source driver used by the server (bfs_multi.cu).  The host
+// keeps a mirror of the lane table; every call is asynchronous on `s`.
+bfs_status ms_step_reset(bfs_graph* g, MultiWork& w, cudaStream_t s);
+bfs_status ms_step_admit(bfs_graph* g, MultiWork& w, const void* lane_table_host, unsigned long long newmask,
+                         cudaStream_t s);
+bfs_status ms_step_drop(bfs_graph* g, MultiWork& w, unsigned long long mask, cudaStream_t s);
+// ctrl_pinned: host (pinned) copy of the slot's control block, filled at the end of the level
+bfs_status ms_step_iterate(bfs_graph* g, MultiWork& w, int iter, int dir, unsigned long long active,
+                           void* ctrl_pinned, cudaStream_t s);
+size_t ms_lane_table_bytes();
+void ms_lane_table_set(void* table_host, int lane, int32_t* row, int start, int root);
 
 }  // namespace bfsrt

@@ -191,7 +191,7 @@ __device__ void td_phase(const SingleParams& p, int d, const int* qcur, long lon
                     t.u = u;
                     p.tasks[ti] = t;
                 } else {
-                    atomicMax(&p.ctrl->status, kDevOverflow);
+                    atomicMax(&p.ctrl->b.status, kDevOverflow);
                 }
             }
         } else {
@@ -433,10 +433,10 @@ __device__ void bu_phase(const SingleParams& p, int d, const unsigned* fcur, uns
 __global__ void __launch_bounds__(kBlock, 2) bfs_single_kernel(SingleParams p) {
     Ctrl* c = p.ctrl;
     init_phase(p);
-    if (!grid_sync(c, p.expected, p.timeout_ns)) return;
+    if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
     if (p.nroots > 1) {
         seed_roots_phase(p);
-        if (!grid_sync(c, p.expected, p.timeout_ns)) return;
+        if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
     }
     long long nf = p.nroots;
     long long mf = (long long)ld_acquire64(&c->accm[0]);
@@ -464,18 +464,18 @@ __global__ void __launch_bounds__(kBlock, 2) bfs_single_kernel(SingleParams p) {
         if (dir == TD) {
             if (prev == BU) {
                 bitmap_to_queue(p, fcur, fnext, qcur, &c->tail[scur]);
-                if (!grid_sync(c, p.expected, p.timeout_ns)) return;
+                if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
             }
             unsigned long long am = 0;
             td_phase(p, d, qcur, nf, qnext, snext, am);
             block_add4(0, am, 0, 0, nullptr, &c->accm[snext], nullptr, nullptr);
-            if (!grid_sync(c, p.expected, p.timeout_ns)) return;
+            if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
             const long long nt = (long long)ld_acquire64(&c->ntask[snext]);
             if (nt > 0) {
                 unsigned long long am2 = 0;
                 task_phase(p, d, nt, qnext, snext, am2);
                 block_add4(0, am2, 0, 0, nullptr, &c->accm[snext], nullptr, nullptr);
-                if (!grid_sync(c, p.expected, p.timeout_ns)) return;
+                if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
             }
             nf_next = (long long)ld_acquire64(&c->tail[snext]);
             if (p.parent_mode == BFS_PARENT_MIN_ID && p.parent && p.level) td_min_parent(p, d, qnext, nf_next);
@@ -483,13 +483,13 @@ __global__ void __launch_bounds__(kBlock, 2) bfs_single_kernel(SingleParams p) {
         } else {
             if (prev == TD) {
                 queue_to_bitmap(p, qcur, nf, fcur);
-                if (!grid_sync(c, p.expected, p.timeout_ns)) return;
+                if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
             }
             unsigned long long an = 0, am = 0, asc = 0, aex = 0;
             bu_phase(p, d, fcur, fnext, an, am, asc, aex);
             block_add4(an, am, asc, aex, &c->accn[snext], &c->accm[snext], &c->scanned[snext],
                        &c->examined[snext]);
-            if (!grid_sync(c, p.expected, p.timeout_ns)) return;
+            if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
             nf_next = (long long)ld_acquire64(&c->accn[snext]);
             scanned = (long long)ld_acquire64(&c->scanned[snext]);
             examined = (long long)ld_acquire64(&c->examined[snext]);
@@ -635,9 +635,9 @@ bfs_status single_collect(bfs_graph* g, cudaStream_t s, bfs_stats* stats) {
     Ctrl c;
     BFS_CUDA_TRY(cudaMemcpyAsync(&c, w.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
     BFS_CUDA_TRY(cudaStreamSynchronize(s));
-    if (c.status == bfsk::kDevTimeout)
+    if (c.b.status == bfsk::kDevTimeout)
         return fail(BFS_ERR_TIMEOUT, "device grid barrier wait ran out of time; outputs are undefined");
-    if (c.status == bfsk::kDevOverflow)
+    if (c.b.status == bfsk::kDevOverflow)
         return fail(BFS_ERR_CUDA, "top-down chunk task list overflowed (internal sizing error)");
     if (stats) {
         stats->num_levels = (int32_t)c.num_levels;

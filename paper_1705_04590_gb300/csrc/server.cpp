@@ -1,18 +1,396 @@
-// server.cpp -- placeholder until the continuous-batching server lands.
+// server.cpp -- BFS query server with continuous batching.
+//
+// Graphs stay resident.  Each graph slot runs one multi-source search state
+// (64 lane bits per vertex, see bfs_multi.cu) that advances level by level;
+// a query is a (slot, root) pair.  A host worker thread loops:
+//   1. admission: queued queries of a slot take free lanes, bounded by
+//      max_lanes and by the HBM budget (each lane needs a device row of n
+//      int32 for its levels; rows are allocated on first use and kept);
+//      a new lane starts at the slot's current iteration, so it joins the
+//      running batch at a level boundary;
+//   2. one level of every slot that has active lanes, each slot on its own
+//      stream so the levels of different graphs overlap on the device;
+//   3. completion: a lane whose frontier came back empty is finished; its row
+//      is copied to the caller's host buffer and the ticket completes.
+// Level values of a lane count from its own start, so a query gets the same
+// levels whether it ran alone or in a mix (tested).
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
 #include "bfs_internal.h"
+#include "bfs_multi.h"
 
 using namespace bfsrt;
+using Clock = std::chrono::steady_clock;
+
+namespace {
+
+enum TicketState { kQueued = 0, kRunning = 1, kDone = 2, kFailed = 3 };
+
+struct Ticket {
+    int slot = 0;
+    int root = 0;
+    int32_t* host_out = nullptr;
+    int state = kQueued;
+    bfs_status err = BFS_OK;
+    int lane = -1;
+    Clock::time_point t_submit, t_done;
+};
+
+struct Lane {
+    bool busy = false;
+    uint64_t ticket = 0;
+    int32_t* row = nullptr;   // device [n]
+};
+
+struct Slot {
+    bfs_graph* g = nullptr;
+    MultiWork w;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev = nullptr;
+    std::vector<unsigned char> table;   // host mirror of the lane table
+    Lane lanes[64];
+    unsigned long long active = 0;      // lanes with a search in progress
+    unsigned long long stale = 0;       // finished lanes whose bits are still in seen/front
+    int iter = 0;
+    int prev_dir = 0;
+    long long nf = 0, mf = 0;
+    std::deque<uint64_t> queue;
+    bfsk::MCtrl* ctrl_pinned = nullptr;
+    bool launched = false;
+    unsigned long long launched_new = 0;
+    std::vector<uint64_t> copying;      // tickets whose rows are being copied out
+};
+
+}  // namespace
+
+struct bfs_server {
+    int64_t budget = 0;
+    int64_t used = 0;
+    int32_t max_lanes = 64;
+    int device = 0;
+    std::vector<Slot*> slots;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::unordered_map<uint64_t, Ticket> tickets;
+    uint64_t next_ticket = 1;
+    size_t queue_cap = 1 << 22;
+    size_t queued = 0;
+    bool stop = false;
+    std::thread worker;
+    int64_t completed = 0, launches = 0, lanes_filled = 0;
+    std::string fatal;
+};
+
+namespace {
+
+int pick_dir(const Slot& s) {
+    const bfs_graph* g = s.g;
+    if (s.prev_dir == 0) return (s.mf * 14 > g->nnz / 2) ? 1 : 0;
+    return (s.nf * 24 < g->n) ? 0 : 1;
+}
+
+void fail_slot(bfs_server* sv, Slot& s, const std::string& why) {
+    for (int i = 0; i < 64; i++) {
+        if (!s.lanes[i].busy) continue;
+        auto it = sv->tickets.find(s.lanes[i].ticket);
+        if (it != sv->tickets.end()) {
+            it->second.state = kFailed;
+            it->second.err = BFS_ERR_CUDA;
+            it->second.t_done = Clock::now();
+        }
+        s.lanes[i].busy = false;
+    }
+    s.active = 0;
+    sv->fatal = why;
+}
+
+void worker_main(bfs_server* sv) {
+    cudaSetDevice(sv->device);
+    std::vector<Slot*> snap;
+    while (true) {
+        // ---------------------------------------------------------- 1. admission
+        {
+            std::unique_lock<std::mutex> lk(sv->mu);
+            sv->cv_work.wait(lk, [&] {
+                if (sv->stop) return true;
+                for (Slot* s : sv->slots)
+                    if (s->active || !s->queue.empty()) return true;
+                return false;
+            });
+            if (sv->stop) break;
+            snap = sv->slots;   // slots are only appended; the worker steps this snapshot
+            for (Slot* sp : snap) {
+                Slot& s = *sp;
+                s.launched = false;
+                s.launched_new = 0;
+                const size_t row_bytes = sizeof(int32_t) * (size_t)s.g->n;
+                for (int i = 0; i < sv->max_lanes && !s.queue.empty(); i++) {
+                    Lane& L = s.lanes[i];
+                    if (L.busy) continue;
+                    if (!L.row) {
+                        if (sv->used + (int64_t)row_bytes > sv->budget) break;   // admission bounded by HBM budget
+                        if (cudaMalloc(&L.row, row_bytes) != cudaSuccess) {
+                            (void)cudaGetLastError();
+                            L.row = nullptr;
+                            break;
+                        }
+                        sv->used += (int64_t)row_bytes;
+                    }
+                    const uint64_t tk = s.queue.front();
+                    s.queue.pop_front();
+                    sv->queued--;
+                    Ticket& t = sv->tickets[tk];
+                    t.state = kRunning;
+                    t.lane = i;
+                    L.busy = true;
+                    L.ticket = tk;
+                    ms_lane_table_set(s.table.data(), i, L.row, s.iter, t.root);
+                    s.launched_new |= 1ull << i;
+                }
+            }
+        }
+        // ---------------------------------------------------------- 2. one level per busy slot
+        for (Slot* sp : snap) {
+            Slot& s = *sp;
+            if (!s.active && !s.launched_new) continue;
+            bfs_status st = BFS_OK;
+            const unsigned long long reuse = s.launched_new & s.stale;
+            if (reuse) {
+                st = ms_step_drop(s.g, s.w, reuse, s.stream);
+                s.stale &= ~reuse;
+            }
+            if (st == BFS_OK && s.launched_new) {
+                st = ms_step_admit(s.g, s.w, s.table.data(), s.launched_new, s.stream);
+                s.active |= s.launched_new;
+                s.nf += __builtin_popcountll(s.launched_new);
+            }
+            if (st == BFS_OK) {
+                const int dir = pick_dir(s);
+                st = ms_step_iterate(s.g, s.w, s.iter, dir, s.active, s.ctrl_pinned, s.stream);
+                s.prev_dir = dir;
+            }
+            if (st == BFS_OK && cudaEventRecord(s.ev, s.stream) != cudaSuccess) st = BFS_ERR_CUDA;
+            if (st != BFS_OK) {
+                std::lock_guard<std::mutex> lk(sv->mu);
+                fail_slot(sv, s, bfs_last_error());
+                continue;
+            }
+            s.launched = true;
+            sv->launches++;
+            sv->lanes_filled += __builtin_popcountll(s.active);
+        }
+        // ---------------------------------------------------------- 3. completion
+        for (Slot* sp : snap) {
+            Slot& s = *sp;
+            if (!s.launched) continue;
+            if (cudaEventSynchronize(s.ev) != cudaSuccess) {
+                (void)cudaGetLastError();
+                std::lock_guard<std::mutex> lk(sv->mu);
+                fail_slot(sv, s, "device error while stepping a slot");
+                continue;
+            }
+            const bfsk::MCtrl& c = *s.ctrl_pinned;
+            if (c.b.status != 0) {
+                std::lock_guard<std::mutex> lk(sv->mu);
+                fail_slot(sv, s, "device status error while stepping a slot");
+                continue;
+            }
+            const unsigned long long finished = s.active & ~c.found[0];
+            s.nf = (long long)c.accn[0];
+            s.mf = (long long)c.accm[0];
+            s.iter++;
+            s.copying.clear();
+            for (int i = 0; i < 64; i++) {
+                if (!((finished >> i) & 1ull)) continue;
+                Lane& L = s.lanes[i];
+                int32_t* out = nullptr;
+                {
+                    std::lock_guard<std::mutex> lk(sv->mu);
+                    out = sv->tickets[L.ticket].host_out;
+                }
+                cudaMemcpyAsync(out, L.row, sizeof(int32_t) * (size_t)s.g->n, cudaMemcpyDeviceToHost, s.stream);
+                s.copying.push_back(L.ticket);
+            }
+            s.active &= ~finished;
+            s.stale |= finished;
+        }
+        for (Slot* sp : snap) {
+            Slot& s = *sp;
+            if (s.copying.empty()) continue;
+            const cudaError_t e = cudaStreamSynchronize(s.stream);
+            std::lock_guard<std::mutex> lk(sv->mu);
+            const auto now = Clock::now();
+            for (uint64_t tk : s.copying) {
+                Ticket& t = sv->tickets[tk];
+                t.state = e == cudaSuccess ? kDone : kFailed;
+                t.err = e == cudaSuccess ? BFS_OK : BFS_ERR_CUDA;
+                t.t_done = now;
+                s.lanes[t.lane].busy = false;
+                sv->completed++;
+            }
+            s.copying.clear();
+        }
+        sv->cv_done.notify_all();
+    }
+}
+
+}  // namespace
 
 extern "C" {
-bfs_status bfs_server_create(int64_t, int32_t, bfs_server** out) {
-    if (out) *out = nullptr;
-    return fail(BFS_ERR_UNSUPPORTED, "server: not built yet");
+
+bfs_status bfs_server_create(int64_t hbm_budget_bytes, int32_t max_lanes, bfs_server** out) {
+    if (!out) return fail(BFS_ERR_INVALID, "out handle pointer is NULL");
+    *out = nullptr;
+    if (hbm_budget_bytes <= 0) return fail(BFS_ERR_INVALID, "hbm_budget_bytes must be > 0");
+    if (max_lanes < 1 || max_lanes > 64) return fail(BFS_ERR_INVALID, "max_lanes must lie in [1, 64]");
+    bfs_server* sv = new (std::nothrow) bfs_server();
+    if (!sv) return fail(BFS_ERR_OOM, "host allocation of the server");
+    sv->budget = hbm_budget_bytes;
+    sv->max_lanes = max_lanes;
+    cudaError_t e = cudaGetDevice(&sv->device);
+    if (e != cudaSuccess) {
+        delete sv;
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    sv->worker = std::thread(worker_main, sv);
+    *out = sv;
+    return BFS_OK;
 }
-bfs_status bfs_server_add_graph(bfs_server*, bfs_graph*, int32_t*) { return fail(BFS_ERR_UNSUPPORTED, "server"); }
-bfs_status bfs_submit(bfs_server*, int32_t, int32_t, int32_t*, uint64_t*) { return fail(BFS_ERR_UNSUPPORTED, "server"); }
-bfs_status bfs_poll(bfs_server*, uint64_t) { return fail(BFS_ERR_UNSUPPORTED, "server"); }
-bfs_status bfs_wait(bfs_server*, uint64_t, int64_t) { return fail(BFS_ERR_UNSUPPORTED, "server"); }
-bfs_status bfs_server_stats(bfs_server*, int64_t*) { return fail(BFS_ERR_UNSUPPORTED, "server"); }
-bfs_status bfs_ticket_latency_us(bfs_server*, uint64_t, double*) { return fail(BFS_ERR_UNSUPPORTED, "server"); }
-void bfs_server_destroy(bfs_server*) {}
+
+bfs_status bfs_server_add_graph(bfs_server* sv, bfs_graph* g, int32_t* slot) {
+    if (!sv || !g) return fail(BFS_ERR_INVALID, "NULL server or graph");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    Slot* s = new (std::nothrow) Slot();
+    if (!s) return fail(BFS_ERR_OOM, "host allocation of a slot");
+    s->g = g;
+    const int64_t need = (int64_t)(3 * sizeof(unsigned long long) * (size_t)g->n);
+    if (sv->used + need > sv->budget) {
+        delete s;
+        return fail(BFS_ERR_OOM, "HBM budget too small for the graph's lane masks");
+    }
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+        delete s;
+        return fail(BFS_ERR_CUDA, "cudaStreamCreate");
+    }
+    s->stream = st;
+    bfs_status r = multi_alloc(g, s->w, st);
+    if (r == BFS_OK) r = ms_step_reset(g, s->w, st);
+    if (r == BFS_OK && cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming) != cudaSuccess) r = BFS_ERR_CUDA;
+    if (r == BFS_OK && cudaMallocHost((void**)&s->ctrl_pinned, sizeof(bfsk::MCtrl)) != cudaSuccess) r = BFS_ERR_OOM;
+    if (r == BFS_OK && cudaStreamSynchronize(st) != cudaSuccess) r = BFS_ERR_CUDA;
+    if (r != BFS_OK) {
+        std::string msg = bfs_last_error();
+        multi_free(g, s->w);
+        if (s->ev) cudaEventDestroy(s->ev);
+        if (s->ctrl_pinned) cudaFreeHost(s->ctrl_pinned);
+        cudaStreamDestroy(st);
+        delete s;
+        return fail(r, "server: add_graph: " + msg);
+    }
+    memset(s->ctrl_pinned, 0, sizeof(bfsk::MCtrl));
+    s->table.assign(ms_lane_table_bytes(), 0);
+    sv->used += (int64_t)s->w.bytes;
+    sv->slots.push_back(s);
+    if (slot) *slot = (int32_t)(sv->slots.size() - 1);
+    return BFS_OK;
 }
+
+bfs_status bfs_submit(bfs_server* sv, int32_t slot, int32_t root, int32_t* level_out_host, uint64_t* ticket) {
+    if (!sv || !ticket || !level_out_host) return fail(BFS_ERR_INVALID, "NULL argument");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (slot < 0 || (size_t)slot >= sv->slots.size()) return fail(BFS_ERR_INVALID, "unknown graph slot");
+    Slot& s = *sv->slots[slot];
+    if (root < 0 || (int64_t)root >= s.g->n) return fail(BFS_ERR_INVALID, "root outside [0, n)");
+    if (sv->queued >= sv->queue_cap) return fail(BFS_ERR_BUSY, "request queue is full");
+    const uint64_t tk = sv->next_ticket++;
+    Ticket t;
+    t.slot = slot;
+    t.root = root;
+    t.host_out = level_out_host;
+    t.t_submit = Clock::now();
+    sv->tickets[tk] = t;
+    s.queue.push_back(tk);
+    sv->queued++;
+    *ticket = tk;
+    sv->cv_work.notify_one();
+    return BFS_OK;
+}
+
+bfs_status bfs_poll(bfs_server* sv, uint64_t ticket) {
+    if (!sv) return fail(BFS_ERR_INVALID, "NULL server");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->tickets.find(ticket);
+    if (it == sv->tickets.end()) return fail(BFS_ERR_INVALID, "unknown ticket");
+    if (it->second.state == kDone) return BFS_OK;
+    if (it->second.state == kFailed) return fail(it->second.err, "query failed: " + sv->fatal);
+    return BFS_ERR_NOT_READY;
+}
+
+bfs_status bfs_wait(bfs_server* sv, uint64_t ticket, int64_t timeout_ms) {
+    if (!sv) return fail(BFS_ERR_INVALID, "NULL server");
+    std::unique_lock<std::mutex> lk(sv->mu);
+    auto it = sv->tickets.find(ticket);
+    if (it == sv->tickets.end()) return fail(BFS_ERR_INVALID, "unknown ticket");
+    auto ready = [&] { return it->second.state == kDone || it->second.state == kFailed; };
+    if (timeout_ms < 0) {
+        sv->cv_done.wait(lk, ready);
+    } else if (!sv->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready)) {
+        return BFS_ERR_NOT_READY;
+    }
+    if (it->second.state == kFailed) return fail(it->second.err, "query failed: " + sv->fatal);
+    return BFS_OK;
+}
+
+bfs_status bfs_server_stats(bfs_server* sv, int64_t* counters3) {
+    if (!sv || !counters3) return fail(BFS_ERR_INVALID, "NULL argument");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    counters3[0] = sv->completed;
+    counters3[1] = sv->launches;
+    counters3[2] = sv->lanes_filled;
+    return BFS_OK;
+}
+
+bfs_status bfs_ticket_latency_us(bfs_server* sv, uint64_t ticket, double* us) {
+    if (!sv || !us) return fail(BFS_ERR_INVALID, "NULL argument");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->tickets.find(ticket);
+    if (it == sv->tickets.end()) return fail(BFS_ERR_INVALID, "unknown ticket");
+    if (it->second.state != kDone) return BFS_ERR_NOT_READY;
+    *us = std::chrono::duration<double, std::micro>(it->second.t_done - it->second.t_submit).count();
+    return BFS_OK;
+}
+
+void bfs_server_destroy(bfs_server* sv) {
+    if (!sv) return;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->stop = true;
+    }
+    sv->cv_work.notify_all();
+    if (sv->worker.joinable()) sv->worker.join();
+    for (Slot* s : sv->slots) {
+        cudaStreamSynchronize(s->stream);
+        for (auto& L : s->lanes)
+            if (L.row) cudaFree(L.row);
+        multi_free(s->g, s->w);
+        cudaEventDestroy(s->ev);
+        cudaFreeHost(s->ctrl_pinned);
+        cudaStreamDestroy(s->stream);
+        delete s;
+    }
+    for (auto& kv : sv->tickets)
+        if (kv.second.state == kQueued || kv.second.state == kRunning) kv.second.state = kFailed;
+    sv->cv_done.notify_all();
+    delete sv;
+}
+
+}  // extern "C"
