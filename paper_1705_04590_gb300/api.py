@@ -231,3 +231,73 @@ class Graph:
             self.close()
         except Exception:
             pass
+
+
+class Server:
+    """Continuous-batching BFS query server (bfs_server_* in include/bfs.h).
+
+    Graphs stay resident; each query (slot, root) fills a caller-owned host
+    int32 array of the graph's n levels.  Queries that arrive while others run
+    join the running multi-source search of their graph at the next level.
+    """
+
+    def __init__(self, hbm_budget_bytes: int, max_lanes: int = 64):
+        lib = L.load()
+        h = ctypes.c_void_p()
+        L.check(lib.bfs_server_create(int(hbm_budget_bytes), int(max_lanes), ctypes.byref(h)), "bfs_server_create")
+        self._h = h
+        self._graphs = []
+        self._outs = {}
+
+    def add_graph(self, g: Graph) -> int:
+        slot = ctypes.c_int32()
+        L.check(L.load().bfs_server_add_graph(self._h, g.handle, ctypes.byref(slot)), "bfs_server_add_graph")
+        self._graphs.append(g)
+        return slot.value
+
+    def submit(self, slot: int, root: int, out: np.ndarray) -> int:
+        """out: int32 host array of the graph's n entries (pinned memory copies fastest)."""
+        if out.dtype != np.int32 or not out.flags.c_contiguous:
+            raise TypeError("out must be a contiguous int32 numpy array")
+        t = ctypes.c_uint64()
+        L.check(L.load().bfs_submit(self._h, int(slot), int(root), out.ctypes.data, ctypes.byref(t)), "bfs_submit")
+        self._outs[t.value] = out
+        return t.value
+
+    def poll(self, ticket: int) -> bool:
+        st = L.load().bfs_poll(self._h, ctypes.c_uint64(ticket))
+        if st == L.BFS_ERR_NOT_READY:
+            return False
+        L.check(st, "bfs_poll")
+        self._outs.pop(ticket, None)
+        return True
+
+    def wait(self, ticket: int, timeout_ms: int = -1) -> bool:
+        st = L.load().bfs_wait(self._h, ctypes.c_uint64(ticket), int(timeout_ms))
+        if st == L.BFS_ERR_NOT_READY:
+            return False
+        L.check(st, "bfs_wait")
+        self._outs.pop(ticket, None)
+        return True
+
+    def latency_us(self, ticket: int) -> float:
+        us = ctypes.c_double()
+        L.check(L.load().bfs_ticket_latency_us(self._h, ctypes.c_uint64(ticket), ctypes.byref(us)), "latency")
+        return us.value
+
+    def stats(self) -> dict:
+        c = (ctypes.c_int64 * 3)()
+        L.check(L.load().bfs_server_stats(self._h, c), "bfs_server_stats")
+        return {"completed": c[0], "launches": c[1], "lanes_filled": c[2]}
+
+    def close(self):
+        if self._h:
+            L.load().bfs_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+            self._outs.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,79 @@
+"""The continuous-batching server: every query's levels equal the oracle's and are the
+same whether the query ran alone or in a mix with others on several resident graphs."""
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+from graphgen import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def _graphs(bfs):
+    out = []
+    for e in (workloads.RMAT[12].edges(), workloads.RMAT[15].edges(), graphgen.torus(64, seed=3000),
+              graphgen.erdos_renyi(3001, 9000, seed=8)):
+        out.append((e, oracle.build_csr(e.n, e.src, e.dst), bfs.Graph.from_edges(e.src, e.dst, e.n)))
+    return out
+
+
+def test_server_mix_equals_alone_and_oracle(gpu_lib):
+    bfs = gpu_lib
+    gs = _graphs(bfs)
+    srv = bfs.Server(hbm_budget_bytes=4 << 30, max_lanes=64)
+    slots = [srv.add_graph(g) for _, _, g in gs]
+    rng = np.random.default_rng(11)
+    queries = []
+    for q in range(300):
+        i = int(rng.integers(0, len(gs)))
+        e = gs[i][0]
+        root = int(graphgen.pick_roots(e, 40, 77 + i)[int(rng.integers(0, 40))])
+        queries.append((i, root))
+    # alone: one at a time
+    alone = {}
+    for i, root in queries[:12]:
+        out = np.empty(gs[i][0].n, np.int32)
+        t = srv.submit(slots[i], root, out)
+        assert srv.wait(t, 60000)
+        alone[(i, root)] = out
+    # mix: all at once
+    outs = []
+    for i, root in queries:
+        out = np.empty(gs[i][0].n, np.int32)
+        outs.append((i, root, out, srv.submit(slots[i], root, out)))
+    for i, root, out, t in outs:
+        assert srv.wait(t, 120000)
+        assert np.array_equal(out, oracle.levels(gs[i][1], root)), (i, root)
+        if (i, root) in alone:
+            assert np.array_equal(out, alone[(i, root)])
+        assert srv.latency_us(t) > 0
+    st = srv.stats()
+    assert st["completed"] == len(queries) + 12
+    assert st["lanes_filled"] > st["launches"]       # levels were shared by several queries
+    srv.close()
+
+
+def test_server_budget_limits_lanes(gpu_lib):
+    bfs = gpu_lib
+    e = workloads.RMAT[12].edges()
+    ref = oracle.build_csr(e.n, e.src, e.dst)
+    g = bfs.Graph.from_edges(e.src, e.dst, e.n)
+    with pytest.raises(bfs.BfsError):
+        bfs.Server(hbm_budget_bytes=1024).add_graph(g)
+    # masks (24n) plus room for two level rows (4n each)
+    srv = bfs.Server(hbm_budget_bytes=24 * e.n + 8 * e.n + (1 << 20) * 8, max_lanes=64)
+    slot = srv.add_graph(g)
+    roots = graphgen.pick_roots(e, 30, 5).tolist()
+    outs = [(r, np.empty(e.n, np.int32)) for r in roots]
+    ts = [srv.submit(slot, r, o) for r, o in outs]
+    for (r, o), t in zip(outs, ts):
+        assert srv.wait(t, 60000)
+        assert np.array_equal(o, oracle.levels(ref, r))
+    with pytest.raises(bfs.BfsError):
+        srv.submit(slot, e.n, np.empty(e.n, np.int32))
+    with pytest.raises(bfs.BfsError):
+        srv.submit(7, 0, np.empty(e.n, np.int32))
+    with pytest.raises(bfs.BfsError):
+        srv.poll(123456789)
+    srv.close()
