@@ -288,7 +288,10 @@ __global__ void __launch_bounds__(kMBlock, 2) bfs_multi_kernel(MultiParams p) {
     }
     int prev = 0;
     for (int it = 0;; it++) {
-        const int slot = it % 3, sfree = (it + 2) % 3;
+        // counters of iteration `it` accumulate in slot it % 3 and are read by
+        // every CTA after the closing barrier; the slot of iteration it + 1 is
+        // cleared now (its last readers passed a barrier of iteration it - 1)
+        const int slot = it % 3, sfree = (it + 1) % 3;
         if (blockIdx.x == 0 && threadIdx.x == 0) c->zero_slot(sfree);
         const int dir = ms_decide(p, prev, nf, mf, mu);
         if (dir == 0) {

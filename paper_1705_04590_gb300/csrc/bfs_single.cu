@@ -39,9 +39,17 @@
 namespace bfsk {
 
 constexpr int kBlock = 512;
-constexpr int kChunk = 1024;   // edges per top-down chunk task
+constexpr int kWarps = kBlock / 32;
+constexpr int kChunk = 256;    // edges per top-down chunk task
+constexpr int kStage = 256;    // per-warp shared-memory staging of next-queue entries
 constexpr int kLongRem = 32;   // bottom-up: rows with more ids left than this go warp-cooperative
-constexpr int kWPW = 2;        // bottom-up: bitmap words (32 vertices each) per warp iteration
+#ifndef BFS_BU_VPL
+#define BFS_BU_VPL 2
+#endif
+#ifndef BFS_MIN_BLOCKS
+#define BFS_MIN_BLOCKS 2
+#endif
+constexpr int kVPL = BFS_BU_VPL;  // bottom-up: compacted searchers per lane per round
 constexpr unsigned kFull = 0xffffffffu;
 
 struct Task {
@@ -93,19 +101,28 @@ __device__ __forceinline__ int decide_dir(const SingleParams& p, int prev, long 
 __device__ __forceinline__ long long gtid() { return (long long)blockIdx.x * blockDim.x + threadIdx.x; }
 __device__ __forceinline__ long long gthreads() { return (long long)gridDim.x * blockDim.x; }
 
+// Fill a[0..n) with -1, using 16-byte stores for the aligned body.
+__device__ void fill_minus_one(int* a, long long n) {
+    const long long tid = gtid(), nth = gthreads();
+    const long long head = ((16 - ((unsigned long long)a & 15)) & 15) / 4;
+    const long long h = head < n ? head : n;
+    if (tid < h) a[tid] = -1;
+    const long long body = (n - h) / 4;
+    int4* v = reinterpret_cast<int4*>(a + h);
+    const int4 m1 = make_int4(-1, -1, -1, -1);
+    for (long long i = tid; i < body; i += nth) v[i] = m1;
+    for (long long i = h + body * 4 + tid; i < n; i += nth) a[i] = -1;
+}
+
 // parent/level fill, completed bitmap = isolated vertices (+ root), clear both
-// frontier bitmaps.
+// frontier bitmaps.  The root's own entries are written after the barrier
+// that ends this phase.
 __device__ void init_phase(const SingleParams& p) {
     const long long tid = gtid(), nth = gthreads();
     const bool single = p.nroots == 1;
     const long long r = p.root0;
-    if (p.parent || p.level) {
-        for (long long v = tid; v < p.n; v += nth) {
-            const bool isr = single && v == r;
-            if (p.parent) p.parent[v] = isr ? (int)r : -1;
-            if (p.level) p.level[v] = isr ? 0 : -1;
-        }
-    }
+    if (p.parent) fill_minus_one(p.parent, p.n);
+    if (p.level) fill_minus_one(p.level, p.n);
     const long long rw = single ? (r >> 5) : -1;
     const unsigned rb = single ? (1u << (r & 31)) : 0u;
     for (long long w = tid; w < p.W; w += nth) {
@@ -139,9 +156,30 @@ __device__ void seed_roots_phase(const SingleParams& p) {
 
 // ------------------------------------------------------------------ top-down
 
-// Visit edge (u, v) for the whole warp (every lane calls; `act` masks).
-__device__ __forceinline__ void td_visit(const SingleParams& p, int d, int u, int v, bool act, int* qnext,
-                                         unsigned long long* tail, unsigned long long& acc_m) {
+// Per-warp staging of next-queue entries in shared memory, flushed to the
+// global queue in batches: the queue tail sees one atomicAdd per batch
+// instead of one per warp iteration with a claim.
+struct WarpStage {
+    int* buf;   // kStage entries of this warp's shared-memory slice
+    int cnt;    // warp-uniform fill level
+};
+
+__device__ __forceinline__ void stage_flush(WarpStage& st, int* qnext, unsigned long long* tail) {
+    if (st.cnt == 0) return;
+    __syncwarp();
+    unsigned long long base = 0;
+    if (lane_id() == 0) base = atomicAdd(tail, (unsigned long long)st.cnt);
+    base = __shfl_sync(kFull, base, 0);
+    for (int i = lane_id(); i < st.cnt; i += 32) qnext[base + i] = st.buf[i];
+    __syncwarp();
+    st.cnt = 0;
+}
+
+// Visit edge (u, v) for the whole warp (every lane calls; `act` masks): claim
+// v with an atomicOr on the visited bitmap; the winner records parent/level
+// and stages v for the next queue.
+__device__ __forceinline__ void td_visit(const SingleParams& p, int d, int u, int v, bool act, WarpStage& st,
+                                         int* qnext, unsigned long long* tail, unsigned long long& acc_m) {
     bool claimed = false;
     if (act) {
         const unsigned bit = 1u << (v & 31);
@@ -150,17 +188,23 @@ __device__ __forceinline__ void td_visit(const SingleParams& p, int d, int u, in
     }
     const unsigned cm = __ballot_sync(kFull, claimed);
     if (cm) {
-        const int leader = __ffs(cm) - 1;
-        unsigned long long base = 0;
-        if (lane_id() == leader) base = atomicAdd(tail, (unsigned long long)__popc(cm));
-        base = __shfl_sync(kFull, base, leader);
         if (claimed) {
-            qnext[base + __popc(cm & lanemask_lt())] = v;
+            st.buf[st.cnt + __popc(cm & lanemask_lt())] = v;
             if (p.parent) p.parent[v] = u;
             if (p.level) p.level[v] = d + 1;
             acc_m += (unsigned long long)(__ldg(p.off + v + 1) - __ldg(p.off + v));
         }
+        st.cnt += __popc(cm);
+        if (st.cnt > kStage - 32) stage_flush(st, qnext, tail);
     }
+}
+
+__device__ __forceinline__ WarpStage warp_stage() {
+    __shared__ int s_stage[kWarps][kStage];
+    WarpStage st;
+    st.buf = s_stage[threadIdx.x >> 5];
+    st.cnt = 0;
+    return st;
 }
 
 __device__ void td_phase(const SingleParams& p, int d, const int* qcur, long long nf, int* qnext, int snext,
@@ -168,6 +212,7 @@ __device__ void td_phase(const SingleParams& p, int d, const int* qcur, long lon
     const int lane = lane_id();
     const long long gw = gtid() >> 5, nw = gthreads() >> 5;
     unsigned long long* tail = &p.ctrl->tail[snext];
+    WarpStage st = warp_stage();
     for (long long base = gw * 32; base < nf; base += nw * 32) {
         const long long i = base + lane;
         int u = 0;
@@ -213,9 +258,10 @@ __device__ void td_phase(const SingleParams& p, int d, const int* qcur, long lon
             const int uj = __shfl_sync(kFull, u, j);
             const bool act = k < total;
             const int v = act ? __ldg(p.cols + sj + (k - exj)) : 0;
-            td_visit(p, d, uj, v, act, qnext, tail, acc_m);
+            td_visit(p, d, uj, v, act, st, qnext, tail, acc_m);
         }
     }
+    stage_flush(st, qnext, tail);
 }
 
 __device__ void task_phase(const SingleParams& p, int d, long long ntask, int* qnext, int snext,
@@ -223,6 +269,7 @@ __device__ void task_phase(const SingleParams& p, int d, long long ntask, int* q
     const int lane = lane_id();
     const long long gw = gtid() >> 5, nw = gthreads() >> 5;
     unsigned long long* tail = &p.ctrl->tail[snext];
+    WarpStage st = warp_stage();
     const long long nt = ntask < p.task_cap ? ntask : p.task_cap;
     for (long long t = gw; t < nt; t += nw) {
         const int4 raw = __ldcg(reinterpret_cast<const int4*>(p.tasks + t));
@@ -232,9 +279,10 @@ __device__ void task_phase(const SingleParams& p, int d, long long ntask, int* q
             const int k = k0 + lane;
             const bool act = k < len;
             const int v = act ? __ldg(p.cols + start + k) : 0;
-            td_visit(p, d, u, v, act, qnext, tail, acc_m);
+            td_visit(p, d, u, v, act, st, qnext, tail, acc_m);
         }
     }
+    stage_flush(st, qnext, tail);
 }
 
 // parent_mode MIN_ID after a top-down level: each newly found v takes the
@@ -299,141 +347,175 @@ __device__ __forceinline__ bool in_frontier(const unsigned* f, int v) {
     return (__ldcg(f + (v >> 5)) >> (v & 31)) & 1u;
 }
 
+// A warp takes 32 completed-bitmap words (1024 vertices) at a time, compacts
+// the unvisited ones with a warp prefix sum, and gives every lane kVPL of them
+// per round, so lanes stay busy however sparse the unvisited set is.
+// Found vertices are collected per word in shared memory and written as whole
+// next-frontier / completed words (the warp owns its 32 words).
 __device__ void bu_phase(const SingleParams& p, int d, const unsigned* fcur, unsigned* fnext,
                          unsigned long long& acc_n, unsigned long long& acc_m, unsigned long long& acc_sc,
                          unsigned long long& acc_ex) {
-    const int lane = lane_id();
+    __shared__ unsigned s_next[kWarps][32];
+    const int lane = lane_id(), wib = threadIdx.x >> 5;
     const long long gw = gtid() >> 5, nw = gthreads() >> 5;
-    for (long long w0 = gw * kWPW; w0 < p.W; w0 += nw * kWPW) {
-        unsigned cw[kWPW];
-        long long base[kWPW];   // row start rounded down to 4 ids (16 bytes)
-        int lead[kWPW];         // s - base (0..3)
-        int len[kWPW];          // degree (0 when visited / not searching)
-        int nxt[kWPW];          // next unread position, relative to base
-        int hit[kWPW];          // position of the first frontier neighbour relative to s, or -1
-        int pv[kWPW];
+    const long long nchunk = (p.W + 31) / 32;
+    s_next[wib][lane] = 0u;
+    __syncwarp();
+    for (long long ch = gw; ch < nchunk; ch += nw) {
+        const long long w = ch * 32 + lane;
+        const unsigned cw = (w < p.W) ? __ldcg(p.visited + w) : kFull;
+        const unsigned todo = ~cw;
+        const int cnt = __popc(todo);
+        const int incl = warp_inclusive_scan(cnt);
+        const int T = __shfl_sync(kFull, incl, 31);
+        const int excl = incl - cnt;
+        for (int base = 0; base < T; base += 32 * kVPL) {
+            long long u[kVPL];      // vertex id (valid when len > 0)
+            long long rb[kVPL];     // row start rounded down to 4 ids (16 bytes)
+            int lead[kVPL];         // s - rb (0..3)
+            int len[kVPL];          // degree (0: no searcher in this slot)
+            int nxt[kVPL];          // next unread position, relative to rb
+            int hit[kVPL];          // first frontier neighbour, relative to s, or -1
+            int pv[kVPL];
+            int wj[kVPL], bj[kVPL];
 #pragma unroll
-        for (int j = 0; j < kWPW; j++) cw[j] = (w0 + j < p.W) ? __ldcg(p.visited + w0 + j) : kFull;
+            for (int q = 0; q < kVPL; q++) {
+                const int k = base + q * 32 + lane;
+                int j = 0;
 #pragma unroll
-        for (int j = 0; j < kWPW; j++) {
-            base[j] = 0;
-            lead[j] = 0;
-            len[j] = 0;
-            nxt[j] = 0;
-            hit[j] = -1;
-            pv[j] = -1;
-            if (!((cw[j] >> lane) & 1u)) {
-                const long long u = (w0 + j) * 32 + lane;
-                const long long s = __ldg(p.off + u);
-                len[j] = (int)(__ldg(p.off + u + 1) - s);
-                base[j] = s & ~3LL;
-                lead[j] = (int)(s - base[j]);
-                nxt[j] = 0;
-            }
-        }
-        // thread-wise rounds of 8 ids (two int4 loads, eight bitmap probes in flight)
-        for (int r = 0;; r++) {
-            bool need[kWPW];
-            int4 xa[kWPW], xb[kWPW];
-            bool any = false;
-#pragma unroll
-            for (int j = 0; j < kWPW; j++) {
-                const int endrel = lead[j] + len[j];
-                need[j] = len[j] > 0 && hit[j] < 0 && nxt[j] < endrel && (r == 0 || endrel - nxt[j] <= kLongRem);
-                if (need[j]) {
-                    const int4* q = reinterpret_cast<const int4*>(p.cols + base[j] + nxt[j]);
-                    xa[j] = __ldg(q);
-                    xb[j] = (nxt[j] + 4 < endrel) ? __ldg(q + 1) : make_int4(0, 0, 0, 0);
-                    any = true;
+                for (int step = 16; step >= 1; step >>= 1) {
+                    const int c = __shfl_sync(kFull, incl, j + step - 1);
+                    if (c <= k) j += step;
+                }
+                const int exj = __shfl_sync(kFull, excl, j);
+                const unsigned tj = __shfl_sync(kFull, todo, j);
+                wj[q] = j;
+                bj[q] = 0;
+                u[q] = 0;
+                rb[q] = 0;
+                lead[q] = 0;
+                len[q] = 0;
+                nxt[q] = 0;
+                hit[q] = -1;
+                pv[q] = -1;
+                if (k < T) {
+                    bj[q] = (int)__fns(tj, 0, k - exj + 1);
+                    u[q] = (ch * 32 + j) * 32 + bj[q];
+                    const long long s0 = __ldg(p.off + u[q]);
+                    len[q] = (int)(__ldg(p.off + u[q] + 1) - s0);
+                    rb[q] = s0 & ~3LL;
+                    lead[q] = (int)(s0 - rb[q]);
                 }
             }
-            if (!__any_sync(kFull, any)) break;
+            // thread-wise rounds of 8 ids (two int4 loads, eight bitmap probes in flight)
+            for (int r = 0;; r++) {
+                bool need[kVPL];
+                int4 xa[kVPL], xb[kVPL];
+                bool any = false;
 #pragma unroll
-            for (int j = 0; j < kWPW; j++) {
-                if (need[j]) {
-                    const int ids[8] = {xa[j].x, xa[j].y, xa[j].z, xa[j].w, xb[j].x, xb[j].y, xb[j].z, xb[j].w};
-                    unsigned hb = 0;
+                for (int q = 0; q < kVPL; q++) {
+                    const int endrel = lead[q] + len[q];
+                    need[q] = len[q] > 0 && hit[q] < 0 && nxt[q] < endrel &&
+                              (r == 0 || endrel - nxt[q] <= kLongRem);
+                    if (need[q]) {
+                        const int4* src = reinterpret_cast<const int4*>(p.cols + rb[q] + nxt[q]);
+                        xa[q] = __ldg(src);
+                        xb[q] = (nxt[q] + 4 < endrel) ? __ldg(src + 1) : make_int4(0, 0, 0, 0);
+                        any = true;
+                    }
+                }
+                if (!__any_sync(kFull, any)) break;
 #pragma unroll
-                    for (int t = 0; t < 8; t++) {
-                        const int rel = nxt[j] + t;
-                        if (rel >= lead[j] && rel < lead[j] + len[j] && in_frontier(fcur, ids[t])) hb |= 1u << t;
+                for (int q = 0; q < kVPL; q++) {
+                    if (need[q]) {
+                        const int ids[8] = {xa[q].x, xa[q].y, xa[q].z, xa[q].w, xb[q].x, xb[q].y, xb[q].z, xb[q].w};
+                        unsigned hb = 0;
+#pragma unroll
+                        for (int t = 0; t < 8; t++) {
+                            const int rel = nxt[q] + t;
+                            if (rel >= lead[q] && rel < lead[q] + len[q] && in_frontier(fcur, ids[t])) hb |= 1u << t;
+                        }
+                        if (hb) {
+                            const int t = __ffs(hb) - 1;
+                            hit[q] = nxt[q] + t - lead[q];
+                            pv[q] = ids[t];
+                        }
+                        nxt[q] += 8;
                     }
-                    if (hb) {
-                        const int t = __ffs(hb) - 1;
-                        hit[j] = nxt[j] + t - lead[j];
-                        pv[j] = ids[t];
+                }
+            }
+            // warp-cooperative continuation of long rows, one vertex at a time
+#pragma unroll
+            for (int q = 0; q < kVPL; q++) {
+                unsigned pend = __ballot_sync(kFull, len[q] > 0 && hit[q] < 0 && nxt[q] < lead[q] + len[q]);
+                while (pend) {
+                    const int L = __ffs(pend) - 1;
+                    pend &= pend - 1;
+                    const long long b = __shfl_sync(kFull, rb[q], L);
+                    const int from = __shfl_sync(kFull, nxt[q], L);
+                    const int to = __shfl_sync(kFull, lead[q] + len[q], L);
+                    const int ld = __shfl_sync(kFull, lead[q], L);
+                    int fpos = -1, fv = -1;
+                    for (int q0 = from; q0 < to; q0 += 32) {
+                        const int qq = q0 + lane;
+                        int v = 0;
+                        bool h = false;
+                        if (qq < to) {
+                            v = __ldg(p.cols + b + qq);
+                            h = in_frontier(fcur, v);
+                        }
+                        const unsigned hm = __ballot_sync(kFull, h);
+                        if (hm) {
+                            const int f = __ffs(hm) - 1;
+                            fpos = q0 + f - ld;
+                            fv = __shfl_sync(kFull, v, f);
+                            break;
+                        }
                     }
-                    nxt[j] += 8;
+                    if (lane == L) {
+                        hit[q] = fpos;
+                        pv[q] = fv;
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kVPL; q++) {
+                if (len[q] > 0) {
+                    acc_sc += 1;
+                    if (hit[q] >= 0) {
+                        acc_ex += (unsigned long long)(hit[q] + 1);
+                        acc_m += (unsigned long long)len[q];
+                        if (p.parent) p.parent[u[q]] = pv[q];
+                        if (p.level) p.level[u[q]] = d + 1;
+                        atomicOr(&s_next[wib][wj[q]], 1u << bj[q]);
+                    } else {
+                        acc_ex += (unsigned long long)len[q];
+                    }
                 }
             }
         }
-        // warp-cooperative continuation of long rows, one vertex at a time
-#pragma unroll
-        for (int j = 0; j < kWPW; j++) {
-            unsigned pend = __ballot_sync(kFull, len[j] > 0 && hit[j] < 0 && nxt[j] < lead[j] + len[j]);
-            while (pend) {
-                const int L = __ffs(pend) - 1;
-                pend &= pend - 1;
-                const long long b = __shfl_sync(kFull, base[j], L);
-                const int from = __shfl_sync(kFull, nxt[j], L);
-                const int to = __shfl_sync(kFull, lead[j] + len[j], L);
-                const int ld = __shfl_sync(kFull, lead[j], L);
-                int fpos = -1, fv = -1;
-                for (int q0 = from; q0 < to; q0 += 32) {
-                    const int q = q0 + lane;
-                    int v = 0;
-                    bool h = false;
-                    if (q < to) {
-                        v = __ldg(p.cols + b + q);
-                        h = in_frontier(fcur, v);
-                    }
-                    const unsigned hm = __ballot_sync(kFull, h);
-                    if (hm) {
-                        const int f = __ffs(hm) - 1;
-                        fpos = q0 + f - ld;
-                        fv = __shfl_sync(kFull, v, f);
-                        break;
-                    }
-                }
-                if (lane == L) {
-                    hit[j] = fpos;
-                    pv[j] = fv;
-                }
-            }
+        __syncwarp();
+        const unsigned nx = s_next[wib][lane];
+        if (w < p.W) {
+            fnext[w] = nx;
+            if (nx) p.visited[w] = cw | nx;
         }
-        // outputs: parent/level, next-frontier word, completed word, counters
-#pragma unroll
-        for (int j = 0; j < kWPW; j++) {
-            const long long w = w0 + j;
-            if (w >= p.W) break;
-            const bool act = len[j] > 0;
-            const bool found = act && hit[j] >= 0;
-            if (act) {
-                acc_sc += 1;
-                acc_ex += (unsigned long long)(found ? hit[j] + 1 : len[j]);
-            }
-            const unsigned fm = __ballot_sync(kFull, found);
-            if (found) {
-                const long long u = w * 32 + lane;
-                if (p.parent) p.parent[u] = pv[j];
-                if (p.level) p.level[u] = d + 1;
-                acc_m += (unsigned long long)len[j];
-            }
-            if (lane == 0) {
-                fnext[w] = fm;
-                if (fm) p.visited[w] = cw[j] | fm;
-                acc_n += (unsigned long long)__popc(fm);
-            }
-        }
+        acc_n += (unsigned long long)__popc(nx);
+        s_next[wib][lane] = 0u;
+        __syncwarp();
     }
 }
 
 // ------------------------------------------------------------------ kernel
 
-__global__ void __launch_bounds__(kBlock, 2) bfs_single_kernel(SingleParams p) {
+__global__ void __launch_bounds__(kBlock, BFS_MIN_BLOCKS) bfs_single_kernel(SingleParams p) {
     Ctrl* c = p.ctrl;
     init_phase(p);
     if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
+    if (p.nroots == 1 && gtid() == 0) {
+        if (p.parent) p.parent[p.root0] = p.root0;
+        if (p.level) p.level[p.root0] = 0;
+    }
     if (p.nroots > 1) {
         seed_roots_phase(p);
         if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
@@ -539,7 +621,7 @@ bfs_status single_prepare(bfs_graph* g, cudaStream_t s) {
     SingleWork& w = g->single;
     if (w.ready) return BFS_OK;
     const long long n = g->n, W = g->W;
-    const long long task_cap = g->nnz / bfsk::kChunk + g->nnz / 64 + 1024;
+    const long long task_cap = g->nnz / bfsk::kChunk + g->nnz / 64 + 1024;  // big degree is >= 64
     const int rec_cap = 1 << 16;
     struct Item { void** p; size_t bytes; };
     Item items[] = {
@@ -618,7 +700,7 @@ bfs_status single_launch(bfs_graph* g, const int32_t* roots_host, int32_t k, int
     p.alpha = opt.alpha;
     p.beta = opt.beta;
     p.parent_mode = opt.parent_mode;
-    p.big_deg = opt.td_big_degree > 0 ? opt.td_big_degree : 128;
+    p.big_deg = opt.td_big_degree > 0 ? opt.td_big_degree : 96;
     p.seed = opt.seed;
     p.timeout_ns = (unsigned long long)(opt.timeout_ms > 0 ? opt.timeout_ms : 10000) * 1000000ull;
     p.expected = (unsigned)w.grid + (unsigned)(opt.debug_barrier_extra > 0 ? opt.debug_barrier_extra : 0);
