@@ -173,15 +173,27 @@ bfs_status bfs_graph_csr(const bfs_graph* g, const int64_t** row_offsets, const 
  */
 bfs_status bfs_graph_copy_csr(const bfs_graph* g, int64_t* offsets_out, int32_t* cols_out, void* stream);
 
-/* Device pointers of the DCSC tiles (see bfs_dcsc_layout); INVALID if not built. */
+/*
+ * Device pointers of the DCSC tiles built with BFS_FLAG_BUILD_DCSC ("Graph
+ * Representation": IR row ids, JC ids of non-empty columns, CP column
+ * pointers).  Vertices are cut into num_blocks blocks of block_size
+ * consecutive ids; tile (i, j) holds entries with row in block i and column
+ * in block j, stored i-major as DCSC over its columns:
+ *   tile_ptr[i*p + j] .. tile_ptr[i*p + j + 1]   range of JC/CP entries
+ *   jc[x]       column - j*block_size, ascending within the tile
+ *   cp[x] .. cp[x+1]   range of ir entries of that column
+ *   ir[e]       row - i*block_size, ascending within a column
+ * Owned by the graph; valid until bfs_graph_destroy.  INVALID if not built.
+ */
 typedef struct {
-    int32_t num_blocks;          /* p_c column blocks */
-    int32_t block_shift;         /* block of column v = v >> block_shift */
-    const int64_t* tile_ptr;     /* [num_blocks+1] start of each tile in jc/cp (entries) */
-    const int32_t* jc;           /* non-empty row ids of each tile, ascending */
-    const int64_t* cp;           /* [total rows + num_blocks] edge start per listed row (tile-local end sentinel) */
-    const int32_t* ir;           /* column ids (global), rows sorted ascending */
-    int64_t total_rows;          /* sum of non-empty rows over tiles (= entries of jc) */
+    int32_t num_blocks;          /* p */
+    int32_t reserved;
+    int64_t block_size;          /* vertices per block (multiple of 32) */
+    const int64_t* tile_ptr;     /* [p*p + 1] */
+    const int32_t* jc;           /* [nzc] */
+    const int64_t* cp;           /* [nzc + 1] */
+    const int32_t* ir;           /* [nnz] */
+    int64_t nzc;                 /* non-empty (tile, column) pairs */
 } bfs_dcsc_layout;
 bfs_status bfs_graph_dcsc(const bfs_graph* g, bfs_dcsc_layout* out);
 

@@ -42,8 +42,8 @@ class Stats(ctypes.Structure):
 
 
 class DcscLayout(ctypes.Structure):
-    _fields_ = [("num_blocks", c_i32), ("block_shift", c_i32), ("tile_ptr", c_vp), ("jc", c_vp), ("cp", c_vp),
-                ("ir", c_vp), ("total_rows", c_i64)]
+    _fields_ = [("num_blocks", c_i32), ("reserved", c_i32), ("block_size", c_i64), ("tile_ptr", c_vp), ("jc", c_vp),
+                ("cp", c_vp), ("ir", c_vp), ("nzc", c_i64)]
 
 
 # (name, restype, argtypes) of every entry point in include/bfs.h

@@ -54,12 +54,7 @@ static void destroy_graph(bfs_graph* g) {
     cudaDeviceSynchronize();
     single_release(g);
     multi_release(g);
-    if (g->dcsc.built) {
-        g->mem.release(g->dcsc.tile_ptr, 0, nullptr);
-        g->mem.release(g->dcsc.jc, 0, nullptr);
-        g->mem.release(g->dcsc.cp, 0, nullptr);
-        g->mem.release(g->dcsc.ir, 0, nullptr);
-    }
+    release_dcsc_tiles(g);
     g->mem.release(g->offsets, sizeof(int64_t) * (size_t)(g->n + 1), nullptr);
     g->mem.release(g->cols, sizeof(int32_t) * (size_t)(g->nnz + kColPad), nullptr);
     g->mem.release(g->isolated, sizeof(uint32_t) * (size_t)g->W, nullptr);
@@ -225,12 +220,13 @@ bfs_status bfs_graph_dcsc(const bfs_graph* g, bfs_dcsc_layout* out) {
     if (!g || !out) return fail(BFS_ERR_INVALID, "NULL argument");
     if (!g->dcsc.built) return fail(BFS_ERR_INVALID, "graph was built without BFS_FLAG_BUILD_DCSC");
     out->num_blocks = g->dcsc.num_blocks;
-    out->block_shift = g->dcsc.block_shift;
+    out->reserved = 0;
+    out->block_size = g->dcsc.block_size;
     out->tile_ptr = g->dcsc.tile_ptr;
     out->jc = g->dcsc.jc;
     out->cp = g->dcsc.cp;
     out->ir = g->dcsc.ir;
-    out->total_rows = g->dcsc.total_rows;
+    out->nzc = g->dcsc.nzc;
     return BFS_OK;
 }
 

@@ -69,13 +69,14 @@ struct MultiWork {
 
 struct DcscTiles {
     bool built = false;
-    int num_blocks = 0;
-    int block_shift = 0;
-    int64_t* tile_ptr = nullptr;   // [num_blocks+1]
-    int32_t* jc = nullptr;         // [total_rows]
-    int64_t* cp = nullptr;         // [total_rows + num_blocks]
-    int32_t* ir = nullptr;         // [nnz + pad]
-    int64_t total_rows = 0;
+    int num_blocks = 0;            // p
+    long long block_size = 0;      // B (multiple of 32)
+    int bits = 0;                  // bits of B
+    int64_t* tile_ptr = nullptr;   // [p*p+1]
+    int32_t* jc = nullptr;         // [nzc] column within block
+    int64_t* cp = nullptr;         // [nzc+1] IR position of each column
+    int32_t* ir = nullptr;         // [nnz + kColPad] row within block
+    long long nzc = 0;
     size_t bytes = 0;
 };
 
@@ -113,6 +114,7 @@ bfs_status build_csr_from_csr(bfs_graph* g, const int64_t* off, const int32_t* c
                               bool check_symmetry, cudaStream_t s);
 bfs_status build_isolated_bitmap(bfs_graph* g, cudaStream_t s);
 bfs_status build_dcsc_tiles(bfs_graph* g, cudaStream_t s);
+void release_dcsc_tiles(bfs_graph* g);
 
 // bfs_single.cu
 bfs_status single_prepare(bfs_graph* g, cudaStream_t s);

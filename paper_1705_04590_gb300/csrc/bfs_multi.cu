@@ -151,6 +151,7 @@ __device__ void ms_bu_phase(const MultiParams& p, unsigned long long active) {
             if (miss) {
                 s = __ldg(p.off + u);
                 e = __ldg(p.off + u + 1);
+                pos = s;   // a degree-0 row has nothing left to scan
             }
         }
         if (miss && e > s) {

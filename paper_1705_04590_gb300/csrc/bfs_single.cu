@@ -42,14 +42,9 @@ constexpr int kBlock = 512;
 constexpr int kWarps = kBlock / 32;
 constexpr int kChunk = 256;    // edges per top-down chunk task
 constexpr int kStage = 256;    // per-warp shared-memory staging of next-queue entries
-constexpr int kLongRem = 32;   // bottom-up: rows with more ids left than this go warp-cooperative
-#ifndef BFS_BU_VPL
-#define BFS_BU_VPL 2
-#endif
 #ifndef BFS_MIN_BLOCKS
 #define BFS_MIN_BLOCKS 2
 #endif
-constexpr int kVPL = BFS_BU_VPL;  // bottom-up: compacted searchers per lane per round
 constexpr unsigned kFull = 0xffffffffu;
 
 struct Task {
@@ -164,13 +159,20 @@ struct WarpStage {
     int cnt;    // warp-uniform fill level
 };
 
-__device__ __forceinline__ void stage_flush(WarpStage& st, int* qnext, unsigned long long* tail) {
+__device__ __forceinline__ void stage_flush(const SingleParams& p, WarpStage& st, int* qnext,
+                                            unsigned long long* tail, unsigned long long& acc_m) {
     if (st.cnt == 0) return;
     __syncwarp();
     unsigned long long base = 0;
     if (lane_id() == 0) base = atomicAdd(tail, (unsigned long long)st.cnt);
     base = __shfl_sync(kFull, base, 0);
-    for (int i = lane_id(); i < st.cnt; i += 32) qnext[base + i] = st.buf[i];
+    for (int i = lane_id(); i < st.cnt; i += 32) {
+        const int v = st.buf[i];
+        qnext[base + i] = v;
+        // degree sum of the next frontier (the switch rule's m_f), read here in
+        // batches rather than on the claim path
+        acc_m += (unsigned long long)(__ldg(p.off + v + 1) - __ldg(p.off + v));
+    }
     __syncwarp();
     st.cnt = 0;
 }
@@ -192,10 +194,9 @@ __device__ __forceinline__ void td_visit(const SingleParams& p, int d, int u, in
             st.buf[st.cnt + __popc(cm & lanemask_lt())] = v;
             if (p.parent) p.parent[v] = u;
             if (p.level) p.level[v] = d + 1;
-            acc_m += (unsigned long long)(__ldg(p.off + v + 1) - __ldg(p.off + v));
         }
         st.cnt += __popc(cm);
-        if (st.cnt > kStage - 32) stage_flush(st, qnext, tail);
+        if (st.cnt > kStage - 32) stage_flush(p, st, qnext, tail, acc_m);
     }
 }
 
@@ -261,7 +262,7 @@ __device__ void td_phase(const SingleParams& p, int d, const int* qcur, long lon
             td_visit(p, d, uj, v, act, st, qnext, tail, acc_m);
         }
     }
-    stage_flush(st, qnext, tail);
+    stage_flush(p, st, qnext, tail, acc_m);
 }
 
 __device__ void task_phase(const SingleParams& p, int d, long long ntask, int* qnext, int snext,
@@ -282,7 +283,7 @@ __device__ void task_phase(const SingleParams& p, int d, long long ntask, int* q
             td_visit(p, d, u, v, act, st, qnext, tail, acc_m);
         }
     }
-    stage_flush(st, qnext, tail);
+    stage_flush(p, st, qnext, tail, acc_m);
 }
 
 // parent_mode MIN_ID after a top-down level: each newly found v takes the
@@ -347,14 +348,17 @@ __device__ __forceinline__ bool in_frontier(const unsigned* f, int v) {
     return (__ldcg(f + (v >> 5)) >> (v & 31)) & 1u;
 }
 
-// A warp takes 32 completed-bitmap words (1024 vertices) at a time, compacts
-// the unvisited ones with a warp prefix sum, and gives every lane kVPL of them
-// per round, so lanes stay busy however sparse the unvisited set is.
-// Found vertices are collected per word in shared memory and written as whole
-// next-frontier / completed words (the warp owns its 32 words).
-__device__ void bu_phase(const SingleParams& p, int d, const unsigned* fcur, unsigned* fnext,
-                         unsigned long long& acc_n, unsigned long long& acc_m, unsigned long long& acc_sc,
-                         unsigned long long& acc_ex) {
+// Bottom-up, phase A.  A warp takes 32 completed-bitmap words (1024
+// vertices) at a time and compacts the unvisited ones with a warp prefix sum;
+// each lane then takes one searcher per round: its row offsets (prefetched one
+// round ahead), one aligned window of 8 ids (two int4 loads) and 8 frontier
+// probes.  A searcher whose row continues past the window without a hit goes
+// on the long list (phase B).  Found vertices are collected per word in shared
+// memory and written as whole next-frontier / completed words (the warp owns
+// its 32 words, so no atomics).
+__device__ void bu_phase_a(const SingleParams& p, int d, const unsigned* fcur, unsigned* fnext, int* longlist,
+                           unsigned long long* longcnt, unsigned long long& acc_n, unsigned long long& acc_m,
+                           unsigned long long& acc_sc, unsigned long long& acc_ex) {
     __shared__ unsigned s_next[kWarps][32];
     const int lane = lane_id(), wib = threadIdx.x >> 5;
     const long long gw = gtid() >> 5, nw = gthreads() >> 5;
@@ -369,130 +373,80 @@ __device__ void bu_phase(const SingleParams& p, int d, const unsigned* fcur, uns
         const int incl = warp_inclusive_scan(cnt);
         const int T = __shfl_sync(kFull, incl, 31);
         const int excl = incl - cnt;
-        for (int base = 0; base < T; base += 32 * kVPL) {
-            long long u[kVPL];      // vertex id (valid when len > 0)
-            long long rb[kVPL];     // row start rounded down to 4 ids (16 bytes)
-            int lead[kVPL];         // s - rb (0..3)
-            int len[kVPL];          // degree (0: no searcher in this slot)
-            int nxt[kVPL];          // next unread position, relative to rb
-            int hit[kVPL];          // first frontier neighbour, relative to s, or -1
-            int pv[kVPL];
-            int wj[kVPL], bj[kVPL];
+        // searcher k of this chunk -> (word j, bit b, vertex u)
+        auto locate = [&](int k, int& j, int& b, long long& u) {
+            j = 0;
 #pragma unroll
-            for (int q = 0; q < kVPL; q++) {
-                const int k = base + q * 32 + lane;
-                int j = 0;
+            for (int step = 16; step >= 1; step >>= 1) {
+                const int c = __shfl_sync(kFull, incl, j + step - 1);
+                if (c <= k) j += step;
+            }
+            const int exj = __shfl_sync(kFull, excl, j);
+            const unsigned tj = __shfl_sync(kFull, todo, j);
+            b = 0;
+            u = -1;
+            if (k < T) {
+                b = (int)__fns(tj, 0, k - exj + 1);
+                u = (ch * 32 + j) * 32 + b;
+            }
+        };
+        int j0, b0;
+        long long u0;
+        locate(lane, j0, b0, u0);
+        long long s0 = 0, e0 = 0;
+        if (u0 >= 0) {
+            s0 = __ldg(p.off + u0);
+            e0 = __ldg(p.off + u0 + 1);
+        }
+        for (int base = 0; base < T; base += 32) {
+            // prefetch the next round's row offsets
+            int j1, b1;
+            long long u1, s1 = 0, e1 = 0;
+            locate(base + 32 + lane, j1, b1, u1);
+            if (u1 >= 0) {
+                s1 = __ldg(p.off + u1);
+                e1 = __ldg(p.off + u1 + 1);
+            }
+            bool to_long = false;
+            if (u0 >= 0) {
+                const long long rb = s0 & ~3LL;
+                const int4* src = reinterpret_cast<const int4*>(p.cols + rb);
+                const int4 xa = __ldg(src);
+                const int4 xb = (rb + 4 < e0) ? __ldg(src + 1) : make_int4(0, 0, 0, 0);
+                const int ids[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
+                unsigned hb = 0;
 #pragma unroll
-                for (int step = 16; step >= 1; step >>= 1) {
-                    const int c = __shfl_sync(kFull, incl, j + step - 1);
-                    if (c <= k) j += step;
+                for (int t = 0; t < 8; t++) {
+                    const long long q = rb + t;
+                    if (q >= s0 && q < e0 && in_frontier(fcur, ids[t])) hb |= 1u << t;
                 }
-                const int exj = __shfl_sync(kFull, excl, j);
-                const unsigned tj = __shfl_sync(kFull, todo, j);
-                wj[q] = j;
-                bj[q] = 0;
-                u[q] = 0;
-                rb[q] = 0;
-                lead[q] = 0;
-                len[q] = 0;
-                nxt[q] = 0;
-                hit[q] = -1;
-                pv[q] = -1;
-                if (k < T) {
-                    bj[q] = (int)__fns(tj, 0, k - exj + 1);
-                    u[q] = (ch * 32 + j) * 32 + bj[q];
-                    const long long s0 = __ldg(p.off + u[q]);
-                    len[q] = (int)(__ldg(p.off + u[q] + 1) - s0);
-                    rb[q] = s0 & ~3LL;
-                    lead[q] = (int)(s0 - rb[q]);
+                acc_sc += 1;
+                if (hb) {
+                    const int t = __ffs(hb) - 1;
+                    acc_ex += (unsigned long long)(rb + t - s0 + 1);
+                    acc_m += (unsigned long long)(e0 - s0);
+                    if (p.parent) p.parent[u0] = ids[t];
+                    if (p.level) p.level[u0] = d + 1;
+                    atomicOr(&s_next[wib][j0], 1u << b0);
+                } else if (rb + 8 < e0) {
+                    to_long = true;       // examinations counted by phase B
+                } else {
+                    acc_ex += (unsigned long long)(e0 - s0);
                 }
             }
-            // thread-wise rounds of 8 ids (two int4 loads, eight bitmap probes in flight)
-            for (int r = 0;; r++) {
-                bool need[kVPL];
-                int4 xa[kVPL], xb[kVPL];
-                bool any = false;
-#pragma unroll
-                for (int q = 0; q < kVPL; q++) {
-                    const int endrel = lead[q] + len[q];
-                    need[q] = len[q] > 0 && hit[q] < 0 && nxt[q] < endrel &&
-                              (r == 0 || endrel - nxt[q] <= kLongRem);
-                    if (need[q]) {
-                        const int4* src = reinterpret_cast<const int4*>(p.cols + rb[q] + nxt[q]);
-                        xa[q] = __ldg(src);
-                        xb[q] = (nxt[q] + 4 < endrel) ? __ldg(src + 1) : make_int4(0, 0, 0, 0);
-                        any = true;
-                    }
-                }
-                if (!__any_sync(kFull, any)) break;
-#pragma unroll
-                for (int q = 0; q < kVPL; q++) {
-                    if (need[q]) {
-                        const int ids[8] = {xa[q].x, xa[q].y, xa[q].z, xa[q].w, xb[q].x, xb[q].y, xb[q].z, xb[q].w};
-                        unsigned hb = 0;
-#pragma unroll
-                        for (int t = 0; t < 8; t++) {
-                            const int rel = nxt[q] + t;
-                            if (rel >= lead[q] && rel < lead[q] + len[q] && in_frontier(fcur, ids[t])) hb |= 1u << t;
-                        }
-                        if (hb) {
-                            const int t = __ffs(hb) - 1;
-                            hit[q] = nxt[q] + t - lead[q];
-                            pv[q] = ids[t];
-                        }
-                        nxt[q] += 8;
-                    }
-                }
+            // long-list append, one atomicAdd per warp round with entries
+            const unsigned lm = __ballot_sync(kFull, to_long);
+            if (lm) {
+                unsigned long long lb = 0;
+                if (lane == 0) lb = atomicAdd(longcnt, (unsigned long long)__popc(lm));
+                lb = __shfl_sync(kFull, lb, 0);
+                if (to_long) longlist[lb + __popc(lm & lanemask_lt())] = (int)u0;
             }
-            // warp-cooperative continuation of long rows, one vertex at a time
-#pragma unroll
-            for (int q = 0; q < kVPL; q++) {
-                unsigned pend = __ballot_sync(kFull, len[q] > 0 && hit[q] < 0 && nxt[q] < lead[q] + len[q]);
-                while (pend) {
-                    const int L = __ffs(pend) - 1;
-                    pend &= pend - 1;
-                    const long long b = __shfl_sync(kFull, rb[q], L);
-                    const int from = __shfl_sync(kFull, nxt[q], L);
-                    const int to = __shfl_sync(kFull, lead[q] + len[q], L);
-                    const int ld = __shfl_sync(kFull, lead[q], L);
-                    int fpos = -1, fv = -1;
-                    for (int q0 = from; q0 < to; q0 += 32) {
-                        const int qq = q0 + lane;
-                        int v = 0;
-                        bool h = false;
-                        if (qq < to) {
-                            v = __ldg(p.cols + b + qq);
-                            h = in_frontier(fcur, v);
-                        }
-                        const unsigned hm = __ballot_sync(kFull, h);
-                        if (hm) {
-                            const int f = __ffs(hm) - 1;
-                            fpos = q0 + f - ld;
-                            fv = __shfl_sync(kFull, v, f);
-                            break;
-                        }
-                    }
-                    if (lane == L) {
-                        hit[q] = fpos;
-                        pv[q] = fv;
-                    }
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < kVPL; q++) {
-                if (len[q] > 0) {
-                    acc_sc += 1;
-                    if (hit[q] >= 0) {
-                        acc_ex += (unsigned long long)(hit[q] + 1);
-                        acc_m += (unsigned long long)len[q];
-                        if (p.parent) p.parent[u[q]] = pv[q];
-                        if (p.level) p.level[u[q]] = d + 1;
-                        atomicOr(&s_next[wib][wj[q]], 1u << bj[q]);
-                    } else {
-                        acc_ex += (unsigned long long)len[q];
-                    }
-                }
-            }
+            j0 = j1;
+            b0 = b1;
+            u0 = u1;
+            s0 = s1;
+            e0 = e1;
         }
         __syncwarp();
         const unsigned nx = s_next[wib][lane];
@@ -503,6 +457,53 @@ __device__ void bu_phase(const SingleParams& p, int d, const unsigned* fcur, uns
         acc_n += (unsigned long long)__popc(nx);
         s_next[wib][lane] = 0u;
         __syncwarp();
+    }
+}
+
+// Bottom-up, phase B: the long list, one warp per searcher, 32 ids per step in
+// row order, stopping at the first frontier neighbour (ballot: lowest lane =
+// first position, so parents stay the minimum-id ones).  Next-frontier and
+// completed words are shared across warps here, hence atomicOr.
+__device__ void bu_phase_b(const SingleParams& p, int d, const unsigned* fcur, unsigned* fnext, const int* longlist,
+                           long long nlong, unsigned long long& acc_n, unsigned long long& acc_m,
+                           unsigned long long& acc_ex) {
+    const int lane = lane_id();
+    const long long gw = gtid() >> 5, nw = gthreads() >> 5;
+    for (long long i = gw; i < nlong; i += nw) {
+        const int u = __ldcg(longlist + i);
+        const long long s0 = __ldg(p.off + u), e0 = __ldg(p.off + u + 1);
+        const long long from = (s0 & ~3LL) + 8;
+        long long hitpos = -1;
+        int pv = -1;
+        for (long long q0 = from; q0 < e0; q0 += 32) {
+            const long long q = q0 + lane;
+            int v = 0;
+            bool h = false;
+            if (q < e0) {
+                v = __ldg(p.cols + q);
+                h = in_frontier(fcur, v);
+            }
+            const unsigned hm = __ballot_sync(kFull, h);
+            if (hm) {
+                const int f = __ffs(hm) - 1;
+                hitpos = q0 + f;
+                pv = __shfl_sync(kFull, v, f);
+                break;
+            }
+        }
+        if (lane == 0) {
+            if (hitpos >= 0) {
+                acc_ex += (unsigned long long)(hitpos - s0 + 1);
+                acc_m += (unsigned long long)(e0 - s0);
+                acc_n += 1;
+                if (p.parent) p.parent[u] = pv;
+                if (p.level) p.level[u] = d + 1;
+                atomicOr(fnext + (u >> 5), 1u << (u & 31));
+                atomicOr(p.visited + (u >> 5), 1u << (u & 31));
+            } else {
+                acc_ex += (unsigned long long)(e0 - s0);
+            }
+        }
     }
 }
 
@@ -568,10 +569,18 @@ __global__ void __launch_bounds__(kBlock, BFS_MIN_BLOCKS) bfs_single_kernel(Sing
                 if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
             }
             unsigned long long an = 0, am = 0, asc = 0, aex = 0;
-            bu_phase(p, d, fcur, fnext, an, am, asc, aex);
+            int* longlist = qnext;   // the queues are idle during bottom-up levels
+            bu_phase_a(p, d, fcur, fnext, longlist, &c->ntask[snext], an, am, asc, aex);
             block_add4(an, am, asc, aex, &c->accn[snext], &c->accm[snext], &c->scanned[snext],
                        &c->examined[snext]);
             if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
+            const long long nlong = (long long)ld_acquire64(&c->ntask[snext]);
+            if (nlong > 0) {
+                unsigned long long bn = 0, bm = 0, bex = 0;
+                bu_phase_b(p, d, fcur, fnext, longlist, nlong, bn, bm, bex);
+                block_add4(bn, bm, 0, bex, &c->accn[snext], &c->accm[snext], nullptr, &c->examined[snext]);
+                if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
+            }
             nf_next = (long long)ld_acquire64(&c->accn[snext]);
             scanned = (long long)ld_acquire64(&c->scanned[snext]);
             examined = (long long)ld_acquire64(&c->examined[snext]);
