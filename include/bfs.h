@@ -197,6 +197,14 @@ typedef struct {
 } bfs_dcsc_layout;
 bfs_status bfs_graph_dcsc(const bfs_graph* g, bfs_dcsc_layout* out);
 
+/*
+ * Copy the DCSC tile arrays into caller buffers (host or device; sizes from
+ * bfs_graph_dcsc: tile_ptr p*p+1, jc nzc, cp nzc+1, ir nnz).  Any pointer may
+ * be NULL.  Synchronises `stream`.  INVALID if the tiles were not built.
+ */
+bfs_status bfs_graph_copy_dcsc(const bfs_graph* g, int64_t* tile_ptr_out, int32_t* jc_out, int64_t* cp_out,
+                               int32_t* ir_out, void* stream);
+
 void bfs_graph_destroy(bfs_graph* g);
 
 /* ----------------------------------------------------------------- search */

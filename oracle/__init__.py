@@ -15,6 +15,8 @@ Contents (each cites the passage of Bulu\\c{c} et al. 2015 it follows):
 * :func:`certify`         -- BFS invariants, valid at any size (C)
 * :func:`do_schedule`     -- per-level direction and work counts of the
                              direction-optimizing search ("Parallel Direction-Optimizing BFS") (C)
+* :func:`dcsc_tiles`      -- DCSC of the row-block x column-block tiles ("Graph Representation":
+                             IR row ids, JC non-empty column ids, CP column pointers), numpy
 * :func:`brute_force_levels` -- all-pairs unit-weight relaxation to a fixpoint
                              (Bellman-Ford style), numpy, tiny graphs only
 
@@ -250,3 +252,34 @@ def brute_force_levels(n: int, src: np.ndarray, dst: np.ndarray, root: int) -> n
         d = new
     out = np.where(d >= INF, -1, d)
     return out.astype(np.int32)
+
+
+def dcsc_tiles(n: int, offsets: np.ndarray, cols: np.ndarray, row_block: int, col_block: int):
+    """DCSC of every tile of a CSR matrix ("Graph Representation": for each
+    tile, IR holds row ids, JC the ids of the columns with at least one
+    nonzero, CP the column pointers into IR).  Tile (i, j) covers rows
+    [i*row_block, (i+1)*row_block) and columns [j*col_block, (j+1)*col_block);
+    tiles are listed i-major.  Row and column ids are local to the tile
+    (minus the block start).  Returns (tile_ptr, JC, CP, IR) with JC/CP
+    concatenated over tiles (CP holds positions into the concatenated IR).
+
+    Written as the definition: every nonzero (u, v) ordered by (tile, v, u)."""
+    offsets = np.asarray(offsets, np.int64)
+    cols = np.asarray(cols, np.int64)
+    nrb = (n + row_block - 1) // row_block
+    ncb = (n + col_block - 1) // col_block
+    rows = np.repeat(np.arange(n, dtype=np.int64), np.diff(offsets))
+    tile = (rows // row_block) * ncb + cols // col_block
+    order = np.lexsort((rows, cols, tile))
+    t, v, u = tile[order], cols[order] % col_block, rows[order] % row_block
+    IR = u.astype(np.int32)
+    new_col = np.ones(len(order), bool)
+    if len(order):
+        new_col[1:] = (t[1:] != t[:-1]) | (v[1:] != v[:-1])
+    starts = np.flatnonzero(new_col)
+    JC = v[starts].astype(np.int32)
+    CP = np.append(starts, len(order)).astype(np.int64)
+    tile_of_col = t[starts]
+    tile_ptr = np.zeros(nrb * ncb + 1, np.int64)
+    np.cumsum(np.bincount(tile_of_col, minlength=nrb * ncb), out=tile_ptr[1:])
+    return tile_ptr, JC, CP, IR

@@ -57,6 +57,7 @@ SIGNATURES = [
     ("bfs_graph_csr", c_i32, [c_vp, ctypes.POINTER(c_vp), ctypes.POINTER(c_vp)]),
     ("bfs_graph_copy_csr", c_i32, [c_vp, c_vp, c_vp, c_vp]),
     ("bfs_graph_dcsc", c_i32, [c_vp, ctypes.POINTER(DcscLayout)]),
+    ("bfs_graph_copy_dcsc", c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     ("bfs_graph_destroy", None, [c_vp]),
     ("bfs_run", c_i32, [c_vp, c_i32, c_vp, c_vp, ctypes.POINTER(Options), c_vp, ctypes.POINTER(Stats)]),
     ("bfs_run_multiroot", c_i32, [c_vp, c_vp, c_i32, c_vp, c_vp, ctypes.POINTER(Options), c_vp,

@@ -160,6 +160,18 @@ class Graph:
         L.check(L.load().bfs_graph_dcsc(self._h, ctypes.byref(d)), "graph_dcsc")
         return d
 
+    def dcsc_host(self):
+        """(num_blocks, block_size, tile_ptr, jc, cp, ir) of the DCSC tiles, copied to host numpy arrays."""
+        d = self.dcsc_layout()
+        p = d.num_blocks
+        tp = np.empty(p * p + 1, np.int64)
+        jc = np.empty(max(d.nzc, 1), np.int32)
+        cp = np.empty(d.nzc + 1, np.int64)
+        ir = np.empty(max(self.nnz, 1), np.int32)
+        L.check(L.load().bfs_graph_copy_dcsc(self._h, tp.ctypes.data, jc.ctypes.data, cp.ctypes.data, ir.ctypes.data,
+                                             None), "graph_copy_dcsc")
+        return p, d.block_size, tp, jc[: d.nzc], cp, ir[: self.nnz]
+
     # ---------------------------------------------------------------- searches
     def run(self, root: int, parent=None, level=None, opts: L.Options | None = None, stream=None,
             stats: bool = False, record_levels: int = 0):

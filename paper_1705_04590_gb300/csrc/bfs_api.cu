@@ -230,6 +230,24 @@ bfs_status bfs_graph_dcsc(const bfs_graph* g, bfs_dcsc_layout* out) {
     return BFS_OK;
 }
 
+bfs_status bfs_graph_copy_dcsc(const bfs_graph* g, int64_t* tile_ptr_out, int32_t* jc_out, int64_t* cp_out,
+                               int32_t* ir_out, void* stream) {
+    if (!g) return fail(BFS_ERR_INVALID, "graph handle is NULL");
+    const DcscTiles& D = g->dcsc;
+    if (!D.built) return fail(BFS_ERR_INVALID, "graph was built without BFS_FLAG_BUILD_DCSC");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t tiles = (size_t)D.num_blocks * (size_t)D.num_blocks;
+    if (tile_ptr_out)
+        BFS_CUDA_TRY(cudaMemcpyAsync(tile_ptr_out, D.tile_ptr, sizeof(int64_t) * (tiles + 1), cudaMemcpyDefault, s));
+    if (jc_out && D.nzc > 0)
+        BFS_CUDA_TRY(cudaMemcpyAsync(jc_out, D.jc, sizeof(int32_t) * (size_t)D.nzc, cudaMemcpyDefault, s));
+    if (cp_out) BFS_CUDA_TRY(cudaMemcpyAsync(cp_out, D.cp, sizeof(int64_t) * (size_t)(D.nzc + 1), cudaMemcpyDefault, s));
+    if (ir_out && g->nnz > 0)
+        BFS_CUDA_TRY(cudaMemcpyAsync(ir_out, D.ir, sizeof(int32_t) * (size_t)g->nnz, cudaMemcpyDefault, s));
+    BFS_CUDA_TRY(cudaStreamSynchronize(s));
+    return BFS_OK;
+}
+
 void bfs_graph_destroy(bfs_graph* g) { destroy_graph(g); }
 
 static bfs_status run_common(bfs_graph* g, const int32_t* roots, int32_t k, int32_t* parent_dev, int32_t* level_dev,

@@ -281,3 +281,52 @@ def test_schedule_counts_match_literal_walk(seed):
         elif cur == 1 and sd.nf[d] * 24 < c.n:
             cur = 0
         assert sd.dir[d] == cur
+
+
+# ------------------------------------------------------------------ DCSC definition
+
+def _fig3_csr():
+    f = fixtures.fig3()
+    off = np.zeros(7, np.int64)
+    cols = []
+    for r in range(6):
+        cols += sorted(f["rows"][r])
+        off[r + 1] = len(cols)
+    return f, off, np.array(cols, np.int64)
+
+
+def test_dcsc_fig3_whole_matrix():
+    """Figure 3's matrix as one tile: JC/CP/IR exactly as derived by hand."""
+    f, off, cols = _fig3_csr()
+    tp, JC, CP, IR = oracle.dcsc_tiles(6, off, cols, 6, 6)
+    assert tp.tolist() == [0, len(f["jc"])]
+    assert JC.tolist() == f["jc"] and CP.tolist() == f["cp"] and IR.tolist() == f["ir"]
+
+
+def test_dcsc_fig3_two_thread_row_split():
+    """The row split of the multithreaded 2D layout (rows 0-2 and 3-5, one DCSC each)."""
+    f, off, cols = _fig3_csr()
+    tp, JC, CP, IR = oracle.dcsc_tiles(6, off, cols, 3, 6)
+    for i, (jc, cp, ir) in enumerate(f["split"]):
+        a, b = tp[i], tp[i + 1]
+        assert JC[a:b].tolist() == jc
+        assert (CP[a:b + 1] - CP[a]).tolist() == cp
+        assert (IR[CP[a]:CP[b]] + 3 * i).tolist() == ir
+
+
+def test_dcsc_round_trip_random():
+    """Expanding every tile's DCSC gives back exactly the CSR's nonzeros."""
+    g = graphgen.random_small(50, 200, 9)
+    c = csr(g)
+    for rb, cb in ((7, 7), (5, 13), (50, 50), (64, 3)):
+        tp, JC, CP, IR = oracle.dcsc_tiles(c.n, c.offsets, c.cols, rb, cb)
+        ncb = (c.n + cb - 1) // cb
+        got = set()
+        for t in range(len(tp) - 1):
+            i, j = divmod(t, ncb)
+            for x in range(tp[t], tp[t + 1]):
+                for e in range(CP[x], CP[x + 1]):
+                    got.add((i * rb + int(IR[e]), j * cb + int(JC[x])))
+        want = {(u, int(v)) for u in range(c.n) for v in c.cols[c.offsets[u]:c.offsets[u + 1]]}
+        assert got == want
+        assert np.all(np.diff(CP) > 0)
