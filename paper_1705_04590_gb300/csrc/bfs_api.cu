@@ -262,7 +262,6 @@ static bfs_status run_common(bfs_graph* g, const int32_t* roots, int32_t k, int3
     if (st != BFS_OK) return st;
     st = single_prepare(g, s);
     if (st != BFS_OK) return st;
-    if (o.layout == BFS_LAYOUT_DCSC_TILED) return fail(BFS_ERR_UNSUPPORTED, "DCSC layout not available for bfs_run");
     st = single_launch(g, roots, k, parent_dev, level_dev, o, s);
     if (st != BFS_OK) return st;
     st = mark_done(g, s);

@@ -38,8 +38,9 @@
 
 namespace bfsk {
 
-constexpr int kBlock = 512;
-constexpr int kWarps = kBlock / 32;
+constexpr int kBlock = 512;     // CSR kernel
+constexpr int kDBlock = 1024;   // DCSC kernel (one CTA per vertex block)
+constexpr int kWarps = 32;      // shared-memory per-warp arrays sized for up to 1024 threads
 constexpr int kChunk = 256;    // edges per top-down chunk task
 constexpr int kStage = 256;    // per-warp shared-memory staging of next-queue entries
 #ifndef BFS_MIN_BLOCKS
@@ -76,6 +77,14 @@ struct SingleParams {
     unsigned long long seed;
     unsigned long long timeout_ns;
     unsigned expected;
+    // DCSC tiles (layout BFS_LAYOUT_DCSC_TILED)
+    const long long* __restrict__ tile_ptr;
+    const int* __restrict__ jc;
+    const long long* __restrict__ cp;
+    const int* __restrict__ ir;
+    int nb;            // p blocks
+    long long B;       // vertices per block (multiple of 32)
+    long long Bw;      // words per block
 };
 
 constexpr int TD = 0, BU = 1;
@@ -614,6 +623,242 @@ __global__ void __launch_bounds__(kBlock, BFS_MIN_BLOCKS) bfs_single_kernel(Sing
     }
 }
 
+// ------------------------------------------------------------------ DCSC tiles
+
+// Words of vertex block b that exist (the last block may run past n).
+__device__ __forceinline__ long long block_words(const SingleParams& p, int b) {
+    const long long w0 = (long long)b * p.Bw;
+    const long long w1 = min(w0 + p.Bw, p.W);
+    return w1 > w0 ? w1 - w0 : 0;
+}
+
+// Top-down on tiles (b, *) (Algorithm 3's local discovery, t = A_bj * f_j):
+// every CTA reads the whole frontier queue, finds each frontier vertex k's
+// column in its tile (b, block(k)) by binary search over JC, and claims the
+// column's rows -- all in block b, so claims are CTA-local bit operations on
+// the block's visited words held in shared memory (the sparse accumulator).
+__device__ void td_dcsc_phase(const SingleParams& p, int d, const int* qcur, long long nf, int* qnext, int snext,
+                              unsigned* s_own, unsigned long long& acc_m) {
+    const int b = blockIdx.x, lane = lane_id();
+    const long long nbw = block_words(p, b), wbase = (long long)b * p.Bw;
+    for (long long w = threadIdx.x; w < nbw; w += blockDim.x) s_own[w] = __ldcg(p.visited + wbase + w);
+    __syncthreads();
+    unsigned long long* tail = &p.ctrl->tail[snext];
+    WarpStage st = warp_stage();
+    const int wib = threadIdx.x >> 5, nwb = blockDim.x >> 5;
+    for (long long base = (long long)wib * 32; base < nf; base += (long long)nwb * 32) {
+        const long long i = base + lane;
+        int k = -1;
+        long long cs = 0, ce = 0;
+        if (i < nf) {
+            k = __ldcg(qcur + i);
+            const long long j = k / p.B;
+            const long long t = (long long)b * p.nb + j;
+            long long lo = __ldg(p.tile_ptr + t), hi = __ldg(p.tile_ptr + t + 1);
+            const int kl = (int)(k - j * p.B);
+            while (lo < hi) {
+                const long long mid = (lo + hi) >> 1;
+                if (__ldg(p.jc + mid) < kl) lo = mid + 1; else hi = mid;
+            }
+            if (lo < __ldg(p.tile_ptr + t + 1) && __ldg(p.jc + lo) == kl) {
+                cs = __ldg(p.cp + lo);
+                ce = __ldg(p.cp + lo + 1);
+            }
+        }
+        const int mydeg = (int)(ce - cs);
+        const int incl = warp_inclusive_scan(mydeg);
+        const int total = __shfl_sync(kFull, incl, 31);
+        const int excl = incl - mydeg;
+        for (int k0 = 0; k0 < total; k0 += 32) {
+            const int kk = k0 + lane;
+            int j = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+                const int c = __shfl_sync(kFull, incl, j + step - 1);
+                if (c <= kk) j += step;
+            }
+            const long long cj = __shfl_sync(kFull, cs, j);
+            const int exj = __shfl_sync(kFull, excl, j);
+            const int kj = __shfl_sync(kFull, k, j);
+            bool claimed = false;
+            int u = 0;
+            if (kk < total) {
+                const int ul = __ldg(p.ir + cj + (kk - exj));
+                const unsigned bit = 1u << (ul & 31);
+                if (!(s_own[ul >> 5] & bit)) claimed = !(atomicOr(s_own + (ul >> 5), bit) & bit);
+                u = (int)((long long)b * p.B + ul);
+            }
+            const unsigned cm = __ballot_sync(kFull, claimed);
+            if (cm) {
+                if (claimed) {
+                    st.buf[st.cnt + __popc(cm & lanemask_lt())] = u;
+                    if (p.parent) p.parent[u] = kj;
+                    if (p.level) p.level[u] = d + 1;
+                }
+                st.cnt += __popc(cm);
+                if (st.cnt > kStage - 32) stage_flush(p, st, qnext, tail, acc_m);
+            }
+        }
+    }
+    stage_flush(p, st, qnext, tail, acc_m);
+    __syncthreads();
+    for (long long w = threadIdx.x; w < nbw; w += blockDim.x) p.visited[wbase + w] = s_own[w];
+}
+
+// Bottom-up on tiles (*, b) (Algorithm 4's sub-steps without messages): the
+// CTA owning block b walks the p tiles of its column of the grid, staging the
+// frontier segment of block i in shared memory for tile (i, b); each
+// searcher u of block b (a column of the tile: the matrix is symmetric) not
+// yet completed scans its rows in block i and stops at the first one in the
+// frontier.  The completed bits of block b live in shared memory for the whole
+// level; tile order rotates with b (every CTA starts on a different segment),
+// or runs 0..p-1 for minimum-id parents.
+__device__ void bu_dcsc_phase(const SingleParams& p, int d, const unsigned* fcur, unsigned* fnext, unsigned* s_own,
+                              unsigned* s_seg, unsigned long long& acc_n, unsigned long long& acc_m,
+                              unsigned long long& acc_sc, unsigned long long& acc_ex) {
+    const int b = blockIdx.x;
+    const long long nbw = block_words(p, b), wbase = (long long)b * p.Bw;
+    for (long long w = threadIdx.x; w < nbw; w += blockDim.x) {
+        const unsigned x = __ldcg(p.visited + wbase + w);
+        s_own[w] = x;
+        acc_sc += (unsigned long long)__popc(~x);
+    }
+    for (int t = 0; t < p.nb; t++) {
+        const int i = (p.parent_mode == BFS_PARENT_MIN_ID) ? t : (b + t) % p.nb;
+        const long long ibw = block_words(p, i), ibase = (long long)i * p.Bw;
+        __syncthreads();
+        for (long long w = threadIdx.x; w < ibw; w += blockDim.x) s_seg[w] = __ldcg(fcur + ibase + w);
+        __syncthreads();
+        const long long tt = (long long)i * p.nb + b;
+        const long long lo = __ldg(p.tile_ptr + tt), hi = __ldg(p.tile_ptr + tt + 1);
+        for (long long x = lo + threadIdx.x; x < hi; x += blockDim.x) {
+            const int ul = __ldg(p.jc + x);
+            if ((s_own[ul >> 5] >> (ul & 31)) & 1u) continue;
+            const long long e0 = __ldg(p.cp + x), e1 = __ldg(p.cp + x + 1);
+            for (long long e = e0; e < e1; e++) {
+                const int vl = __ldg(p.ir + e);
+                if ((s_seg[vl >> 5] >> (vl & 31)) & 1u) {
+                    const long long u = (long long)b * p.B + ul;
+                    if (p.parent) p.parent[u] = (int)((long long)i * p.B + vl);
+                    if (p.level) p.level[u] = d + 1;
+                    atomicOr(s_own + (ul >> 5), 1u << (ul & 31));
+                    acc_ex += (unsigned long long)(e - e0 + 1);
+                    break;
+                }
+                if (e + 1 == e1) acc_ex += (unsigned long long)(e1 - e0);
+            }
+        }
+    }
+    __syncthreads();
+    for (long long w = threadIdx.x; w < nbw; w += blockDim.x) {
+        const unsigned old = __ldcg(p.visited + wbase + w);
+        const unsigned now = s_own[w];
+        const unsigned nw = now & ~old;
+        fnext[wbase + w] = nw;
+        if (nw) p.visited[wbase + w] = now;
+        acc_n += (unsigned long long)__popc(nw);
+        unsigned bits = nw;
+        while (bits) {
+            const int bt = __ffs(bits) - 1;
+            bits &= bits - 1;
+            const long long u = (wbase + w) * 32 + bt;
+            acc_m += (unsigned long long)(__ldg(p.off + u + 1) - __ldg(p.off + u));
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kDBlock, 1) bfs_dcsc_kernel(SingleParams p) {
+    extern __shared__ unsigned dyn[];
+    unsigned* s_own = dyn;
+    unsigned* s_seg = dyn + p.Bw;
+    Ctrl* c = p.ctrl;
+    init_phase(p);
+    if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
+    if (p.nroots == 1 && gtid() == 0) {
+        if (p.parent) p.parent[p.root0] = p.root0;
+        if (p.level) p.level[p.root0] = 0;
+    }
+    if (p.nroots > 1) {
+        seed_roots_phase(p);
+        if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
+    }
+    long long nf = p.nroots;
+    long long mf = (long long)ld_acquire64(&c->accm[0]);
+    long long mu = p.nnz - mf;
+    long long reached = nf;
+    int prev = TD, qsel = 0, bsel = 0, d = 0;
+    const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+    const uint64_t t_start = lead ? globaltimer_ns() : 0;
+    while (true) {
+        const int dir = decide_dir(p, prev, nf, mf, mu, d);
+        const int scur = d % 3, snext = (d + 1) % 3, sfree = (d + 2) % 3;
+        if (lead) {
+            c->tail[sfree] = 0;
+            c->accn[sfree] = 0;
+            c->accm[sfree] = 0;
+            c->scanned[sfree] = 0;
+            c->examined[sfree] = 0;
+            c->ntask[sfree] = 0;
+        }
+        long long nf_next, scanned = 0, examined = mf;
+        int* qcur = qsel ? p.queue1 : p.queue0;
+        int* qnext = qsel ? p.queue0 : p.queue1;
+        unsigned* fcur = bsel ? p.front1 : p.front0;
+        unsigned* fnext = bsel ? p.front0 : p.front1;
+        if (dir == TD) {
+            if (prev == BU) {
+                bitmap_to_queue(p, fcur, fnext, qcur, &c->tail[scur]);
+                if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
+            }
+            unsigned long long am = 0;
+            td_dcsc_phase(p, d, qcur, nf, qnext, snext, s_own, am);
+            block_add4(0, am, 0, 0, nullptr, &c->accm[snext], nullptr, nullptr);
+            if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
+            nf_next = (long long)ld_acquire64(&c->tail[snext]);
+            if (p.parent_mode == BFS_PARENT_MIN_ID && p.parent && p.level) td_min_parent(p, d, qnext, nf_next);
+            qsel ^= 1;
+        } else {
+            if (prev == TD) {
+                queue_to_bitmap(p, qcur, nf, fcur);
+                if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
+            }
+            unsigned long long an = 0, am = 0, asc = 0, aex = 0;
+            bu_dcsc_phase(p, d, fcur, fnext, s_own, s_seg, an, am, asc, aex);
+            block_add4(an, am, asc, aex, &c->accn[snext], &c->accm[snext], &c->scanned[snext], &c->examined[snext]);
+            if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
+            nf_next = (long long)ld_acquire64(&c->accn[snext]);
+            scanned = (long long)ld_acquire64(&c->scanned[snext]);
+            examined = (long long)ld_acquire64(&c->examined[snext]);
+            bsel ^= 1;
+        }
+        const long long mf_next = (long long)ld_acquire64(&c->accm[snext]);
+        if (lead && d < p.rec_cap) {
+            bfs_level_record r;
+            r.dir = dir;
+            r.reserved = 0;
+            r.nf = nf;
+            r.mf = mf;
+            r.nnext = nf_next;
+            r.mnext = mf_next;
+            r.scanned = scanned;
+            r.examined = examined;
+            r.t_ns = (long long)(globaltimer_ns() - t_start);
+            p.rec[d] = r;
+        }
+        if (nf_next == 0) break;
+        reached += nf_next;
+        mu -= mf_next;
+        nf = nf_next;
+        mf = mf_next;
+        prev = dir;
+        d++;
+    }
+    if (lead) {
+        c->num_levels = d + 1;
+        c->reached = reached;
+    }
+}
+
 }  // namespace bfsk
 
 // ====================================================================== host
@@ -712,12 +957,42 @@ bfs_status single_launch(bfs_graph* g, const int32_t* roots_host, int32_t k, int
     p.big_deg = opt.td_big_degree > 0 ? opt.td_big_degree : 96;
     p.seed = opt.seed;
     p.timeout_ns = (unsigned long long)(opt.timeout_ms > 0 ? opt.timeout_ms : 10000) * 1000000ull;
-    p.expected = (unsigned)w.grid + (unsigned)(opt.debug_barrier_extra > 0 ? opt.debug_barrier_extra : 0);
+    const unsigned extra = (unsigned)(opt.debug_barrier_extra > 0 ? opt.debug_barrier_extra : 0);
+    p.expected = (unsigned)w.grid + extra;
+    p.tile_ptr = nullptr;
+    p.jc = nullptr;
+    p.cp = nullptr;
+    p.ir = nullptr;
+    p.nb = 0;
+    p.B = 0;
+    p.Bw = 0;
+    const bool dcsc = opt.layout == BFS_LAYOUT_DCSC_TILED;
+    int grid = w.grid, block = w.block;
+    size_t dyn = 0;
+    if (dcsc) {
+        const DcscTiles& D = g->dcsc;
+        p.tile_ptr = reinterpret_cast<const long long*>(D.tile_ptr);
+        p.jc = D.jc;
+        p.cp = reinterpret_cast<const long long*>(D.cp);
+        p.ir = D.ir;
+        p.nb = D.num_blocks;
+        p.B = D.block_size;
+        p.Bw = D.block_size / 32;
+        dyn = sizeof(unsigned) * 2 * (size_t)p.Bw;
+        BFS_CUDA_TRY(cudaFuncSetAttribute(bfsk::bfs_dcsc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+        int occ = 0;
+        BFS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bfsk::bfs_dcsc_kernel, bfsk::kDBlock, dyn));
+        if (occ < 1 || (long long)occ * g->sm_count < D.num_blocks)
+            return fail(BFS_ERR_UNSUPPORTED, "DCSC kernel: the tile grid cannot be co-resident on this device");
+        grid = D.num_blocks;
+        block = bfsk::kDBlock;
+        p.expected = (unsigned)grid + extra;
+    }
     BFS_CUDA_TRY(cudaMemsetAsync(w.ctrl, 0, sizeof(Ctrl), s));
     if (k > 1) BFS_CUDA_TRY(cudaMemcpyAsync(w.queue0, roots_host, sizeof(int32_t) * (size_t)k, cudaMemcpyHostToDevice, s));
     void* args[] = {&p};
-    BFS_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)bfsk::bfs_single_kernel, dim3(w.grid), dim3(w.block),
-                                             args, 0, s));
+    const void* fn = dcsc ? (const void*)bfsk::bfs_dcsc_kernel : (const void*)bfsk::bfs_single_kernel;
+    BFS_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, dyn, s));
     return BFS_OK;
 }
 
