@@ -38,7 +38,10 @@
 
 namespace bfsk {
 
-constexpr int kBlock = 512;     // CSR kernel
+#ifndef BFS_BLOCK
+#define BFS_BLOCK 512
+#endif
+constexpr int kBlock = BFS_BLOCK;  // CSR kernel
 constexpr int kDBlock = 1024;   // DCSC kernel (one CTA per vertex block)
 constexpr int kWarps = 32;      // shared-memory per-warp arrays sized for up to 1024 threads
 constexpr int kChunk = 256;    // edges per top-down chunk task
@@ -195,7 +198,7 @@ __device__ __forceinline__ void td_visit(const SingleParams& p, int d, int u, in
     if (act) {
         const unsigned bit = 1u << (v & 31);
         unsigned* wp = p.visited + (v >> 5);
-        if (!(__ldcg(wp) & bit)) claimed = !(atomicOr(wp, bit) & bit);
+        claimed = !(atomicOr(wp, bit) & bit);
     }
     const unsigned cm = __ballot_sync(kFull, claimed);
     if (cm) {
@@ -359,12 +362,27 @@ __device__ __forceinline__ bool in_frontier(const unsigned* f, int v) {
 
 // Bottom-up, phase A.  A warp takes 32 completed-bitmap words (1024
 // vertices) at a time and compacts the unvisited ones with a warp prefix sum;
-// each lane then takes one searcher per round: its row offsets (prefetched one
-// round ahead), one aligned window of 8 ids (two int4 loads) and 8 frontier
-// probes.  A searcher whose row continues past the window without a hit goes
-// on the long list (phase B).  Found vertices are collected per word in shared
-// memory and written as whole next-frontier / completed words (the warp owns
-// its 32 words, so no atomics).
+// each lane then handles one searcher per round: its row offsets, one aligned
+// window of 8 ids (two int4 loads) and 8 frontier probes.  The rounds are
+// software-pipelined three deep -- while round r's probes run, round r+1's
+// window and round r+2's offsets are already in flight -- so each round costs
+// about one L2 probe latency instead of two DRAM round trips.  A searcher
+// whose row continues past the window without a hit goes on the long list
+// (phase B).  Found vertices are collected per word in shared memory and
+// written as whole next-frontier / completed words (the warp owns its words).
+__device__ __forceinline__ int bu_locate(int k, int T, int incl, int excl, unsigned todo, long long ch) {
+    int j = 0;
+#pragma unroll
+    for (int step = 16; step >= 1; step >>= 1) {
+        const int c = __shfl_sync(kFull, incl, j + step - 1);
+        if (c <= k) j += step;
+    }
+    const int exj = __shfl_sync(kFull, excl, j);
+    const unsigned tj = __shfl_sync(kFull, todo, j);
+    if (k >= T) return -1;
+    return (int)((ch * 32 + j) * 32 + (long long)__fns(tj, 0, k - exj + 1));
+}
+
 __device__ void bu_phase_a(const SingleParams& p, int d, const unsigned* fcur, unsigned* fnext, int* longlist,
                            unsigned long long* longcnt, unsigned long long& acc_n, unsigned long long& acc_m,
                            unsigned long long& acc_sc, unsigned long long& acc_ex) {
@@ -372,6 +390,7 @@ __device__ void bu_phase_a(const SingleParams& p, int d, const unsigned* fcur, u
     const int lane = lane_id(), wib = threadIdx.x >> 5;
     const long long gw = gtid() >> 5, nw = gthreads() >> 5;
     const long long nchunk = (p.W + 31) / 32;
+    const int4 z4 = make_int4(0, 0, 0, 0);
     s_next[wib][lane] = 0u;
     __syncwarp();
     for (long long ch = gw; ch < nchunk; ch += nw) {
@@ -382,47 +401,45 @@ __device__ void bu_phase_a(const SingleParams& p, int d, const unsigned* fcur, u
         const int incl = warp_inclusive_scan(cnt);
         const int T = __shfl_sync(kFull, incl, 31);
         const int excl = incl - cnt;
-        // searcher k of this chunk -> (word j, bit b, vertex u)
-        auto locate = [&](int k, int& j, int& b, long long& u) {
-            j = 0;
-#pragma unroll
-            for (int step = 16; step >= 1; step >>= 1) {
-                const int c = __shfl_sync(kFull, incl, j + step - 1);
-                if (c <= k) j += step;
-            }
-            const int exj = __shfl_sync(kFull, excl, j);
-            const unsigned tj = __shfl_sync(kFull, todo, j);
-            b = 0;
-            u = -1;
-            if (k < T) {
-                b = (int)__fns(tj, 0, k - exj + 1);
-                u = (ch * 32 + j) * 32 + b;
-            }
-        };
-        int j0, b0;
-        long long u0;
-        locate(lane, j0, b0, u0);
+        // pipeline prologue: round 0 offsets + window, round 1 offsets
+        int u0 = bu_locate(lane, T, incl, excl, todo, ch);
         long long s0 = 0, e0 = 0;
         if (u0 >= 0) {
             s0 = __ldg(p.off + u0);
             e0 = __ldg(p.off + u0 + 1);
         }
+        int4 xa0 = z4, xb0 = z4;
+        if (u0 >= 0 && e0 > s0) {
+            const int4* src = reinterpret_cast<const int4*>(p.cols + (s0 & ~3LL));
+            xa0 = __ldg(src);
+            if ((s0 & ~3LL) + 4 < e0) xb0 = __ldg(src + 1);
+        }
+        int u1 = bu_locate(32 + lane, T, incl, excl, todo, ch);
+        long long s1 = 0, e1 = 0;
+        if (u1 >= 0) {
+            s1 = __ldg(p.off + u1);
+            e1 = __ldg(p.off + u1 + 1);
+        }
         for (int base = 0; base < T; base += 32) {
-            // prefetch the next round's row offsets
-            int j1, b1;
-            long long u1, s1 = 0, e1 = 0;
-            locate(base + 32 + lane, j1, b1, u1);
-            if (u1 >= 0) {
-                s1 = __ldg(p.off + u1);
-                e1 = __ldg(p.off + u1 + 1);
+            // round r+2: offsets
+            const int u2 = bu_locate(base + 64 + lane, T, incl, excl, todo, ch);
+            long long s2 = 0, e2 = 0;
+            if (u2 >= 0) {
+                s2 = __ldg(p.off + u2);
+                e2 = __ldg(p.off + u2 + 1);
             }
+            // round r+1: window
+            int4 xa1 = z4, xb1 = z4;
+            if (u1 >= 0 && e1 > s1) {
+                const int4* src = reinterpret_cast<const int4*>(p.cols + (s1 & ~3LL));
+                xa1 = __ldg(src);
+                if ((s1 & ~3LL) + 4 < e1) xb1 = __ldg(src + 1);
+            }
+            // round r: probes
             bool to_long = false;
             if (u0 >= 0) {
                 const long long rb = s0 & ~3LL;
-                const int4* src = reinterpret_cast<const int4*>(p.cols + rb);
-                const int4 xa = __ldg(src);
-                const int4 xb = (rb + 4 < e0) ? __ldg(src + 1) : make_int4(0, 0, 0, 0);
-                const int ids[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
+                const int ids[8] = {xa0.x, xa0.y, xa0.z, xa0.w, xb0.x, xb0.y, xb0.z, xb0.w};
                 unsigned hb = 0;
 #pragma unroll
                 for (int t = 0; t < 8; t++) {
@@ -436,26 +453,28 @@ __device__ void bu_phase_a(const SingleParams& p, int d, const unsigned* fcur, u
                     acc_m += (unsigned long long)(e0 - s0);
                     if (p.parent) p.parent[u0] = ids[t];
                     if (p.level) p.level[u0] = d + 1;
-                    atomicOr(&s_next[wib][j0], 1u << b0);
+                    atomicOr(&s_next[wib][(u0 >> 5) - ch * 32], 1u << (u0 & 31));
                 } else if (rb + 8 < e0) {
                     to_long = true;       // examinations counted by phase B
                 } else {
                     acc_ex += (unsigned long long)(e0 - s0);
                 }
             }
-            // long-list append, one atomicAdd per warp round with entries
             const unsigned lm = __ballot_sync(kFull, to_long);
             if (lm) {
                 unsigned long long lb = 0;
                 if (lane == 0) lb = atomicAdd(longcnt, (unsigned long long)__popc(lm));
                 lb = __shfl_sync(kFull, lb, 0);
-                if (to_long) longlist[lb + __popc(lm & lanemask_lt())] = (int)u0;
+                if (to_long) longlist[lb + __popc(lm & lanemask_lt())] = u0;
             }
-            j0 = j1;
-            b0 = b1;
             u0 = u1;
             s0 = s1;
             e0 = e1;
+            xa0 = xa1;
+            xb0 = xb1;
+            u1 = u2;
+            s1 = s2;
+            e1 = e2;
         }
         __syncwarp();
         const unsigned nx = s_next[wib][lane];
@@ -469,38 +488,64 @@ __device__ void bu_phase_a(const SingleParams& p, int d, const unsigned* fcur, u
     }
 }
 
-// Bottom-up, phase B: the long list, one warp per searcher, 32 ids per step in
-// row order, stopping at the first frontier neighbour (ballot: lowest lane =
-// first position, so parents stay the minimum-id ones).  Next-frontier and
-// completed words are shared across warps here, hence atomicOr.
+// Bottom-up, phase B: the long list.  Groups of 4 lanes take one searcher
+// each (8 per warp); a group reads 16 ids per step (one int4 per lane, in row
+// order) and stops at the first frontier neighbour: the lowest lane of the
+// group with a hit, its lowest id -- so parents stay the minimum-id ones.
+// Next-frontier and completed words are shared across warps here, hence
+// atomicOr.
 __device__ void bu_phase_b(const SingleParams& p, int d, const unsigned* fcur, unsigned* fnext, const int* longlist,
                            long long nlong, unsigned long long& acc_n, unsigned long long& acc_m,
                            unsigned long long& acc_ex) {
-    const int lane = lane_id();
+    const int lane = lane_id(), grp = lane >> 2, gl = lane & 3;
     const long long gw = gtid() >> 5, nw = gthreads() >> 5;
-    for (long long i = gw; i < nlong; i += nw) {
-        const int u = __ldcg(longlist + i);
-        const long long s0 = __ldg(p.off + u), e0 = __ldg(p.off + u + 1);
-        const long long from = (s0 & ~3LL) + 8;
+    for (long long base = gw * 8; base < nlong; base += nw * 8) {
+        const long long i = base + grp;
+        int u = -1;
+        long long s0 = 0, e0 = 0, pos = 0;
+        if (i < nlong) {
+            u = __ldcg(longlist + i);
+            s0 = __ldg(p.off + u);
+            e0 = __ldg(p.off + u + 1);
+            pos = (s0 & ~3LL) + 8 + 4 * gl;
+        }
         long long hitpos = -1;
         int pv = -1;
-        for (long long q0 = from; q0 < e0; q0 += 32) {
-            const long long q = q0 + lane;
-            int v = 0;
-            bool h = false;
-            if (q < e0) {
-                v = __ldg(p.cols + q);
-                h = in_frontier(fcur, v);
+        bool live = u >= 0;
+        while (__any_sync(kFull, live)) {
+            unsigned hb = 0;
+            int4 x = make_int4(0, 0, 0, 0);
+            if (live && pos < e0) {
+                x = __ldg(reinterpret_cast<const int4*>(p.cols + pos));
+                const int ids[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                for (int t = 0; t < 4; t++)
+                    if (pos + t < e0 && in_frontier(fcur, ids[t])) hb |= 1u << t;
             }
-            const unsigned hm = __ballot_sync(kFull, h);
-            if (hm) {
-                const int f = __ffs(hm) - 1;
-                hitpos = q0 + f;
-                pv = __shfl_sync(kFull, v, f);
-                break;
+            const unsigned any = __ballot_sync(kFull, hb != 0);
+            const unsigned gm = (any >> (grp * 4)) & 0xFu;
+            const long long gstart = pos - 4 * gl;   // group's position this step
+            if (live) {
+                if (gm) {
+                    const int first = __ffs(gm) - 1;
+                    const unsigned hbf = __shfl_sync(kFull, hb, grp * 4 + first);
+                    const int t = __ffs(hbf) - 1;
+                    const int ids_src = (t == 0) ? x.x : (t == 1) ? x.y : (t == 2) ? x.z : x.w;
+                    const int vfirst = __shfl_sync(kFull, ids_src, grp * 4 + first);
+                    hitpos = gstart + 4 * first + t;
+                    pv = vfirst;
+                    live = false;
+                } else if (gstart + 16 >= e0) {
+                    live = false;
+                }
+            } else {
+                // keep the shuffles convergent
+                (void)__shfl_sync(kFull, hb, grp * 4);
+                (void)__shfl_sync(kFull, x.x, grp * 4);
             }
+            pos += 16;
         }
-        if (lane == 0) {
+        if (u >= 0 && gl == 0) {
             if (hitpos >= 0) {
                 acc_ex += (unsigned long long)(hitpos - s0 + 1);
                 acc_m += (unsigned long long)(e0 - s0);
