@@ -525,23 +525,21 @@ __device__ void bu_phase_b(const SingleParams& p, int d, const unsigned* fcur, u
             const unsigned any = __ballot_sync(kFull, hb != 0);
             const unsigned gm = (any >> (grp * 4)) & 0xFu;
             const long long gstart = pos - 4 * gl;   // group's position this step
+            // every lane runs both shuffles (full-mask warp primitives must be convergent):
+            // each lane offers its own first hit, the group reads its lowest lane with one
+            const int t_own = hb ? __ffs(hb) - 1 : 0;
+            const int v_own = (t_own == 0) ? x.x : (t_own == 1) ? x.y : (t_own == 2) ? x.z : x.w;
+            const int first = gm ? __ffs(gm) - 1 : 0;
+            const int t_src = __shfl_sync(kFull, t_own, grp * 4 + first);
+            const int v_src = __shfl_sync(kFull, v_own, grp * 4 + first);
             if (live) {
                 if (gm) {
-                    const int first = __ffs(gm) - 1;
-                    const unsigned hbf = __shfl_sync(kFull, hb, grp * 4 + first);
-                    const int t = __ffs(hbf) - 1;
-                    const int ids_src = (t == 0) ? x.x : (t == 1) ? x.y : (t == 2) ? x.z : x.w;
-                    const int vfirst = __shfl_sync(kFull, ids_src, grp * 4 + first);
-                    hitpos = gstart + 4 * first + t;
-                    pv = vfirst;
+                    hitpos = gstart + 4 * first + t_src;
+                    pv = v_src;
                     live = false;
                 } else if (gstart + 16 >= e0) {
                     live = false;
                 }
-            } else {
-                // keep the shuffles convergent
-                (void)__shfl_sync(kFull, hb, grp * 4);
-                (void)__shfl_sync(kFull, x.x, grp * 4);
             }
             pos += 16;
         }
