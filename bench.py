@@ -18,6 +18,12 @@ roofline: algorithmic bytes per search from the search's own per-level
           against the measured HBM copy bandwidth (MEASURED_PEAKS.json).
 cpu_baseline: the serial CPU oracle (Algorithm 1) on one host core, on a
           bounded sample: R-MAT at a smaller scale with the same generator.
+batched: 64-lane multi-source search (R-MAT 22, 64 roots, one launch) and an
+          uneven batch of 256 graphs (one multi-root launch over their union),
+          each against looping the plain single-source search.
+served:  continuous-batching server over 8 resident graphs, Poisson arrivals at
+          0.25/0.5/0.9 of the saturated throughput, p50/p99 latency and GTEPS,
+          against a one-at-a-time plain FIFO on the same arrival trace.
 
 --impl reference times that oracle alone, the same way, one search per step.
 Multi-GPU (torchrun): replicas only -- each rank searches its own copy of the
@@ -179,6 +185,201 @@ def reference_arm(args):
     return 0
 
 
+# ------------------------------------------------------------------ batched / served sections
+
+def _events(stream):
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def batched_section(seed: int = 4242) -> dict:
+    """Batched multi-source BFS against looping the plain search.
+
+    (i)  R-MAT scale 22, 64 roots: one bfs_run_multi (64 lanes, one persistent
+         launch) vs 64 bfs_run, levels only, CUDA events, best of 3.
+    (ii) 256 R-MAT graphs with scales drawn uniformly from 10..20 (seeded), one
+         root each: one bfs_run_multiroot over their disjoint union (one
+         launch) vs a loop of 256 plain searches on the separate graphs.
+    """
+    import numpy as np
+    import torch
+
+    import graphgen
+    import paper_1705_04590_gb300 as bfs
+    from graphgen import workloads
+
+    out = {}
+    w = workloads.RMAT[22]
+    e = w.edges()
+    roots = w.roots(e, 64).tolist()
+    g = bfs.Graph.from_edges(e.src, e.dst, e.n)
+    n, m = e.n, g.nnz // 2
+    del e
+    lv1 = torch.empty(n, dtype=torch.int32, device="cuda")
+    lvk = torch.empty(64 * n, dtype=torch.int32, device="cuda")
+
+    def best_ms(fn, reps=3):
+        best = None
+        for _ in range(reps + 1):
+            a, b = _events(None)
+            torch.cuda.synchronize()
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            t = a.elapsed_time(b)
+            best = t if best is None else min(best, t)
+        return best
+
+    t_multi = best_ms(lambda: g.run_multi(roots, lvk))
+    t_plain = best_ms(lambda: [g.run(r, level=lv1) for r in roots])
+    g.sync()
+    out["rmat22_64roots"] = {"multi_ms": t_multi, "plain_ms": t_plain, "multi_gteps": 64 * m / t_multi / 1e6,
+                             "plain_gteps": 64 * m / t_plain / 1e6, "speedup": t_plain / t_multi,
+                             "launches_multi": 1, "launches_plain": 64}
+    g.close()
+    del lvk
+    rng = np.random.default_rng(seed)
+    scales = rng.integers(10, 21, 256)
+    parts = [graphgen.rmat(int(sc), seed=50_000 + i) for i, sc in enumerate(scales)]
+    u, offs = graphgen.disjoint_union(parts)
+    uroots = [int(offs[i]) + int(graphgen.pick_roots(pp, 1, 7 + i)[0]) for i, pp in enumerate(parts)]
+    gu = bfs.Graph.from_edges(u.src, u.dst, u.n)
+    gs = [bfs.Graph.from_edges(pp.src, pp.dst, pp.n) for pp in parts]
+    mu = gu.nnz // 2
+    lu = torch.empty(u.n, dtype=torch.int32, device="cuda")
+    bufs = [torch.empty(pp.n, dtype=torch.int32, device="cuda") for pp in parts]
+    t_union = best_ms(lambda: gu.run_multiroot(uroots, level=lu))
+    t_loop = best_ms(lambda: [gg.run(uroots[i] - int(offs[i]), level=bufs[i]) for i, gg in enumerate(gs)])
+    out["uneven_256_graphs"] = {"scales": "U{10..20} seed %d" % seed, "vertices": int(u.n), "undirected_edges": mu,
+                                "union_ms": t_union, "loop_ms": t_loop, "union_gteps": mu / t_union / 1e6,
+                                "loop_gteps": mu / t_loop / 1e6, "speedup": t_loop / t_union}
+    for gg in gs:
+        gg.close()
+    gu.close()
+    return out
+
+
+def served_section(g26, roots26, n_queries: int = 2000, seed: int = 5151) -> dict:
+    """Served BFS: 8 resident graphs (R-MAT 16, 18, 20, 22, 24, 25, 26 and the
+    4096x4096 torus), queries = (graph uniform over the 8, seeded root), each
+    returning level[] into pinned host memory.  The saturated throughput is
+    measured with a burst; then Poisson arrivals at 0.25, 0.5 and 0.9 of it,
+    n_queries each, through the continuous-batching server and through a
+    one-at-a-time plain FIFO (bfs_run + copy-out) on the same trace.
+    Latency = submit -> result in host memory."""
+    import numpy as np
+    import torch
+
+    import paper_1705_04590_gb300 as bfs
+    from graphgen import workloads
+
+    specs = [("rmat16", workloads.RMAT[16]), ("rmat18", workloads.RMAT[18]), ("rmat20", workloads.RMAT[20]),
+             ("rmat22", workloads.RMAT[22]), ("rmat24", workloads.RMAT[24]), ("rmat25", workloads.RMAT[25]),
+             ("rmat26", None), ("torus4096", workloads.TORUS4096)]
+    graphs, rootsets, ms = [], [], []
+    for name, wl in specs:
+        if wl is None:
+            g, rs = g26, roots26
+        else:
+            e = wl.edges()
+            rs = wl.roots(e, 64).tolist()
+            g = bfs.Graph.from_edges(e.src, e.dst, e.n)
+            del e
+        graphs.append(g)
+        rootsets.append(rs)
+        ms.append(g.nnz // 2)
+    pool_size = [64 if g.n < (1 << 24) else 16 for g in graphs]
+    pinned = [[torch.empty(g.n, dtype=torch.int32, pin_memory=True) for _ in range(k)]
+              for g, k in zip(graphs, pool_size)]
+    pools = [[t.numpy() for t in pl] for pl in pinned]
+    srv = bfs.Server(hbm_budget_bytes=96 << 30, max_lanes=64)
+    slots = [srv.add_graph(g) for g in graphs]
+    rng = np.random.default_rng(seed)
+
+    def trace(k):
+        gi = rng.integers(0, len(graphs), k)
+        ri = rng.integers(0, 64, k)
+        return [(int(a), rootsets[int(a)][int(b)]) for a, b in zip(gi, ri)]
+
+    def run_server(tr, arrivals):
+        free = [list(range(len(pl))) for pl in pools]
+        inflight = []    # (ticket, graph, buffer index)
+        lat, done_m = [], 0
+        t0 = time.perf_counter()
+        for (gi, root), at in zip(tr, arrivals):
+            while time.perf_counter() - t0 < at:
+                pass
+            while not free[gi]:
+                # buffer pool of this graph exhausted: retire the oldest in-flight query of that graph
+                for idx, (tk, gj, bi) in enumerate(inflight):
+                    if gj == gi:
+                        srv.wait(tk)
+                        lat.append(srv.latency_us(tk))
+                        done_m += ms[gj]
+                        free[gj].append(bi)
+                        inflight.pop(idx)
+                        break
+            bi = free[gi].pop()
+            inflight.append((srv.submit(slots[gi], root, pools[gi][bi]), gi, bi))
+            # opportunistically retire finished queries
+            keep = []
+            for tk, gj, bj in inflight:
+                if srv.poll(tk):
+                    lat.append(srv.latency_us(tk))
+                    done_m += ms[gj]
+                    free[gj].append(bj)
+                else:
+                    keep.append((tk, gj, bj))
+            inflight = keep
+        for tk, gj, bj in inflight:
+            srv.wait(tk)
+            lat.append(srv.latency_us(tk))
+            done_m += ms[gj]
+        wall = time.perf_counter() - t0
+        lat = np.array(lat) / 1e3
+        return {"wall_s": wall, "qps": len(tr) / wall, "gteps": done_m / wall / 1e9,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))}
+
+    def run_fifo(tr, arrivals):
+        lvs = [torch.empty(g.n, dtype=torch.int32, device="cuda") for g in graphs]
+        lat, done_m = [], 0
+        t0 = time.perf_counter()
+        for (gi, root), at in zip(tr, arrivals):
+            while time.perf_counter() - t0 < at:
+                pass
+            graphs[gi].run(root, level=lvs[gi])
+            pinned[gi][0].copy_(lvs[gi], non_blocking=True)
+            torch.cuda.synchronize()
+            lat.append((time.perf_counter() - t0 - at) * 1e3)
+            done_m += ms[gi]
+        wall = time.perf_counter() - t0
+        lat = np.array(lat)
+        return {"wall_s": wall, "qps": len(tr) / wall, "gteps": done_m / wall / 1e9,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))}
+
+    # warm-up and saturated throughput: a burst of queries all at time 0
+    run_server(trace(256), np.zeros(256))
+    sat = run_server(trace(1024), np.zeros(1024))
+    out = {"graphs": [nme for nme, _ in specs], "saturated": sat, "loads": []}
+    for frac in (0.25, 0.5, 0.9):
+        rate = frac * sat["qps"]
+        tr = trace(n_queries)
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, n_queries))
+        arrivals -= arrivals[0]
+        sv = run_server(tr, arrivals)
+        fi = run_fifo(tr, arrivals)
+        out["loads"].append({"offered_frac": frac, "offered_qps": rate, "served": sv, "plain_fifo": fi,
+                             "gteps_ratio": sv["gteps"] / fi["gteps"]})
+    st = srv.stats()
+    out["server_counters"] = st
+    srv.close()
+    for g in graphs:
+        if g is not g26:
+            g.close()
+    return out
+
+
 # ------------------------------------------------------------------ our arm
 
 def our_arm(args):
@@ -270,6 +471,12 @@ def our_arm(args):
         if tr.get("kernel_source_hash") == kernel_source_hash() and tr.get("scale") == args.scale:
             traffic = tr.get("dram_bytes_per_launch")
 
+    batched = served = None
+    if rank == 0 and not args.no_batched:
+        batched = batched_section()
+    if rank == 0 and not args.no_served:
+        served = served_section(g, roots, n_queries=args.served_queries)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         gteps, secs, cnt, m_s, _ = oracle_sample(args.cpu_scale, 8)
@@ -299,6 +506,8 @@ def our_arm(args):
             "clocks": clocks,
             "cpu_baseline": cpu,
             "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
+            "batched": batched,
+            "served": served,
         }
         print(json.dumps(line), flush=True)
     g.close()
@@ -317,6 +526,9 @@ def main():
     ap.add_argument("--roots", type=int, default=64)
     ap.add_argument("--cpu-scale", type=int, default=22)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched multi-source section")
+    ap.add_argument("--no-served", action="store_true", help="skip the served section")
+    ap.add_argument("--served-queries", type=int, default=2000, help="queries per offered load")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

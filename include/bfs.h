@@ -119,6 +119,8 @@ typedef struct {
     int64_t examined;     /* top-down: m_f; bottom-up: sum over searching vertices of the 1-based
                              position of the first frontier neighbour in sorted order, or the degree */
     int64_t t_ns;         /* device time from the end of initialisation to the end of this level */
+    int64_t aux;          /* top-down: edge-chunk tasks; bottom-up: searchers continued past their first window */
+    int64_t t_mid_ns;     /* device time at the level's first internal barrier (0 if none) */
 } bfs_level_record;
 
 typedef struct {

@@ -33,7 +33,8 @@ class Options(ctypes.Structure):
 
 class LevelRecord(ctypes.Structure):
     _fields_ = [("dir", c_i32), ("reserved", c_i32), ("nf", c_i64), ("mf", c_i64), ("nnext", c_i64),
-                ("mnext", c_i64), ("scanned", c_i64), ("examined", c_i64), ("t_ns", c_i64)]
+                ("mnext", c_i64), ("scanned", c_i64), ("examined", c_i64), ("t_ns", c_i64), ("aux", c_i64),
+                ("t_mid_ns", c_i64)]
 
 
 class Stats(ctypes.Structure):

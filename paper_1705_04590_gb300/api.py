@@ -228,8 +228,9 @@ class Graph:
             return None
         s, recs, cap = holder
         nrec = min(s.num_levels, cap)
-        rows = [(r.dir, r.nf, r.mf, r.nnext, r.mnext, r.scanned, r.examined, r.t_ns) for r in recs[:nrec]]
-        arr = np.array(rows, dtype=np.int64).reshape(-1, 8)
+        rows = [(r.dir, r.nf, r.mf, r.nnext, r.mnext, r.scanned, r.examined, r.t_ns, r.aux, r.t_mid_ns)
+                for r in recs[:nrec]]
+        arr = np.array(rows, dtype=np.int64).reshape(-1, 10)
         return {"num_levels": s.num_levels, "reached": s.vertices_reached, "edges_examined": s.edges_examined,
                 "records": arr}
 

@@ -591,7 +591,8 @@ __global__ void __launch_bounds__(kBlock, BFS_MIN_BLOCKS) bfs_single_kernel(Sing
             c->examined[sfree] = 0;
             c->ntask[sfree] = 0;
         }
-        long long nf_next, scanned = 0, examined = mf;
+        long long nf_next, scanned = 0, examined = mf, aux = 0;
+        uint64_t t_mid = 0;
         int* qcur = qsel ? p.queue1 : p.queue0;
         int* qnext = qsel ? p.queue0 : p.queue1;
         unsigned* fcur = bsel ? p.front1 : p.front0;
@@ -606,6 +607,8 @@ __global__ void __launch_bounds__(kBlock, BFS_MIN_BLOCKS) bfs_single_kernel(Sing
             block_add4(0, am, 0, 0, nullptr, &c->accm[snext], nullptr, nullptr);
             if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
             const long long nt = (long long)ld_acquire64(&c->ntask[snext]);
+            aux = nt;
+            if (lead) t_mid = globaltimer_ns();
             if (nt > 0) {
                 unsigned long long am2 = 0;
                 task_phase(p, d, nt, qnext, snext, am2);
@@ -627,6 +630,8 @@ __global__ void __launch_bounds__(kBlock, BFS_MIN_BLOCKS) bfs_single_kernel(Sing
                        &c->examined[snext]);
             if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
             const long long nlong = (long long)ld_acquire64(&c->ntask[snext]);
+            aux = nlong;
+            if (lead) t_mid = globaltimer_ns();
             if (nlong > 0) {
                 unsigned long long bn = 0, bm = 0, bex = 0;
                 bu_phase_b(p, d, fcur, fnext, longlist, nlong, bn, bm, bex);
@@ -650,6 +655,8 @@ __global__ void __launch_bounds__(kBlock, BFS_MIN_BLOCKS) bfs_single_kernel(Sing
             r.scanned = scanned;
             r.examined = examined;
             r.t_ns = (long long)(globaltimer_ns() - t_start);
+            r.aux = aux;
+            r.t_mid_ns = t_mid ? (long long)(t_mid - t_start) : 0;
             p.rec[d] = r;
         }
         if (nf_next == 0) break;
@@ -886,6 +893,8 @@ __global__ void __launch_bounds__(kDBlock, 1) bfs_dcsc_kernel(SingleParams p) {
             r.scanned = scanned;
             r.examined = examined;
             r.t_ns = (long long)(globaltimer_ns() - t_start);
+            r.aux = 0;
+            r.t_mid_ns = 0;
             p.rec[d] = r;
         }
         if (nf_next == 0) break;
