@@ -251,6 +251,32 @@ bfs_status bfs_run_multiroot(bfs_graph* g, const int32_t* roots_host, int32_t k,
 bfs_status bfs_run_multi(bfs_graph* g, const int32_t* roots_host, int32_t k, int32_t* level_dev,
                          int32_t* parent_dev, const bfs_options* opt, void* stream);
 
+/*
+ * Allocation-free search for callers that cannot allocate device memory: a
+ * caller whose device memory is fully pre-allocated by its own pool or arena,
+ * or one on a path where cudaMalloc/cudaFree -- which may synchronise the
+ * device and take time that cannot be bounded -- must not run.  The paper has
+ * no counterpart; this is the direction-optimizing search of bfs_run with
+ * default options over a caller-provided CSR, with every work buffer in one
+ * fixed device array of about 14 MB compiled into the library.
+ *   row_offsets: device int64[n+1]; col_ids: device int32[nnz] holding an
+ *   undirected graph as bfs_graph_create_from_csr accepts it (rows strictly
+ *   ascending, no self-loops, symmetric), readable for 32 entries past nnz
+ *   (16-byte loads may run up to 28 bytes beyond the last row; those values
+ *   are ignored).  parent_dev / level_dev: device int32[n], either may be
+ *   NULL.  Limits: 1 <= n <= 1,048,576 and nnz <= 16,777,216, else
+ *   BFS_ERR_INVALID with a message naming the limit.
+ * Calls no cudaMalloc, cudaFree or allocating routine.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress, once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Every call shares the array: calls whose work overlaps on the GPU
+ * (on different streams) race and must be ordered by the caller.  Each call
+ * re-initialises all of it that it reads.  Asynchronous on `stream`; no device
+ * error is reported back (use bfs_run for that).
+ */
+bfs_status bfs_run_csr_noalloc(const int64_t* row_offsets, const int32_t* col_ids, int64_t n, int64_t nnz,
+                               int32_t root, int32_t* parent_dev, int32_t* level_dev, void* stream);
+
 /* Wait for the graph's enqueued searches; returns the first device-side error since the last sync. */
 bfs_status bfs_graph_sync(bfs_graph* g, void* stream);
 

@@ -32,6 +32,9 @@
 // swapped in after the level (the reading of Algorithm 2 that keeps levels
 // exact).
 #include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
 
 #include "bfs_common.cuh"
 #include "bfs_internal.h"
@@ -911,6 +914,45 @@ __global__ void __launch_bounds__(kDBlock, 1) bfs_dcsc_kernel(SingleParams p) {
     }
 }
 
+// ------------------------------------------------------------------ allocation-free variant
+
+// Work buffers of bfs_run_csr_noalloc live in this file-scope device array, so
+// that entry point never allocates.  Limits: n <= kStaticMaxN, nnz <=
+// kStaticMaxNnz.  Every call shares it (calls that overlap on the GPU race);
+// each call re-initialises everything it reads.
+constexpr long long kStaticMaxN = 1LL << 20;
+constexpr long long kStaticMaxNnz = 1LL << 24;
+constexpr long long kStaticW = kStaticMaxN / 32;
+constexpr long long kStaticTasks = kStaticMaxNnz / kChunk + kStaticMaxNnz / 64 + 1024;
+constexpr int kStaticRec = 64;
+constexpr size_t kStaticCtrlOff = 0;
+constexpr size_t kStaticIsoOff = 256;
+constexpr size_t kStaticVisOff = kStaticIsoOff + 4 * kStaticW;
+constexpr size_t kStaticF0Off = kStaticVisOff + 4 * kStaticW;
+constexpr size_t kStaticF1Off = kStaticF0Off + 4 * kStaticW;
+constexpr size_t kStaticQ0Off = kStaticF1Off + 4 * kStaticW;
+constexpr size_t kStaticQ1Off = kStaticQ0Off + 4 * (kStaticMaxN + 64);
+constexpr size_t kStaticTaskOff = kStaticQ1Off + 4 * (kStaticMaxN + 64);
+constexpr size_t kStaticRecOff = kStaticTaskOff + sizeof(Task) * kStaticTasks;
+constexpr size_t kStaticBytes = kStaticRecOff + sizeof(bfs_level_record) * kStaticRec;
+static_assert(sizeof(Ctrl) <= 256, "control block must fit its slot");
+static_assert(kStaticQ1Off % 16 == 0 && kStaticTaskOff % 16 == 0 && kStaticRecOff % 8 == 0, "alignment");
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kStaticBytes];
+
+// bit v set when deg(v) = 0 or v >= n (vertices that never search)
+__global__ void k_static_isolated(const long long* __restrict__ off, long long n, long long W, unsigned* iso) {
+    const long long nth = (long long)gridDim.x * blockDim.x;
+    for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < W; w += nth) {
+        unsigned x = 0;
+        for (int b = 0; b < 32; b++) {
+            const long long v = w * 32 + b;
+            if (v >= n || off[v + 1] == off[v]) x |= 1u << b;
+        }
+        iso[w] = x;
+    }
+}
+
 }  // namespace bfsk
 
 // ====================================================================== host
@@ -920,8 +962,6 @@ namespace bfsrt {
 using bfsk::Ctrl;
 using bfsk::SingleParams;
 using bfsk::Task;
-
-static int round_up_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 bfs_status single_prepare(bfs_graph* g, cudaStream_t s) {
     SingleWork& w = g->single;
@@ -1077,3 +1117,88 @@ bfs_status single_collect(bfs_graph* g, cudaStream_t s, bfs_stats* stats) {
 }
 
 }  // namespace bfsrt
+
+// ====================================================================== allocation-free entry point
+
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[64] = {};   // device address of g_noalloc_scratch, per device
+int g_noalloc_grid[64] = {};
+int g_noalloc_sms[64] = {};
+}  // namespace
+
+extern "C" bfs_status bfs_run_csr_noalloc(const int64_t* row_offsets, const int32_t* col_ids, int64_t n, int64_t nnz,
+                                          int32_t root, int32_t* parent_dev, int32_t* level_dev, void* stream) {
+    using namespace bfsrt;
+    if (!row_offsets || (nnz > 0 && !col_ids)) return fail(BFS_ERR_INVALID, "row_offsets / col_ids must not be NULL");
+    if (n < 1 || n > bfsk::kStaticMaxN)
+        return fail(BFS_ERR_INVALID, "bfs_run_csr_noalloc: n must lie in [1, " + std::to_string(bfsk::kStaticMaxN) +
+                                         "] (its scratch is a fixed device array)");
+    if (nnz < 0 || nnz > bfsk::kStaticMaxNnz)
+        return fail(BFS_ERR_INVALID, "bfs_run_csr_noalloc: nnz must lie in [0, " +
+                                         std::to_string(bfsk::kStaticMaxNnz) + "] (its scratch is a fixed device array)");
+    if (root < 0 || (int64_t)root >= n) return fail(BFS_ERR_INVALID, "root outside [0, n)");
+    int dev = 0;
+    BFS_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(BFS_ERR_UNSUPPORTED, "device index above 63");
+    void* base = nullptr;
+    int grid = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            // once per device, with that device current: the host-side name of the
+            // array is not a device address, so fetch the real one
+            void* ptr = nullptr;
+            BFS_CUDA_TRY(cudaGetSymbolAddress(&ptr, bfsk::g_noalloc_scratch));
+            int sms = 0, occ = 0;
+            BFS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            BFS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bfsk::bfs_single_kernel, bfsk::kBlock, 0));
+            if (occ < 1) return fail(BFS_ERR_UNSUPPORTED, "BFS kernel cannot be resident on this device");
+            g_noalloc_sms[dev] = sms;
+            g_noalloc_grid[dev] = occ * sms;
+            g_noalloc_ptr[dev] = ptr;
+        }
+        base = g_noalloc_ptr[dev];
+        grid = g_noalloc_grid[dev];
+    }
+    unsigned char* b = reinterpret_cast<unsigned char*>(base);
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long W = (n + 31) / 32;
+    bfsk::SingleParams p;
+    memset(&p, 0, sizeof p);
+    p.off = reinterpret_cast<const long long*>(row_offsets);
+    p.cols = col_ids;
+    p.isolated = reinterpret_cast<const unsigned*>(b + bfsk::kStaticIsoOff);
+    p.n = n;
+    p.nnz = nnz;
+    p.W = W;
+    p.parent = parent_dev;
+    p.level = level_dev;
+    p.visited = reinterpret_cast<unsigned*>(b + bfsk::kStaticVisOff);
+    p.front0 = reinterpret_cast<unsigned*>(b + bfsk::kStaticF0Off);
+    p.front1 = reinterpret_cast<unsigned*>(b + bfsk::kStaticF1Off);
+    p.queue0 = reinterpret_cast<int*>(b + bfsk::kStaticQ0Off);
+    p.queue1 = reinterpret_cast<int*>(b + bfsk::kStaticQ1Off);
+    p.tasks = reinterpret_cast<bfsk::Task*>(b + bfsk::kStaticTaskOff);
+    p.task_cap = bfsk::kStaticTasks;
+    p.ctrl = reinterpret_cast<bfsk::Ctrl*>(b + bfsk::kStaticCtrlOff);
+    p.rec = reinterpret_cast<bfs_level_record*>(b + bfsk::kStaticRecOff);
+    p.rec_cap = bfsk::kStaticRec;
+    p.root0 = root;
+    p.nroots = 1;
+    p.mode = BFS_MODE_DO;
+    p.alpha = 14;
+    p.beta = 24;
+    p.parent_mode = BFS_PARENT_ANY;
+    p.big_deg = 96;
+    p.timeout_ns = 10000ull * 1000000ull;
+    p.expected = (unsigned)grid;
+    const int ig = (int)std::min<long long>((W + 255) / 256, (long long)g_noalloc_sms[dev] * 4);
+    bfsk::k_static_isolated<<<ig > 0 ? ig : 1, 256, 0, s>>>(p.off, n, W, const_cast<unsigned*>(p.isolated));
+    BFS_CUDA_TRY(cudaGetLastError());
+    BFS_CUDA_TRY(cudaMemsetAsync(p.ctrl, 0, sizeof(bfsk::Ctrl), s));
+    void* args[] = {&p};
+    BFS_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)bfsk::bfs_single_kernel, dim3(grid), dim3(bfsk::kBlock),
+                                             args, 0, s));
+    return BFS_OK;
+}
