@@ -166,9 +166,11 @@ static int or_has_edge(const int64_t* off, const int32_t* cols, int32_t u, int32
  *   5 the reached set is exactly the connected component of root (label[]
  *     from or_components) and unreached vertices carry parent = level = -1.
  * 2 gives dist <= level along the parent chain; 3 gives level <= dist along a
- * shortest path; together level = dist.  `parent` may be NULL (skips 2's
- * parent clauses).  Returns 0 if valid, else (code << 40) | vertex where code
- * is the failed invariant.
+ * shortest path; together level = dist.  `parent` may be NULL: then 2 asks
+ * instead that every reached v != root has some neighbour at level[v] - 1 and
+ * that only the root sits at level 0, which gives the same chain (dist <=
+ * level) without naming the parents.  Returns 0 if valid, else
+ * (code << 40) | vertex where code is the failed invariant.
  */
 int64_t or_certify(int64_t n, const int64_t* off, const int32_t* cols, int32_t root,
                    const int32_t* parent, const int32_t* level, const int32_t* label) {
@@ -190,6 +192,11 @@ int64_t or_certify(int64_t n, const int64_t* off, const int32_t* cols, int32_t r
                 if (p < 0 || p >= n) return ((int64_t)2 << 40) | v;
                 if (!or_has_edge(off, cols, p, (int32_t)v)) return ((int64_t)2 << 40) | v;
                 if (level[p] != level[v] - 1) return ((int64_t)2 << 40) | v;
+            } else {
+                int has_pred = 0;
+                for (int64_t k = off[v]; k < off[v + 1] && !has_pred; k++)
+                    if (level[cols[k]] == level[v] - 1) has_pred = 1;
+                if (!has_pred) return ((int64_t)2 << 40) | v;
             }
         }
         for (int64_t k = off[v]; k < off[v + 1]; k++) {

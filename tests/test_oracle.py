@@ -330,3 +330,21 @@ def test_dcsc_round_trip_random():
         want = {(u, int(v)) for u in range(c.n) for v in c.cols[c.offsets[u]:c.offsets[u + 1]]}
         assert got == want
         assert np.all(np.diff(CP) > 0)
+
+
+def test_certificate_without_parents_needs_predecessors():
+    """Level-only certification: levels that are too small pass the edge-span and
+    component checks, so the certificate must also find a predecessor one level
+    closer for every reached vertex."""
+    g = graphgen.rmat(9, seed=1009)
+    c = csr(g)
+    root = int(graphgen.pick_roots(g, 1, 5)[0])
+    lv = oracle.levels(c, root)
+    lab = oracle.components(c)
+    assert oracle.certify(c, root, lv, None, lab) == (0, -1)
+    flat = np.where(lv > 0, 1, lv).astype(np.int32)       # every reached vertex at level 1
+    assert (lv > 1).any()
+    assert oracle.certify(c, root, flat, None, lab)[0] == 2
+    zero = lv.copy()
+    zero[np.flatnonzero(lv == 1)[0]] = 0                   # a second vertex at level 0
+    assert oracle.certify(c, root, zero, None, lab)[0] == 2
