@@ -63,6 +63,8 @@ struct MultiWork {
     void* tasks = nullptr;                // bfsk::MTask[task_cap]
     long long task_cap = 0;
     void* lanes = nullptr;                // bfsk::LaneTable
+    int* q0 = nullptr;                    // [n+64] vertex queues (frontier / touched)
+    int* q1 = nullptr;
     size_t bytes = 0;
     int grid = 0, block = 0;
 };
@@ -132,16 +134,17 @@ void multi_release(bfs_graph* g);
 bfs_status multi_alloc(bfs_graph* g, MultiWork& w, cudaStream_t s);
 void multi_free(bfs_graph* g, MultiWork& w);
 
-// Stepped multi-source driver used by the server (bfs_multi.cu).  The host
-// keeps a mirror of the lane table; every call is asynchronous on `s`.
-bfs_status ms_step_reset(bfs_graph* g, MultiWork& w, cudaStream_t s);
-bfs_status ms_step_admit(bfs_graph* g, MultiWork& w, const void* lane_table_host, unsigned long long newmask,
-                         cudaStream_t s);
-bfs_status ms_step_drop(bfs_graph* g, MultiWork& w, unsigned long long mask, cudaStream_t s);
-// ctrl_pinned: host (pinned) copy of the slot's control block, filled at the end of the level
-bfs_status ms_step_iterate(bfs_graph* g, MultiWork& w, int iter, int dir, unsigned long long active,
-                           void* ctrl_pinned, cudaStream_t s);
+// Server driver (bfs_multi.cu): one persistent launch per step of a slot.
 size_t ms_lane_table_bytes();
 void ms_lane_table_set(void* table_host, int lane, int32_t* row, int start, int root);
+int ms_serve_max_grid(bfs_graph* g, MultiWork& w);
+bfs_status ms_serve_reset(bfs_graph* g, MultiWork& w, cudaStream_t s);
+// Admit `newmask` lanes (lane table copied from lane_table_host), clear the
+// stale bits of `drop` lanes, then run up to max_iters levels of `active`
+// lanes from iteration iter0 on `grid` CTAs; the slot's control block is
+// copied to ctrl_pinned (host, pinned) when the launch ends.
+bfs_status ms_serve_launch(bfs_graph* g, MultiWork& w, const void* lane_table_host, unsigned long long newmask,
+                           unsigned long long drop, unsigned long long active, int iter0, int max_iters, int grid,
+                           void* ctrl_pinned, cudaStream_t s);
 
 }  // namespace bfsrt

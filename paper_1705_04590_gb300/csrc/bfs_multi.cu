@@ -59,17 +59,51 @@ __device__ __forceinline__ void load_lanes(const MultiParams& p, LaneSmem& L) {
 }
 
 // ---------------------------------------------------------------- phases
+//
+// The union frontier is kept twice: as masks (front[v] != 0) and as a queue of
+// its vertices (fq); the vertices that gain lane bits during a level are
+// listed once each in the touched queue (tq), which becomes the next fq.  So a
+// top-down level and the apply step cost O(frontier + touched), not O(n); only
+// bottom-up levels sweep all vertices (they are chosen when the frontier is
+// large).  The two queues alternate: qsel picks fq.
 
-// Top-down push over vertices with front != 0 (warp-balanced gather; heavy
-// rows become chunk tasks processed by ms_tasks_phase after a barrier).
-__device__ void ms_td_phase(const MultiParams& p, MCtrl* c, int slot) {
+// Warp-aggregated append of `v` (where `want`) to queue q with counter *len.
+__device__ __forceinline__ void q_append(int* q, unsigned long long* len, bool want, int v) {
+    const unsigned m = __ballot_sync(kMFull, want);
+    if (m) {
+        const int leader = __ffs(m) - 1;
+        unsigned long long b = 0;
+        if (lane_id() == leader) b = atomicAdd(len, (unsigned long long)__popc(m));
+        b = __shfl_sync(kMFull, b, leader);
+        if (want) q[b + __popc(m & lanemask_lt())] = v;
+    }
+}
+
+// Push lane bits along edge (v -> u); record u the first time its next mask
+// becomes nonzero.  All lanes call.
+__device__ __forceinline__ void ms_push(const MultiParams& p, unsigned long long f, int u, bool act, int* tq,
+                                        unsigned long long* tlen) {
+    bool first = false;
+    if (act) {
+        const unsigned long long nb = f & ~ldcg64(p.seen + u);
+        if (nb) first = atomicOr(p.next + u, nb) == 0ull;
+    }
+    q_append(tq, tlen, first, u);
+}
+
+// Top-down push over the frontier queue (warp-balanced gather; heavy rows
+// become chunk tasks processed by ms_tasks_phase after a barrier).
+__device__ void ms_td_phase(const MultiParams& p, MCtrl* c, int slot, const int* fq, long long flen, int* tq,
+                            unsigned long long* tlen) {
     const int lane = lane_id();
     const long long gw = m_gtid() >> 5, nw = m_gthreads() >> 5;
-    for (long long base = gw * 32; base < p.n; base += nw * 32) {
-        const long long v = base + lane;
+    for (long long base = gw * 32; base < flen; base += nw * 32) {
+        const long long i = base + lane;
+        int v = 0;
         unsigned long long f = 0;
         long long s = 0, e = 0;
-        if (v < p.n) {
+        if (i < flen) {
+            v = __ldcg(fq + i);
             f = ldcg64(p.front + v);
             if (f) {
                 s = __ldg(p.off + v);
@@ -77,24 +111,30 @@ __device__ void ms_td_phase(const MultiParams& p, MCtrl* c, int slot) {
             }
         }
         const long long deg = e - s;
-        int mydeg = 0;
-        if (deg > p.big_deg) {
-            const long long nch = (deg + kMChunk - 1) / kMChunk;
-            const unsigned long long t0 = atomicAdd(&c->ntask[slot], (unsigned long long)nch);
-            for (long long k = 0; k < nch; k++) {
+        const bool big = deg > p.big_deg;
+        const int mydeg = big ? 0 : (int)deg;
+        unsigned bm = __ballot_sync(kMFull, big);
+        while (bm) {
+            const int L = __ffs(bm) - 1;
+            bm &= bm - 1;
+            const long long bs = __shfl_sync(kMFull, s, L), be = __shfl_sync(kMFull, e, L);
+            const int bv = __shfl_sync(kMFull, v, L);
+            const long long nch = (be - bs + kMChunk - 1) / kMChunk;
+            unsigned long long t0 = 0;
+            if (lane == 0) t0 = atomicAdd(&c->ntask[slot], (unsigned long long)nch);
+            t0 = __shfl_sync(kMFull, t0, 0);
+            for (long long k = lane; k < nch; k += 32) {
                 const long long ti = (long long)t0 + k;
                 if (ti < p.task_cap) {
                     MTask t;
-                    t.start = s + k * kMChunk;
-                    t.len = (int)min((long long)kMChunk, e - t.start);
-                    t.v = (int)v;
+                    t.start = bs + k * kMChunk;
+                    t.len = (int)min((long long)kMChunk, be - t.start);
+                    t.v = bv;
                     p.tasks[ti] = t;
                 } else {
                     atomicMax(&c->b.status, kDevOverflow);
                 }
             }
-        } else {
-            mydeg = (int)deg;
         }
         const int incl = warp_inclusive_scan(mydeg);
         const int total = __shfl_sync(kMFull, incl, 31);
@@ -110,16 +150,14 @@ __device__ void ms_td_phase(const MultiParams& p, MCtrl* c, int slot) {
             const long long sj = __shfl_sync(kMFull, s, j);
             const int exj = __shfl_sync(kMFull, excl, j);
             const unsigned long long fj = __shfl_sync(kMFull, f, j);
-            if (k < total) {
-                const int u = __ldg(p.cols + sj + (k - exj));
-                const unsigned long long nb = fj & ~ldcg64(p.seen + u);
-                if (nb) atomicOr(p.next + u, nb);
-            }
+            const bool act = k < total;
+            const int u = act ? __ldg(p.cols + sj + (k - exj)) : 0;
+            ms_push(p, fj, u, act, tq, tlen);
         }
     }
 }
 
-__device__ void ms_tasks_phase(const MultiParams& p, MCtrl* c, int slot) {
+__device__ void ms_tasks_phase(const MultiParams& p, MCtrl* c, int slot, int* tq, unsigned long long* tlen) {
     const int lane = lane_id();
     const long long gw = m_gtid() >> 5, nw = m_gthreads() >> 5;
     const long long nt = min((long long)ld_acquire64(&c->ntask[slot]), p.task_cap);
@@ -128,10 +166,11 @@ __device__ void ms_tasks_phase(const MultiParams& p, MCtrl* c, int slot) {
         const long long start = (long long)(unsigned)raw.x | ((long long)raw.y << 32);
         const int len = raw.z, v = raw.w;
         const unsigned long long f = ldcg64(p.front + v);
-        for (int k = lane; k < len; k += 32) {
-            const int u = __ldg(p.cols + start + k);
-            const unsigned long long nb = f & ~ldcg64(p.seen + u);
-            if (nb) atomicOr(p.next + u, nb);
+        for (int k0 = 0; k0 < len; k0 += 32) {
+            const int k = k0 + lane;
+            const bool act = k < len;
+            const int u = act ? __ldg(p.cols + start + k) : 0;
+            ms_push(p, f, u, act, tq, tlen);
         }
     }
 }
@@ -139,7 +178,7 @@ __device__ void ms_tasks_phase(const MultiParams& p, MCtrl* c, int slot) {
 // Bottom-up pull: a warp owns 32 consecutive vertices; each lane ORs the
 // frontier masks of its first 8 neighbours, then rows with lanes still
 // missing continue warp-cooperatively 32 neighbours at a time.
-__device__ void ms_bu_phase(const MultiParams& p, unsigned long long active) {
+__device__ void ms_bu_phase(const MultiParams& p, unsigned long long active, int* tq, unsigned long long* tlen) {
     const int lane = lane_id();
     const long long gw = m_gtid() >> 5, nw = m_gthreads() >> 5;
     for (long long base = gw * 32; base < p.n; base += nw * 32) {
@@ -184,44 +223,49 @@ __device__ void ms_bu_phase(const MultiParams& p, unsigned long long active) {
         }
         const unsigned long long nb = acc & miss;
         if (nb) p.next[u] = nb;
+        q_append(tq, tlen, nb != 0ull, (int)u);
     }
 }
 
-// seen |= next, front = next, next = 0, per-lane levels; counts the new
-// frontier (n_f, m_f), the degree of vertices every active lane has now seen
-// (subtracted from m_u) and which lanes found anything.
-__device__ void ms_apply_phase(const MultiParams& p, MCtrl* c, int slot, int iter, unsigned long long active,
-                               const LaneSmem& L) {
+// Apply, part 1: the old frontier leaves front (its vertices are listed in fq).
+__device__ void ms_retire_phase(const MultiParams& p, const int* fq, long long flen) {
     const long long tid = m_gtid(), nth = m_gthreads();
-    unsigned long long an = 0, am = 0, adone = 0, found = 0;
-    for (long long v = tid; v < p.n; v += nth) {
+    for (long long i = tid; i < flen; i += nth) p.front[__ldcg(fq + i)] = 0ull;
+}
+
+// Apply, part 2, over the touched vertices: seen |= next, front = next, next = 0,
+// per-lane levels; counts the new frontier (n_f, m_f), the degree of vertices
+// every active lane has now seen (subtracted from m_u) and which lanes found
+// anything.
+__device__ void ms_apply_phase(const MultiParams& p, MCtrl* c, int slot, int iter, unsigned long long active,
+                               const LaneSmem& L, const int* tq, long long tlen) {
+    const long long tid = m_gtid(), nth = m_gthreads();
+    unsigned long long am = 0, adone = 0, found = 0;
+    for (long long i = tid; i < tlen; i += nth) {
+        const int v = __ldcg(tq + i);
         const unsigned long long x = ldcg64(p.next + v);
-        if (x) {
-            p.next[v] = 0ull;
-            const unsigned long long s = ldcg64(p.seen + v);
-            p.seen[v] = s | x;
-            p.front[v] = x;
-            found |= x;
-            const long long deg = __ldg(p.off + v + 1) - __ldg(p.off + v);
-            an += 1;
-            am += (unsigned long long)deg;
-            if ((s & active) != active && ((s | x) & active) == active) adone += (unsigned long long)deg;
-            unsigned long long bits = x;
-            while (bits) {
-                const int i = __ffsll((long long)bits) - 1;
-                bits &= bits - 1;
-                L.rows[i][v] = iter + 1 - L.start[i];
-            }
-        } else if (ldcg64(p.front + v)) {
-            p.front[v] = 0ull;
+        p.next[v] = 0ull;
+        const unsigned long long s = ldcg64(p.seen + v);
+        p.seen[v] = s | x;
+        p.front[v] = x;
+        found |= x;
+        const long long deg = __ldg(p.off + v + 1) - __ldg(p.off + v);
+        am += (unsigned long long)deg;
+        if ((s & active) != active && ((s | x) & active) == active) adone += (unsigned long long)deg;
+        unsigned long long bits = x;
+        while (bits) {
+            const int i2 = __ffsll((long long)bits) - 1;
+            bits &= bits - 1;
+            L.rows[i2][v] = iter + 1 - L.start[i2];
         }
     }
     found = warp_or64(found);
     if (lane_id() == 0 && found) atomicOr(&c->found[slot], found);
-    block_add4(an, am, adone, 0, &c->accn[slot], &c->accm[slot], &c->mdone[slot], nullptr);
+    block_add4(0, am, adone, 0, nullptr, &c->accm[slot], &c->mdone[slot], nullptr);
+    if (tid == 0) c->accn[slot] = (unsigned long long)tlen;
 }
 
-// Clear the three masks (grid-stride).
+// Clear the three masks and both queue counters (grid-stride).
 __device__ void ms_clear_phase(const MultiParams& p) {
     const long long tid = m_gtid(), nth = m_gthreads();
     for (long long v = tid; v < p.n; v += nth) {
@@ -243,14 +287,23 @@ __device__ void ms_fill_rows(const MultiParams& p, unsigned long long mask, cons
     }
 }
 
-// Seed lanes in `mask` at their roots (atomics: several lanes may share a root).
-__device__ void ms_seed_phase(const MultiParams& p, unsigned long long mask, const LaneSmem& L) {
-    const long long tid = m_gtid();
-    if (tid < 64 && ((mask >> tid) & 1ull)) {
-        const int r = p.roots[tid];
-        atomicOr(p.seen + r, 1ull << tid);
-        atomicOr(p.front + r, 1ull << tid);
-        L.rows[tid][r] = 0;
+// Seed lanes in `mask` at their roots (atomics: several lanes may share a
+// root); a root not yet in the frontier joins the frontier queue.  Run by the
+// first warp (64 lanes at most -> two rounds).
+__device__ void ms_seed_phase(const MultiParams& p, unsigned long long mask, const LaneSmem& L, int* fq,
+                              unsigned long long* flen) {
+    if (m_gtid() >= 32) return;
+    for (int i0 = 0; i0 < 64; i0 += 32) {
+        const int i = i0 + lane_id();
+        bool add = false;
+        int r = 0;
+        if ((mask >> i) & 1ull) {
+            r = p.roots[i];
+            atomicOr(p.seen + r, 1ull << i);
+            add = atomicOr(p.front + r, 1ull << i) == 0ull;
+            L.rows[i][r] = 0;
+        }
+        q_append(fq, flen, add, r);
     }
 }
 
@@ -271,10 +324,10 @@ __global__ void __launch_bounds__(kMBlock, 2) bfs_multi_kernel(MultiParams p) {
     ms_clear_phase(p);
     ms_fill_rows(p, active, L);
     if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
-    ms_seed_phase(p, active, L);
+    ms_seed_phase(p, active, L, p.q0, &c->qlen[0]);
     if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
-    // level-0 frontier statistics from the (few) distinct roots, identical in every CTA
-    long long nf = 0, mf = 0, mu = p.nnz;
+    // level-0 statistics from the (few) distinct roots, identical in every CTA
+    long long mf = 0, mu = p.nnz;
     for (int i = 0; i < 64; i++) {
         if (!((active >> i) & 1ull)) continue;
         const int r = p.roots[i];
@@ -283,38 +336,44 @@ __global__ void __launch_bounds__(kMBlock, 2) bfs_multi_kernel(MultiParams p) {
             if (((active >> j) & 1ull) && p.roots[j] == r) dup = true;
         if (dup) continue;
         const long long deg = __ldg(p.off + r + 1) - __ldg(p.off + r);
-        nf += 1;
         mf += deg;
         if ((ldcg64(p.seen + r) & active) == active) mu -= deg;
     }
-    int prev = 0;
+    int prev = 0, qsel = 0;
     for (int it = 0;; it++) {
         // counters of iteration `it` accumulate in slot it % 3 and are read by
         // every CTA after the closing barrier; the slot of iteration it + 1 is
         // cleared now (its last readers passed a barrier of iteration it - 1)
         const int slot = it % 3, sfree = (it + 1) % 3;
         if (blockIdx.x == 0 && threadIdx.x == 0) c->zero_slot(sfree);
-        const int dir = ms_decide(p, prev, nf, mf, mu);
+        int* fq = qsel ? p.q1 : p.q0;
+        int* tq = qsel ? p.q0 : p.q1;
+        const long long flen = (long long)ld_acquire64(&c->qlen[qsel]);
+        unsigned long long* tlen = &c->qlen[qsel ^ 1];
+        const int dir = ms_decide(p, prev, flen, mf, mu);
         if (dir == 0) {
-            ms_td_phase(p, c, slot);
+            ms_td_phase(p, c, slot, fq, flen, tq, tlen);
             if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
             if (ld_acquire64(&c->ntask[slot]) > 0) {
-                ms_tasks_phase(p, c, slot);
+                ms_tasks_phase(p, c, slot, tq, tlen);
                 if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
             }
         } else {
-            ms_bu_phase(p, active);
+            ms_bu_phase(p, active, tq, tlen);
             if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
         }
-        ms_apply_phase(p, c, slot, it, active, L);
+        ms_retire_phase(p, fq, flen);
         if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
-        const long long nf2 = (long long)ld_acquire64(&c->accn[slot]);
-        if (nf2 == 0) {
+        const long long nt = (long long)ld_acquire64(tlen);
+        ms_apply_phase(p, c, slot, it, active, L, tq, nt);
+        if (m_gtid() == 0) c->qlen[qsel] = 0;   // the old frontier's queue collects the next touched set
+        if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
+        qsel ^= 1;
+        if (nt == 0) {
             if (blockIdx.x == 0 && threadIdx.x == 0) c->iterations = it + 1;
             break;
         }
         mu -= (long long)ld_acquire64(&c->mdone[slot]);
-        nf = nf2;
         mf = (long long)ld_acquire64(&c->accm[slot]);
         prev = dir;
     }
@@ -349,53 +408,94 @@ __global__ void ms_parent_kernel(MultiParams p, int* const* prow) {
     }
 }
 
-// ---------------------------------------------------------------- stepped drivers (server)
-
-__global__ void __launch_bounds__(kMBlock) ms_admit_kernel(MultiParams p, unsigned long long newmask) {
-    __shared__ LaneSmem L;
-    load_lanes(p, L);
-    ms_fill_rows(p, newmask, L);
-}
-
-__global__ void ms_seed_kernel(MultiParams p, unsigned long long newmask) {
-    __shared__ LaneSmem L;
-    load_lanes(p, L);
-    ms_seed_phase(p, newmask, L);
-}
-
+// Clear the three masks of a slot (used when a server slot is created).
 __global__ void __launch_bounds__(kMBlock) ms_clear_kernel(MultiParams p) { ms_clear_phase(p); }
 
-__global__ void __launch_bounds__(kMBlock) ms_td_kernel(MultiParams p, int slot) { ms_td_phase(p, p.ctrl, slot); }
+// ---------------------------------------------------------------- server driver
 
-__global__ void __launch_bounds__(kMBlock) ms_tasks_kernel(MultiParams p, int slot) {
-    ms_tasks_phase(p, p.ctrl, slot);
-}
-
-__global__ void __launch_bounds__(kMBlock) ms_bu_kernel(MultiParams p, unsigned long long active) {
-    ms_bu_phase(p, active);
-}
-
-__global__ void __launch_bounds__(kMBlock) ms_apply_kernel(MultiParams p, int slot, int iter,
-                                                          unsigned long long active) {
+// One launch of a server slot: optional admission of new lanes (drop the
+// stale bits of `drop` lanes, fill new rows with -1, seed new roots), then
+// levels iter0, iter0+1, ... for all `active` lanes until a lane's frontier
+// comes back empty (its result is final), the union frontier is empty, or
+// max_iters levels ran.  The direction per level follows the union frontier
+// (top-down -> bottom-up when m_f * alpha > nnz / 2, back when n_f * beta < n;
+// the per-lane unvisited degree m_u is not tracked when lanes start at
+// different levels).  Results for the host: s_done, s_finished, s_nf, s_mf,
+// s_dir in the control block (which persists across launches of the slot).
+__global__ void __launch_bounds__(kMBlock, 2) bfs_serve_kernel(MultiParams p, int iter0, int max_iters,
+                                                                unsigned long long newmask,
+                                                                unsigned long long drop) {
     __shared__ LaneSmem L;
     load_lanes(p, L);
-    ms_apply_phase(p, p.ctrl, slot, iter, active, L);
-}
-
-// Drop lanes in `mask` from every vertex's masks (lanes that finished or are being reused).
-__global__ void __launch_bounds__(kMBlock) ms_drop_kernel(MultiParams p, unsigned long long mask) {
+    MCtrl* c = p.ctrl;
+    const unsigned long long active = p.active;
     const long long tid = m_gtid(), nth = m_gthreads();
-    const unsigned long long keep = ~mask;
-    for (long long v = tid; v < p.n; v += nth) {
-        const unsigned long long s = p.seen[v];
-        if (s & mask) p.seen[v] = s & keep;
-        const unsigned long long f = p.front[v];
-        if (f & mask) p.front[v] = f & keep;
+    int qsel = c->s_qsel;
+    if (drop) {
+        // lanes being reused: remove their previous query's bits
+        const unsigned long long keep = ~drop;
+        for (long long v = tid; v < p.n; v += nth) {
+            const unsigned long long s = p.seen[v];
+            if (s & drop) p.seen[v] = s & keep;
+            const unsigned long long f = p.front[v];
+            if (f & drop) p.front[v] = f & keep;
+        }
     }
-}
-
-__global__ void ms_zero_slot_kernel(MCtrl* c, int slot) {
-    if (threadIdx.x == 0) c->zero_slot(slot);
+    if (newmask | drop) {
+        ms_fill_rows(p, newmask, L);
+        if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
+        ms_seed_phase(p, newmask, L, qsel ? p.q1 : p.q0, &c->qlen[qsel]);
+        if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
+    }
+    long long mf = c->s_mf;
+    int prev = c->s_dir;
+    int it = iter0, done = 0;
+    long long nt = 0;
+    unsigned long long finished = 0;
+    for (; done < max_iters; it++) {
+        const int slot = it % 3, sfree = (it + 1) % 3;
+        if (blockIdx.x == 0 && threadIdx.x == 0) c->zero_slot(sfree);
+        int* fq = qsel ? p.q1 : p.q0;
+        int* tq = qsel ? p.q0 : p.q1;
+        const long long flen = (long long)ld_acquire64(&c->qlen[qsel]);
+        unsigned long long* tlen = &c->qlen[qsel ^ 1];
+        int dir;
+        if (p.mode == BFS_MODE_TD_ONLY) dir = 0;
+        else if (p.mode == BFS_MODE_BU_ONLY) dir = 1;
+        else if (prev == 0) dir = (mf * (long long)p.alpha > p.nnz / 2) ? 1 : 0;
+        else dir = (flen * (long long)p.beta < p.n) ? 0 : 1;
+        if (dir == 0) {
+            ms_td_phase(p, c, slot, fq, flen, tq, tlen);
+            if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
+            if (ld_acquire64(&c->ntask[slot]) > 0) {
+                ms_tasks_phase(p, c, slot, tq, tlen);
+                if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
+            }
+        } else {
+            ms_bu_phase(p, active, tq, tlen);
+            if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
+        }
+        ms_retire_phase(p, fq, flen);
+        if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
+        nt = (long long)ld_acquire64(tlen);
+        ms_apply_phase(p, c, slot, it, active, L, tq, nt);
+        if (tid == 0) c->qlen[qsel] = 0;
+        if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
+        qsel ^= 1;
+        done++;
+        prev = dir;
+        mf = (long long)ld_acquire64(&c->accm[slot]);
+        finished = active & ~ld_acquire64(&c->found[slot]);
+        if (finished || nt == 0) break;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        c->s_done = done;
+        c->s_finished = finished;
+        c->s_nf = nt;
+        c->s_mf = mf;
+        c->s_dir = prev;
+        c->s_qsel = qsel;
+    }
 }
 
 }  // namespace bfsk
@@ -420,13 +520,16 @@ bfs_status multi_alloc(bfs_graph* g, MultiWork& w, cudaStream_t s) {
     w.ctrl = g->mem.alloc(sizeof(MCtrl), s);
     w.tasks = g->mem.alloc(sizeof(MTask) * (size_t)task_cap, s);
     w.lanes = g->mem.alloc(sizeof(bfsk::LaneTable), s);
+    w.q0 = (int*)g->mem.alloc(sizeof(int) * (size_t)(g->n + 64), s);
+    w.q1 = (int*)g->mem.alloc(sizeof(int) * (size_t)(g->n + 64), s);
     w.task_cap = task_cap;
-    if (!w.seen || !w.front || !w.next || !w.ctrl || !w.tasks || !w.lanes) {
+    if (!w.seen || !w.front || !w.next || !w.ctrl || !w.tasks || !w.lanes || !w.q0 || !w.q1) {
         w.ready = true;
         multi_free(g, w);
         return fail(BFS_ERR_OOM, "multi-source work buffers: device allocation failed");
     }
-    w.bytes = 3 * nb + sizeof(MCtrl) + sizeof(MTask) * (size_t)task_cap + sizeof(bfsk::LaneTable);
+    w.bytes = 3 * nb + sizeof(MCtrl) + sizeof(MTask) * (size_t)task_cap + sizeof(bfsk::LaneTable) +
+              2 * sizeof(int) * (size_t)(g->n + 64);
     int occ = 0;
     BFS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bfsk::bfs_multi_kernel, bfsk::kMBlock, 0));
     if (occ < 1) return fail(BFS_ERR_UNSUPPORTED, "multi-source kernel cannot be resident");
@@ -447,6 +550,8 @@ void multi_free(bfs_graph* g, MultiWork& w) {
     g->mem.release(w.ctrl, sizeof(MCtrl), nullptr);
     g->mem.release(w.tasks, sizeof(MTask) * (size_t)w.task_cap, nullptr);
     g->mem.release(w.lanes, sizeof(bfsk::LaneTable), nullptr);
+    g->mem.release(w.q0, sizeof(int) * (size_t)(g->n + 64), nullptr);
+    g->mem.release(w.q1, sizeof(int) * (size_t)(g->n + 64), nullptr);
     w = MultiWork();
 }
 
@@ -464,6 +569,8 @@ static MultiParams multi_params(bfs_graph* g, MultiWork& w, const bfs_options& o
     p.front = w.front;
     p.next = w.next;
     p.ctrl = reinterpret_cast<MCtrl*>(w.ctrl);
+    p.q0 = w.q0;
+    p.q1 = w.q1;
     p.tasks = reinterpret_cast<MTask*>(w.tasks);
     p.task_cap = w.task_cap;
     bfsk::LaneTable* lt = reinterpret_cast<bfsk::LaneTable*>(w.lanes);
@@ -519,7 +626,7 @@ bfs_status multi_collect_status(bfs_graph* g, cudaStream_t s) {
     return BFS_OK;
 }
 
-// ---------------------------------------------------------------- stepped driver (server)
+// ---------------------------------------------------------------- server driver (host side)
 
 size_t ms_lane_table_bytes() { return sizeof(bfsk::LaneTable); }
 
@@ -531,60 +638,32 @@ void ms_lane_table_set(void* table_host, int lane, int32_t* row, int start, int 
     t->roots[lane] = root;
 }
 
-static bfs_options server_opts() {
+int ms_serve_max_grid(bfs_graph* g, MultiWork& w) { (void)g; return w.grid; }
+
+bfs_status ms_serve_reset(bfs_graph* g, MultiWork& w, cudaStream_t s) {
     bfs_options o;
     bfs_options_default(&o);
-    return o;
-}
-
-bfs_status ms_step_reset(bfs_graph* g, MultiWork& w, cudaStream_t s) {
-    MultiParams p = multi_params(g, w, server_opts());
+    MultiParams p = multi_params(g, w, o);
     bfsk::ms_clear_kernel<<<w.grid, w.block, 0, s>>>(p);
     BFS_CUDA_TRY(cudaGetLastError());
     BFS_CUDA_TRY(cudaMemsetAsync(w.ctrl, 0, sizeof(MCtrl), s));
     return BFS_OK;
 }
 
-bfs_status ms_step_admit(bfs_graph* g, MultiWork& w, const void* lane_table_host, unsigned long long newmask,
-                         cudaStream_t s) {
-    BFS_CUDA_TRY(cudaMemcpyAsync(w.lanes, lane_table_host, sizeof(bfsk::LaneTable), cudaMemcpyHostToDevice, s));
-    MultiParams p = multi_params(g, w, server_opts());
-    bfsk::ms_admit_kernel<<<w.grid, w.block, 0, s>>>(p, newmask);
-    BFS_CUDA_TRY(cudaGetLastError());
-    bfsk::ms_seed_kernel<<<1, 64, 0, s>>>(p, newmask);
-    BFS_CUDA_TRY(cudaGetLastError());
-    return BFS_OK;
-}
-
-bfs_status ms_step_drop(bfs_graph* g, MultiWork& w, unsigned long long mask, cudaStream_t s) {
-    MultiParams p = multi_params(g, w, server_opts());
-    bfsk::ms_drop_kernel<<<w.grid, w.block, 0, s>>>(p, mask);
-    BFS_CUDA_TRY(cudaGetLastError());
-    return BFS_OK;
-}
-
-// One level for every active lane: direction phase(s) then apply; the
-// counters of the level are copied into `counters_pinned` (host pinned).
-bfs_status ms_step_iterate(bfs_graph* g, MultiWork& w, int iter, int dir, unsigned long long active,
+bfs_status ms_serve_launch(bfs_graph* g, MultiWork& w, const void* lane_table_host, unsigned long long newmask,
+                           unsigned long long drop, unsigned long long active, int iter0, int max_iters, int grid,
                            void* ctrl_pinned, cudaStream_t s) {
-    MultiParams p = multi_params(g, w, server_opts());
+    bfs_options o;
+    bfs_options_default(&o);
+    MultiParams p = multi_params(g, w, o);
     p.active = active;
-    const int slot = 0;
-    MCtrl* c = reinterpret_cast<MCtrl*>(w.ctrl);
-    bfsk::ms_zero_slot_kernel<<<1, 32, 0, s>>>(c, slot);
-    BFS_CUDA_TRY(cudaGetLastError());
-    if (dir == 0) {
-        bfsk::ms_td_kernel<<<w.grid, w.block, 0, s>>>(p, slot);
-        BFS_CUDA_TRY(cudaGetLastError());
-        bfsk::ms_tasks_kernel<<<w.grid, w.block, 0, s>>>(p, slot);
-        BFS_CUDA_TRY(cudaGetLastError());
-    } else {
-        bfsk::ms_bu_kernel<<<w.grid, w.block, 0, s>>>(p, active);
-        BFS_CUDA_TRY(cudaGetLastError());
-    }
-    bfsk::ms_apply_kernel<<<w.grid, w.block, 0, s>>>(p, slot, iter, active);
-    BFS_CUDA_TRY(cudaGetLastError());
-    BFS_CUDA_TRY(cudaMemcpyAsync(ctrl_pinned, c, sizeof(MCtrl), cudaMemcpyDeviceToHost, s));
+    grid = std::max(1, std::min(grid, w.grid));
+    p.expected = (unsigned)grid;
+    if (newmask)
+        BFS_CUDA_TRY(cudaMemcpyAsync(w.lanes, lane_table_host, sizeof(bfsk::LaneTable), cudaMemcpyHostToDevice, s));
+    void* args[] = {&p, &iter0, &max_iters, &newmask, &drop};
+    BFS_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)bfsk::bfs_serve_kernel, dim3(grid), dim3(w.block), args, 0, s));
+    BFS_CUDA_TRY(cudaMemcpyAsync(ctrl_pinned, w.ctrl, sizeof(MCtrl), cudaMemcpyDeviceToHost, s));
     return BFS_OK;
 }
 

@@ -21,6 +21,13 @@ struct MCtrl {
     unsigned long long ntask[3];   // top-down chunk tasks
     unsigned long long found[3];   // lanes that found at least one vertex
     long long iterations;
+    // server slot state carried across launches (bfs_serve_kernel)
+    long long s_done;              // iterations run by the last launch
+    unsigned long long s_finished; // lanes whose search ended in the last launch
+    long long s_nf, s_mf;          // union frontier size / degree sum after the last level
+    int s_dir;                     // direction of the last level
+    int s_qsel;                    // which queue holds the frontier
+    unsigned long long qlen[2];    // lengths of the two vertex queues (frontier / touched)
     __host__ __device__ void zero_slot(int s) {
         accn[s] = 0;
         accm[s] = 0;
@@ -48,6 +55,8 @@ struct MultiParams {
     MCtrl* ctrl;
     MTask* tasks;
     long long task_cap;
+    int* q0;                       // vertex queues, n + 64 entries each
+    int* q1;
     int* const* rows;
     const int* start;
     const int* roots;

@@ -49,6 +49,9 @@ constexpr int kDBlock = 1024;   // DCSC kernel (one CTA per vertex block)
 constexpr int kWarps = 32;      // shared-memory per-warp arrays sized for up to 1024 threads
 constexpr int kChunk = 256;    // edges per top-down chunk task
 constexpr int kStage = 256;    // per-warp shared-memory staging of next-queue entries
+#ifndef BFS_BU_PHASEB
+#define BFS_BU_PHASEB 1   // bottom-up long list: 1 = 4-lane groups, 2 = one thread per searcher
+#endif
 #ifndef BFS_MIN_BLOCKS
 #define BFS_MIN_BLOCKS 2
 #endif
@@ -239,24 +242,32 @@ __device__ void td_phase(const SingleParams& p, int d, const int* qcur, long lon
             e = __ldg(p.off + u + 1);
         }
         const long long deg = e - s;
-        int mydeg = 0;
-        if (deg > p.big_deg) {
-            const long long nch = (deg + kChunk - 1) / kChunk;
-            const unsigned long long t0 = atomicAdd(&p.ctrl->ntask[snext], (unsigned long long)nch);
-            for (long long c = 0; c < nch; c++) {
+        const bool big = deg > p.big_deg;
+        const int mydeg = big ? 0 : (int)deg;
+        // heavy rows become edge-chunk tasks; the warp writes each row's chunk
+        // descriptors together
+        unsigned bm = __ballot_sync(kFull, big);
+        while (bm) {
+            const int L = __ffs(bm) - 1;
+            bm &= bm - 1;
+            const long long bs = __shfl_sync(kFull, s, L), be = __shfl_sync(kFull, e, L);
+            const int bu = __shfl_sync(kFull, u, L);
+            const long long nch = (be - bs + kChunk - 1) / kChunk;
+            unsigned long long t0 = 0;
+            if (lane == 0) t0 = atomicAdd(&p.ctrl->ntask[snext], (unsigned long long)nch);
+            t0 = __shfl_sync(kFull, t0, 0);
+            for (long long c = lane; c < nch; c += 32) {
                 const long long ti = (long long)t0 + c;
                 if (ti < p.task_cap) {
                     Task t;
-                    t.start = s + c * kChunk;
-                    t.len = (int)min((long long)kChunk, e - t.start);
-                    t.u = u;
+                    t.start = bs + c * kChunk;
+                    t.len = (int)min((long long)kChunk, be - t.start);
+                    t.u = bu;
                     p.tasks[ti] = t;
                 } else {
                     atomicMax(&p.ctrl->b.status, kDevOverflow);
                 }
             }
-        } else {
-            mydeg = (int)deg;
         }
         const int incl = warp_inclusive_scan(mydeg);
         const int total = __shfl_sync(kFull, incl, 31);
@@ -291,11 +302,18 @@ __device__ void task_phase(const SingleParams& p, int d, long long ntask, int* q
         const int4 raw = __ldcg(reinterpret_cast<const int4*>(p.tasks + t));
         const long long start = (long long)(unsigned)raw.x | ((long long)raw.y << 32);
         const int len = raw.z, u = raw.w;
-        for (int k0 = 0; k0 < len; k0 += 32) {
-            const int k = k0 + lane;
-            const bool act = k < len;
-            const int v = act ? __ldg(p.cols + start + k) : 0;
-            td_visit(p, d, u, v, act, st, qnext, tail, acc_m);
+        // four independent edges per lane per step (coalesced across the warp)
+        for (int k0 = 0; k0 < len; k0 += 128) {
+            int v[4];
+            bool act[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int k = k0 + q * 32 + lane;
+                act[q] = k < len;
+                v[q] = act[q] ? __ldg(p.cols + start + k) : 0;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; q++) td_visit(p, d, u, v[q], act[q], st, qnext, tail, acc_m);
         }
     }
     stage_flush(p, st, qnext, tail, acc_m);
@@ -443,11 +461,19 @@ __device__ void bu_phase_a(const SingleParams& p, int d, const unsigned* fcur, u
             if (u0 >= 0) {
                 const long long rb = s0 & ~3LL;
                 const int ids[8] = {xa0.x, xa0.y, xa0.z, xa0.w, xb0.x, xb0.y, xb0.z, xb0.w};
+                // probe the first id alone (on most levels it is the hit), the rest of
+                // the window only on a miss: L2 requests, not latency, bound this loop
+                const int t0 = (int)(s0 - rb);
+                const int first_id = (t0 == 0) ? xa0.x : (t0 == 1) ? xa0.y : (t0 == 2) ? xa0.z : xa0.w;
                 unsigned hb = 0;
+                if (e0 > s0 && in_frontier(fcur, first_id)) {
+                    hb = 1u << t0;
+                } else {
 #pragma unroll
-                for (int t = 0; t < 8; t++) {
-                    const long long q = rb + t;
-                    if (q >= s0 && q < e0 && in_frontier(fcur, ids[t])) hb |= 1u << t;
+                    for (int t = 0; t < 8; t++) {
+                        const long long q = rb + t;
+                        if (t > t0 && q < e0 && in_frontier(fcur, ids[t])) hb |= 1u << t;
+                    }
                 }
                 acc_sc += 1;
                 if (hb) {
@@ -497,6 +523,49 @@ __device__ void bu_phase_a(const SingleParams& p, int d, const unsigned* fcur, u
 // group with a hit, its lowest id -- so parents stay the minimum-id ones.
 // Next-frontier and completed words are shared across warps here, hence
 // atomicOr.
+#if BFS_BU_PHASEB == 2
+__device__ void bu_phase_b(const SingleParams& p, int d, const unsigned* fcur, unsigned* fnext, const int* longlist,
+                           long long nlong, unsigned long long& acc_n, unsigned long long& acc_m,
+                           unsigned long long& acc_ex) {
+    const long long tid = gtid(), nth = gthreads();
+    const int4 z4 = make_int4(0, 0, 0, 0);
+    for (long long i = tid; i < nlong; i += nth) {
+        const int u = __ldcg(longlist + i);
+        const long long s0 = __ldg(p.off + u), e0 = __ldg(p.off + u + 1);
+        long long pos = (s0 & ~3LL) + 8;
+        long long hitpos = -1;
+        int pv = -1;
+        while (pos < e0) {
+            const int4* src = reinterpret_cast<const int4*>(p.cols + pos);
+            const int4 xa = __ldg(src);
+            const int4 xb = (pos + 4 < e0) ? __ldg(src + 1) : z4;
+            const int ids[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
+            unsigned hb = 0;
+#pragma unroll
+            for (int t = 0; t < 8; t++)
+                if (pos + t < e0 && in_frontier(fcur, ids[t])) hb |= 1u << t;
+            if (hb) {
+                const int t = __ffs(hb) - 1;
+                hitpos = pos + t;
+                pv = ids[t];
+                break;
+            }
+            pos += 8;
+        }
+        if (hitpos >= 0) {
+            acc_ex += (unsigned long long)(hitpos - s0 + 1);
+            acc_m += (unsigned long long)(e0 - s0);
+            acc_n += 1;
+            if (p.parent) p.parent[u] = pv;
+            if (p.level) p.level[u] = d + 1;
+            atomicOr(fnext + (u >> 5), 1u << (u & 31));
+            atomicOr(p.visited + (u >> 5), 1u << (u & 31));
+        } else {
+            acc_ex += (unsigned long long)(e0 - s0);
+        }
+    }
+}
+#else
 __device__ void bu_phase_b(const SingleParams& p, int d, const unsigned* fcur, unsigned* fnext, const int* longlist,
                            long long nlong, unsigned long long& acc_n, unsigned long long& acc_m,
                            unsigned long long& acc_ex) {
@@ -561,6 +630,7 @@ __device__ void bu_phase_b(const SingleParams& p, int d, const unsigned* fcur, u
         }
     }
 }
+#endif
 
 // ------------------------------------------------------------------ kernel
 

@@ -45,28 +45,34 @@ struct Ticket {
 };
 
 struct Lane {
-    bool busy = false;
+    bool busy = false;        // holds a query (running, or its row is being copied out)
     uint64_t ticket = 0;
     int32_t* row = nullptr;   // device [n]
+};
+
+struct CopyBatch {
+    cudaEvent_t ev = nullptr;
+    std::vector<uint64_t> tickets;
 };
 
 struct Slot {
     bfs_graph* g = nullptr;
     MultiWork w;
-    cudaStream_t stream = nullptr;
-    cudaEvent_t ev = nullptr;
-    std::vector<unsigned char> table;   // host mirror of the lane table
+    cudaStream_t stream = nullptr;       // levels of this slot
+    cudaStream_t copy_stream = nullptr;  // result rows to host
+    cudaEvent_t ev = nullptr;            // end of the launch in flight
+    std::vector<unsigned char> table;    // host mirror of the lane table
     Lane lanes[64];
-    unsigned long long active = 0;      // lanes with a search in progress
-    unsigned long long stale = 0;       // finished lanes whose bits are still in seen/front
+    unsigned long long active = 0;       // lanes with a search in progress
+    unsigned long long stale = 0;        // finished lanes whose bits are still in seen/front
+    unsigned long long admitted = 0;     // lanes admitted for the next launch
     int iter = 0;
-    int prev_dir = 0;
-    long long nf = 0, mf = 0;
-    std::deque<uint64_t> queue;
+    bool running = false;
+    int max_iters = 64;
     bfsk::MCtrl* ctrl_pinned = nullptr;
-    bool launched = false;
-    unsigned long long launched_new = 0;
-    std::vector<uint64_t> copying;      // tickets whose rows are being copied out
+    std::deque<uint64_t> queue;
+    std::deque<CopyBatch> copies;
+    std::vector<cudaEvent_t> spare_events;
 };
 
 }  // namespace
@@ -76,6 +82,7 @@ struct bfs_server {
     int64_t used = 0;
     int32_t max_lanes = 64;
     int device = 0;
+    int total_ctas = 0;
     std::vector<Slot*> slots;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -91,12 +98,6 @@ struct bfs_server {
 
 namespace {
 
-int pick_dir(const Slot& s) {
-    const bfs_graph* g = s.g;
-    if (s.prev_dir == 0) return (s.mf * 14 > g->nnz / 2) ? 1 : 0;
-    return (s.nf * 24 < g->n) ? 0 : 1;
-}
-
 void fail_slot(bfs_server* sv, Slot& s, const std::string& why) {
     for (int i = 0; i < 64; i++) {
         if (!s.lanes[i].busy) continue;
@@ -109,28 +110,110 @@ void fail_slot(bfs_server* sv, Slot& s, const std::string& why) {
         s.lanes[i].busy = false;
     }
     s.active = 0;
+    s.admitted = 0;
+    s.running = false;
     sv->fatal = why;
 }
 
+cudaEvent_t take_event(Slot& s) {
+    if (!s.spare_events.empty()) {
+        cudaEvent_t e = s.spare_events.back();
+        s.spare_events.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Worker loop.  Slots progress independently: a slot whose launch ended is
+// harvested (finished lanes -> rows copied out on the copy stream), refilled
+// from its queue (new lanes join at this level boundary) and relaunched; a
+// slot still running is skipped.  No slot waits for another.
 void worker_main(bfs_server* sv) {
     cudaSetDevice(sv->device);
     std::vector<Slot*> snap;
     while (true) {
-        // ---------------------------------------------------------- 1. admission
+        bool progress = false;
         {
             std::unique_lock<std::mutex> lk(sv->mu);
-            sv->cv_work.wait(lk, [&] {
-                if (sv->stop) return true;
+            auto has_work = [&] {
                 for (Slot* s : sv->slots)
-                    if (s->active || !s->queue.empty()) return true;
+                    if (s->running || s->active || !s->queue.empty() || !s->copies.empty()) return true;
                 return false;
-            });
+            };
+            sv->cv_work.wait(lk, [&] { return sv->stop || has_work(); });
             if (sv->stop) break;
-            snap = sv->slots;   // slots are only appended; the worker steps this snapshot
-            for (Slot* sp : snap) {
-                Slot& s = *sp;
-                s.launched = false;
-                s.launched_new = 0;
+            snap = sv->slots;   // slots are only appended
+        }
+        int busy = 0;
+        for (Slot* sp : snap) busy += (sp->running || sp->active || !sp->queue.empty()) ? 1 : 0;
+        for (Slot* sp : snap) {
+            Slot& s = *sp;
+            // ---------------------------------------------- harvest a finished launch
+            if (s.running) {
+                const cudaError_t q = cudaEventQuery(s.ev);
+                if (q == cudaErrorNotReady) continue;
+                s.running = false;
+                progress = true;
+                const bfsk::MCtrl& c = *s.ctrl_pinned;
+                if (q != cudaSuccess || c.b.status != 0) {
+                    (void)cudaGetLastError();
+                    std::lock_guard<std::mutex> lk(sv->mu);
+                    fail_slot(sv, s, q != cudaSuccess ? cudaGetErrorString(q) : "device status error (barrier timeout)");
+                    cudaMemsetAsync(s.w.ctrl, 0, sizeof(bfsk::MCtrl), s.stream);
+                    continue;
+                }
+                s.iter += (int)c.s_done;
+                const unsigned long long finished = s.active & c.s_finished;
+                const unsigned long long all_done = (c.s_nf == 0) ? s.active : 0ull;
+                const unsigned long long ended = finished | all_done;
+                if (ended) {
+                    CopyBatch cb;
+                    cb.ev = take_event(s);
+                    cudaEventRecord(s.ev, s.stream);
+                    cudaStreamWaitEvent(s.copy_stream, s.ev, 0);
+                    std::lock_guard<std::mutex> lk(sv->mu);
+                    for (int i = 0; i < 64; i++) {
+                        if (!((ended >> i) & 1ull)) continue;
+                        Lane& L = s.lanes[i];
+                        cudaMemcpyAsync(sv->tickets[L.ticket].host_out, L.row, sizeof(int32_t) * (size_t)s.g->n,
+                                        cudaMemcpyDeviceToHost, s.copy_stream);
+                        cb.tickets.push_back(L.ticket);
+                    }
+                    if (cb.ev) cudaEventRecord(cb.ev, s.copy_stream);
+                    s.copies.push_back(cb);
+                    s.active &= ~ended;
+                    s.stale |= ended;
+                }
+            }
+            // ---------------------------------------------- complete copied results
+            while (!s.copies.empty()) {
+                CopyBatch& cb = s.copies.front();
+                const cudaError_t q = cb.ev ? cudaEventQuery(cb.ev) : cudaStreamSynchronize(s.copy_stream);
+                if (q == cudaErrorNotReady) break;
+                progress = true;
+                {
+                    std::lock_guard<std::mutex> lk(sv->mu);
+                    const auto now = Clock::now();
+                    for (uint64_t tk : cb.tickets) {
+                        Ticket& t = sv->tickets[tk];
+                        t.state = q == cudaSuccess ? kDone : kFailed;
+                        t.err = q == cudaSuccess ? BFS_OK : BFS_ERR_CUDA;
+                        t.t_done = now;
+                        s.lanes[t.lane].busy = false;
+                        sv->completed++;
+                    }
+                }
+                if (cb.ev) s.spare_events.push_back(cb.ev);
+                s.copies.pop_front();
+                sv->cv_done.notify_all();
+            }
+            if (s.running) continue;
+            // ---------------------------------------------- admission at this level boundary
+            unsigned long long newmask = 0;
+            {
+                std::lock_guard<std::mutex> lk(sv->mu);
                 const size_t row_bytes = sizeof(int32_t) * (size_t)s.g->n;
                 for (int i = 0; i < sv->max_lanes && !s.queue.empty(); i++) {
                     Lane& L = s.lanes[i];
@@ -153,92 +236,31 @@ void worker_main(bfs_server* sv) {
                     L.busy = true;
                     L.ticket = tk;
                     ms_lane_table_set(s.table.data(), i, L.row, s.iter, t.root);
-                    s.launched_new |= 1ull << i;
+                    newmask |= 1ull << i;
                 }
             }
-        }
-        // ---------------------------------------------------------- 2. one level per busy slot
-        for (Slot* sp : snap) {
-            Slot& s = *sp;
-            if (!s.active && !s.launched_new) continue;
-            bfs_status st = BFS_OK;
-            const unsigned long long reuse = s.launched_new & s.stale;
-            if (reuse) {
-                st = ms_step_drop(s.g, s.w, reuse, s.stream);
-                s.stale &= ~reuse;
-            }
-            if (st == BFS_OK && s.launched_new) {
-                st = ms_step_admit(s.g, s.w, s.table.data(), s.launched_new, s.stream);
-                s.active |= s.launched_new;
-                s.nf += __builtin_popcountll(s.launched_new);
-            }
-            if (st == BFS_OK) {
-                const int dir = pick_dir(s);
-                st = ms_step_iterate(s.g, s.w, s.iter, dir, s.active, s.ctrl_pinned, s.stream);
-                s.prev_dir = dir;
-            }
+            if (!s.active && !newmask) continue;
+            // ---------------------------------------------- launch the next levels
+            const unsigned long long drop = s.stale & newmask;
+            s.stale &= ~newmask;
+            s.active |= newmask;
+            const int share = std::max(8, sv->total_ctas / std::max(1, busy));
+            const int by_size = (int)std::max<long long>(8, s.g->n >> 15);
+            const int grid = std::min(share, by_size);
+            bfs_status st = ms_serve_launch(s.g, s.w, s.table.data(), newmask, drop, s.active, s.iter, s.max_iters,
+                                            grid, s.ctrl_pinned, s.stream);
             if (st == BFS_OK && cudaEventRecord(s.ev, s.stream) != cudaSuccess) st = BFS_ERR_CUDA;
             if (st != BFS_OK) {
                 std::lock_guard<std::mutex> lk(sv->mu);
                 fail_slot(sv, s, bfs_last_error());
                 continue;
             }
-            s.launched = true;
+            s.running = true;
+            progress = true;
             sv->launches++;
             sv->lanes_filled += __builtin_popcountll(s.active);
         }
-        // ---------------------------------------------------------- 3. completion
-        for (Slot* sp : snap) {
-            Slot& s = *sp;
-            if (!s.launched) continue;
-            if (cudaEventSynchronize(s.ev) != cudaSuccess) {
-                (void)cudaGetLastError();
-                std::lock_guard<std::mutex> lk(sv->mu);
-                fail_slot(sv, s, "device error while stepping a slot");
-                continue;
-            }
-            const bfsk::MCtrl& c = *s.ctrl_pinned;
-            if (c.b.status != 0) {
-                std::lock_guard<std::mutex> lk(sv->mu);
-                fail_slot(sv, s, "device status error while stepping a slot");
-                continue;
-            }
-            const unsigned long long finished = s.active & ~c.found[0];
-            s.nf = (long long)c.accn[0];
-            s.mf = (long long)c.accm[0];
-            s.iter++;
-            s.copying.clear();
-            for (int i = 0; i < 64; i++) {
-                if (!((finished >> i) & 1ull)) continue;
-                Lane& L = s.lanes[i];
-                int32_t* out = nullptr;
-                {
-                    std::lock_guard<std::mutex> lk(sv->mu);
-                    out = sv->tickets[L.ticket].host_out;
-                }
-                cudaMemcpyAsync(out, L.row, sizeof(int32_t) * (size_t)s.g->n, cudaMemcpyDeviceToHost, s.stream);
-                s.copying.push_back(L.ticket);
-            }
-            s.active &= ~finished;
-            s.stale |= finished;
-        }
-        for (Slot* sp : snap) {
-            Slot& s = *sp;
-            if (s.copying.empty()) continue;
-            const cudaError_t e = cudaStreamSynchronize(s.stream);
-            std::lock_guard<std::mutex> lk(sv->mu);
-            const auto now = Clock::now();
-            for (uint64_t tk : s.copying) {
-                Ticket& t = sv->tickets[tk];
-                t.state = e == cudaSuccess ? kDone : kFailed;
-                t.err = e == cudaSuccess ? BFS_OK : BFS_ERR_CUDA;
-                t.t_done = now;
-                s.lanes[t.lane].busy = false;
-                sv->completed++;
-            }
-            s.copying.clear();
-        }
-        sv->cv_done.notify_all();
+        if (!progress) std::this_thread::sleep_for(std::chrono::microseconds(5));
     }
 }
 
@@ -276,14 +298,17 @@ bfs_status bfs_server_add_graph(bfs_server* sv, bfs_graph* g, int32_t* slot) {
         delete s;
         return fail(BFS_ERR_OOM, "HBM budget too small for the graph's lane masks");
     }
-    cudaStream_t st = nullptr;
-    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaStream_t st = nullptr, cst = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&cst, cudaStreamNonBlocking) != cudaSuccess) {
+        if (st) cudaStreamDestroy(st);
         delete s;
         return fail(BFS_ERR_CUDA, "cudaStreamCreate");
     }
     s->stream = st;
+    s->copy_stream = cst;
     bfs_status r = multi_alloc(g, s->w, st);
-    if (r == BFS_OK) r = ms_step_reset(g, s->w, st);
+    if (r == BFS_OK) r = ms_serve_reset(g, s->w, st);
     if (r == BFS_OK && cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming) != cudaSuccess) r = BFS_ERR_CUDA;
     if (r == BFS_OK && cudaMallocHost((void**)&s->ctrl_pinned, sizeof(bfsk::MCtrl)) != cudaSuccess) r = BFS_ERR_OOM;
     if (r == BFS_OK && cudaStreamSynchronize(st) != cudaSuccess) r = BFS_ERR_CUDA;
@@ -293,9 +318,11 @@ bfs_status bfs_server_add_graph(bfs_server* sv, bfs_graph* g, int32_t* slot) {
         if (s->ev) cudaEventDestroy(s->ev);
         if (s->ctrl_pinned) cudaFreeHost(s->ctrl_pinned);
         cudaStreamDestroy(st);
+        cudaStreamDestroy(cst);
         delete s;
         return fail(r, "server: add_graph: " + msg);
     }
+    if (sv->total_ctas == 0) sv->total_ctas = ms_serve_max_grid(g, s->w);
     memset(s->ctrl_pinned, 0, sizeof(bfsk::MCtrl));
     s->table.assign(ms_lane_table_bytes(), 0);
     sv->used += (int64_t)s->w.bytes;
@@ -379,12 +406,17 @@ void bfs_server_destroy(bfs_server* sv) {
     if (sv->worker.joinable()) sv->worker.join();
     for (Slot* s : sv->slots) {
         cudaStreamSynchronize(s->stream);
+        cudaStreamSynchronize(s->copy_stream);
         for (auto& L : s->lanes)
             if (L.row) cudaFree(L.row);
         multi_free(s->g, s->w);
         cudaEventDestroy(s->ev);
+        for (auto& cb : s->copies)
+            if (cb.ev) cudaEventDestroy(cb.ev);
+        for (auto e : s->spare_events) cudaEventDestroy(e);
         cudaFreeHost(s->ctrl_pinned);
         cudaStreamDestroy(s->stream);
+        cudaStreamDestroy(s->copy_stream);
         delete s;
     }
     for (auto& kv : sv->tickets)
