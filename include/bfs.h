@@ -277,6 +277,19 @@ bfs_status bfs_run_multi(bfs_graph* g, const int32_t* roots_host, int32_t k, int
 bfs_status bfs_run_csr_noalloc(const int64_t* row_offsets, const int32_t* col_ids, int64_t n, int64_t nnz,
                                int32_t root, int32_t* parent_dev, int32_t* level_dev, void* stream);
 
+/*
+ * Autotuner: times bfs_run on `k` sample roots (roots_host) for a small grid
+ * of direction thresholds (alpha, beta) and top-down hub cut-offs
+ * (td_big_degree), each configuration once for warm-up and once timed with
+ * CUDA events, and writes the fastest into *best (other fields from `base`,
+ * or the defaults when base is NULL).  Levels do not depend on these choices
+ * ("Parallel Direction-Optimizing BFS": the heuristic only picks the cheaper
+ * direction).  Synchronises `stream`; *best_ms receives the winner's mean
+ * time per search (may be NULL).  Errors: INVALID, CUDA, TIMEOUT.
+ */
+bfs_status bfs_autotune(bfs_graph* g, const int32_t* roots_host, int32_t k, const bfs_options* base,
+                        bfs_options* best, double* best_ms, void* stream);
+
 /* Wait for the graph's enqueued searches; returns the first device-side error since the last sync. */
 bfs_status bfs_graph_sync(bfs_graph* g, void* stream);
 

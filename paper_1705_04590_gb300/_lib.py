@@ -65,6 +65,8 @@ SIGNATURES = [
                                   ctypes.POINTER(Stats)]),
     ("bfs_run_multi", c_i32, [c_vp, c_vp, c_i32, c_vp, c_vp, ctypes.POINTER(Options), c_vp]),
     ("bfs_run_csr_noalloc", c_i32, [c_vp, c_vp, c_i64, c_i64, c_i32, c_vp, c_vp, c_vp]),
+    ("bfs_autotune", c_i32, [c_vp, c_vp, c_i32, ctypes.POINTER(Options), ctypes.POINTER(Options),
+                             ctypes.POINTER(ctypes.c_double), c_vp]),
     ("bfs_graph_sync", c_i32, [c_vp, c_vp]),
     ("bfs_server_create", c_i32, [c_i64, c_i32, ctypes.POINTER(c_vp)]),
     ("bfs_server_add_graph", c_i32, [c_vp, c_vp, ctypes.POINTER(c_i32)]),

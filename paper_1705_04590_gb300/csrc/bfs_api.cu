@@ -250,6 +250,8 @@ bfs_status bfs_graph_copy_dcsc(const bfs_graph* g, int64_t* tile_ptr_out, int32_
 
 void bfs_graph_destroy(bfs_graph* g) { destroy_graph(g); }
 
+bfs_status bfs_graph_sync(bfs_graph* g, void* stream);
+
 static bfs_status run_common(bfs_graph* g, const int32_t* roots, int32_t k, int32_t* parent_dev, int32_t* level_dev,
                              const bfs_options* opt, void* stream, bfs_stats* stats) {
     if (!g) return fail(BFS_ERR_INVALID, "graph handle is NULL");
@@ -308,6 +310,72 @@ bfs_status bfs_run_multi(bfs_graph* g, const int32_t* roots_host, int32_t k, int
     st = multi_launch(g, roots_host, k, level_dev, parent_dev, o, s);
     if (st != BFS_OK) return st;
     return mark_done(g, s);
+}
+
+bfs_status bfs_autotune(bfs_graph* g, const int32_t* roots_host, int32_t k, const bfs_options* base,
+                        bfs_options* best, double* best_ms, void* stream) {
+    if (!g || !best) return fail(BFS_ERR_INVALID, "NULL graph or output");
+    if (!roots_host || k < 1) return fail(BFS_ERR_INVALID, "need k >= 1 sample roots");
+    for (int32_t i = 0; i < k; i++)
+        if (roots_host[i] < 0 || (int64_t)roots_host[i] >= g->n) return fail(BFS_ERR_INVALID, "a root lies outside [0, n)");
+    bfs_options o0;
+    bfs_status st = check_options(base, &o0, g, false, nullptr);
+    if (st != BFS_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    // time with both outputs written, as a caller's search would
+    const size_t ob = sizeof(int32_t) * (size_t)g->n;
+    int32_t* tpar = (int32_t*)g->mem.alloc(ob, s);
+    int32_t* tlev = (int32_t*)g->mem.alloc(ob, s);
+    if (!tpar || !tlev) {
+        g->mem.release(tpar, ob, s);
+        g->mem.release(tlev, ob, s);
+        return fail(BFS_ERR_OOM, "autotune: output buffers");
+    }
+    static const int alphas[] = {6, 14, 32, 96};
+    static const int betas[] = {12, 24, 64};
+    static const int bigs[] = {64, 96, 256};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    BFS_CUDA_TRY(cudaEventCreate(&e0));
+    BFS_CUDA_TRY(cudaEventCreate(&e1));
+    double best_t = -1.0;
+    bfs_options win = o0;
+    for (int a : alphas)
+        for (int b : betas)
+            for (int big : bigs) {
+                bfs_options o = o0;
+                o.mode = BFS_MODE_DO;
+                o.alpha = a;
+                o.beta = b;
+                o.td_big_degree = big;
+                st = run_common(g, roots_host, 1, tpar, tlev, &o, stream, nullptr);   // warm-up
+                if (st != BFS_OK) break;
+                if (cudaEventRecord(e0, s) != cudaSuccess) { st = BFS_ERR_CUDA; break; }
+                for (int32_t i = 0; i < k && st == BFS_OK; i++)
+                    st = run_common(g, roots_host + i, 1, tpar, tlev, &o, stream, nullptr);
+                if (st != BFS_OK) break;
+                if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+                    st = BFS_ERR_CUDA;
+                    break;
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                const double per = ms / k;
+                if (best_t < 0 || per < best_t) {
+                    best_t = per;
+                    win = o;
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamSynchronize(s);
+    g->mem.release(tpar, ob, s);
+    g->mem.release(tlev, ob, s);
+    if (st != BFS_OK) return st;
+    st = bfs_graph_sync(g, stream);
+    if (st != BFS_OK) return st;
+    *best = win;
+    if (best_ms) *best_ms = best_t;
+    return BFS_OK;
 }
 
 bfs_status bfs_graph_sync(bfs_graph* g, void* stream) {

@@ -300,3 +300,23 @@ def test_streams_and_repeat(gpu_lib):
     torch.cuda.synchronize()
     for i, r in enumerate(roots):
         assert np.array_equal(outs[i].cpu().numpy(), oracle.levels(case.ref, r))
+
+
+def test_autotune_picks_a_grid_point_and_levels_do_not_change(gpu_lib, tmp_path, monkeypatch):
+    bfs = gpu_lib
+    from paper_1705_04590_gb300 import autotune
+    w = workloads.RMAT[14]
+    e = w.edges()
+    case = Case(bfs, e)
+    roots = w.roots(e, 4).tolist()
+    best, ms = autotune.autotune(case.g, roots)
+    assert best.alpha in (6, 14, 32, 96) and best.beta in (12, 24, 64) and best.td_big_degree in (64, 96, 256)
+    assert ms > 0
+    monkeypatch.setenv("BFS_AUTOTUNE_CACHE", str(tmp_path / "cache.json"))
+    o1 = autotune.tuned_options(case.g, roots)
+    o2 = autotune.tuned_options(case.g, roots)        # served from the cache file
+    assert (o1.alpha, o1.beta, o1.td_big_degree) == (o2.alpha, o2.beta, o2.td_big_degree)
+    for root in roots:
+        lv, pa, _ = case.run(root, o1)
+        assert np.array_equal(lv, oracle.levels(case.ref, root))
+        assert oracle.certify(case.ref, root, lv, pa, case.labels) == (0, -1)
