@@ -67,28 +67,53 @@ __device__ __forceinline__ void load_lanes(const MultiParams& p, LaneSmem& L) {
 // bottom-up levels sweep all vertices (they are chosen when the frontier is
 // large).  The two queues alternate: qsel picks fq.
 
-// Warp-aggregated append of `v` (where `want`) to queue q with counter *len.
-__device__ __forceinline__ void q_append(int* q, unsigned long long* len, bool want, int v) {
+// Per-warp staging of queue appends in shared memory, flushed in batches so a
+// queue counter sees one atomicAdd per batch rather than one per warp step.
+constexpr int kMStage = 256;
+struct MStage {
+    int* buf;
+    int cnt;   // warp-uniform
+};
+
+__device__ __forceinline__ MStage m_stage() {
+    __shared__ int s_mstage[kMBlock / 32][kMStage];
+    MStage st;
+    st.buf = s_mstage[threadIdx.x >> 5];
+    st.cnt = 0;
+    return st;
+}
+
+__device__ __forceinline__ void m_flush(MStage& st, int* q, unsigned long long* len) {
+    if (st.cnt == 0) return;
+    __syncwarp();
+    unsigned long long b = 0;
+    if (lane_id() == 0) b = atomicAdd(len, (unsigned long long)st.cnt);
+    b = __shfl_sync(kMFull, b, 0);
+    for (int i = lane_id(); i < st.cnt; i += 32) q[b + i] = st.buf[i];
+    __syncwarp();
+    st.cnt = 0;
+}
+
+// Stage `v` (where `want`) for queue q; all lanes call.
+__device__ __forceinline__ void m_append(MStage& st, int* q, unsigned long long* len, bool want, int v) {
     const unsigned m = __ballot_sync(kMFull, want);
     if (m) {
-        const int leader = __ffs(m) - 1;
-        unsigned long long b = 0;
-        if (lane_id() == leader) b = atomicAdd(len, (unsigned long long)__popc(m));
-        b = __shfl_sync(kMFull, b, leader);
-        if (want) q[b + __popc(m & lanemask_lt())] = v;
+        if (want) st.buf[st.cnt + __popc(m & lanemask_lt())] = v;
+        st.cnt += __popc(m);
+        if (st.cnt > kMStage - 32) m_flush(st, q, len);
     }
 }
 
 // Push lane bits along edge (v -> u); record u the first time its next mask
 // becomes nonzero.  All lanes call.
-__device__ __forceinline__ void ms_push(const MultiParams& p, unsigned long long f, int u, bool act, int* tq,
-                                        unsigned long long* tlen) {
+__device__ __forceinline__ void ms_push(const MultiParams& p, unsigned long long f, int u, bool act, MStage& st,
+                                        int* tq, unsigned long long* tlen) {
     bool first = false;
     if (act) {
         const unsigned long long nb = f & ~ldcg64(p.seen + u);
         if (nb) first = atomicOr(p.next + u, nb) == 0ull;
     }
-    q_append(tq, tlen, first, u);
+    m_append(st, tq, tlen, first, u);
 }
 
 // Top-down push over the frontier queue (warp-balanced gather; heavy rows
@@ -97,6 +122,7 @@ __device__ void ms_td_phase(const MultiParams& p, MCtrl* c, int slot, const int*
                             unsigned long long* tlen) {
     const int lane = lane_id();
     const long long gw = m_gtid() >> 5, nw = m_gthreads() >> 5;
+    MStage st = m_stage();
     for (long long base = gw * 32; base < flen; base += nw * 32) {
         const long long i = base + lane;
         int v = 0;
@@ -152,14 +178,16 @@ __device__ void ms_td_phase(const MultiParams& p, MCtrl* c, int slot, const int*
             const unsigned long long fj = __shfl_sync(kMFull, f, j);
             const bool act = k < total;
             const int u = act ? __ldg(p.cols + sj + (k - exj)) : 0;
-            ms_push(p, fj, u, act, tq, tlen);
+            ms_push(p, fj, u, act, st, tq, tlen);
         }
     }
+    m_flush(st, tq, tlen);
 }
 
 __device__ void ms_tasks_phase(const MultiParams& p, MCtrl* c, int slot, int* tq, unsigned long long* tlen) {
     const int lane = lane_id();
     const long long gw = m_gtid() >> 5, nw = m_gthreads() >> 5;
+    MStage st = m_stage();
     const long long nt = min((long long)ld_acquire64(&c->ntask[slot]), p.task_cap);
     for (long long t = gw; t < nt; t += nw) {
         const int4 raw = __ldcg(reinterpret_cast<const int4*>(p.tasks + t));
@@ -170,15 +198,16 @@ __device__ void ms_tasks_phase(const MultiParams& p, MCtrl* c, int slot, int* tq
             const int k = k0 + lane;
             const bool act = k < len;
             const int u = act ? __ldg(p.cols + start + k) : 0;
-            ms_push(p, f, u, act, tq, tlen);
+            ms_push(p, f, u, act, st, tq, tlen);
         }
     }
+    m_flush(st, tq, tlen);
 }
 
 // Bottom-up pull: a warp owns 32 consecutive vertices; each lane ORs the
 // frontier masks of its first 8 neighbours, then rows with lanes still
 // missing continue warp-cooperatively 32 neighbours at a time.
-__device__ void ms_bu_phase(const MultiParams& p, unsigned long long active, int* tq, unsigned long long* tlen) {
+__device__ void ms_bu_phase(const MultiParams& p, unsigned long long active) {
     const int lane = lane_id();
     const long long gw = m_gtid() >> 5, nw = m_gthreads() >> 5;
     for (long long base = gw * 32; base < p.n; base += nw * 32) {
@@ -223,7 +252,6 @@ __device__ void ms_bu_phase(const MultiParams& p, unsigned long long active, int
         }
         const unsigned long long nb = acc & miss;
         if (nb) p.next[u] = nb;
-        q_append(tq, tlen, nb != 0ull, (int)u);
     }
 }
 
@@ -265,6 +293,47 @@ __device__ void ms_apply_phase(const MultiParams& p, MCtrl* c, int slot, int ite
     if (tid == 0) c->accn[slot] = (unsigned long long)tlen;
 }
 
+// Apply after a bottom-up level, over all vertices (that level swept them all
+// anyway): the same updates as ms_apply_phase, old frontier bits dropped in
+// the same pass, and the new frontier listed in queue nq.
+__device__ void ms_apply_all_phase(const MultiParams& p, MCtrl* c, int slot, int iter, unsigned long long active,
+                                   const LaneSmem& L, int* nq, unsigned long long* nlen) {
+    const long long tid = m_gtid(), nth = m_gthreads();
+    MStage st = m_stage();
+    unsigned long long an = 0, am = 0, adone = 0, found = 0;
+    for (long long base = tid - lane_id(); base < p.n; base += nth) {
+        const long long v = base + lane_id();
+        unsigned long long x = 0;
+        if (v < p.n) {
+            x = ldcg64(p.next + v);
+            if (x) {
+                p.next[v] = 0ull;
+                const unsigned long long s = ldcg64(p.seen + v);
+                p.seen[v] = s | x;
+                p.front[v] = x;
+                found |= x;
+                const long long deg = __ldg(p.off + v + 1) - __ldg(p.off + v);
+                an += 1;
+                am += (unsigned long long)deg;
+                if ((s & active) != active && ((s | x) & active) == active) adone += (unsigned long long)deg;
+                unsigned long long bits = x;
+                while (bits) {
+                    const int i2 = __ffsll((long long)bits) - 1;
+                    bits &= bits - 1;
+                    L.rows[i2][v] = iter + 1 - L.start[i2];
+                }
+            } else if (ldcg64(p.front + v)) {
+                p.front[v] = 0ull;
+            }
+        }
+        m_append(st, nq, nlen, x != 0ull, (int)v);
+    }
+    m_flush(st, nq, nlen);
+    found = warp_or64(found);
+    if (lane_id() == 0 && found) atomicOr(&c->found[slot], found);
+    block_add4(an, am, adone, 0, &c->accn[slot], &c->accm[slot], &c->mdone[slot], nullptr);
+}
+
 // Clear the three masks and both queue counters (grid-stride).
 __device__ void ms_clear_phase(const MultiParams& p) {
     const long long tid = m_gtid(), nth = m_gthreads();
@@ -293,6 +362,7 @@ __device__ void ms_fill_rows(const MultiParams& p, unsigned long long mask, cons
 __device__ void ms_seed_phase(const MultiParams& p, unsigned long long mask, const LaneSmem& L, int* fq,
                               unsigned long long* flen) {
     if (m_gtid() >= 32) return;
+    MStage st = m_stage();
     for (int i0 = 0; i0 < 64; i0 += 32) {
         const int i = i0 + lane_id();
         bool add = false;
@@ -303,8 +373,9 @@ __device__ void ms_seed_phase(const MultiParams& p, unsigned long long mask, con
             add = atomicOr(p.front + r, 1ull << i) == 0ull;
             L.rows[i][r] = 0;
         }
-        q_append(fq, flen, add, r);
+        m_append(st, fq, flen, add, r);
     }
+    m_flush(st, fq, flen);
 }
 
 __device__ __forceinline__ int ms_decide(const MultiParams& p, int prev, long long nf, long long mf, long long mu) {
@@ -358,16 +429,17 @@ __global__ void __launch_bounds__(kMBlock, 2) bfs_multi_kernel(MultiParams p) {
                 ms_tasks_phase(p, c, slot, tq, tlen);
                 if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
             }
-        } else {
-            ms_bu_phase(p, active, tq, tlen);
+            ms_retire_phase(p, fq, flen);
             if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
+            ms_apply_phase(p, c, slot, it, active, L, tq, (long long)ld_acquire64(tlen));
+        } else {
+            ms_bu_phase(p, active);
+            if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
+            ms_apply_all_phase(p, c, slot, it, active, L, tq, tlen);
         }
-        ms_retire_phase(p, fq, flen);
-        if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
-        const long long nt = (long long)ld_acquire64(tlen);
-        ms_apply_phase(p, c, slot, it, active, L, tq, nt);
         if (m_gtid() == 0) c->qlen[qsel] = 0;   // the old frontier's queue collects the next touched set
         if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
+        const long long nt = (long long)ld_acquire64(&c->accn[slot]);
         qsel ^= 1;
         if (nt == 0) {
             if (blockIdx.x == 0 && threadIdx.x == 0) c->iterations = it + 1;
@@ -471,16 +543,17 @@ __global__ void __launch_bounds__(kMBlock, 2) bfs_serve_kernel(MultiParams p, in
                 ms_tasks_phase(p, c, slot, tq, tlen);
                 if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
             }
-        } else {
-            ms_bu_phase(p, active, tq, tlen);
+            ms_retire_phase(p, fq, flen);
             if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
+            ms_apply_phase(p, c, slot, it, active, L, tq, (long long)ld_acquire64(tlen));
+        } else {
+            ms_bu_phase(p, active);
+            if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
+            ms_apply_all_phase(p, c, slot, it, active, L, tq, tlen);
         }
-        ms_retire_phase(p, fq, flen);
-        if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
-        nt = (long long)ld_acquire64(tlen);
-        ms_apply_phase(p, c, slot, it, active, L, tq, nt);
         if (tid == 0) c->qlen[qsel] = 0;
         if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
+        nt = (long long)ld_acquire64(&c->accn[slot]);
         qsel ^= 1;
         done++;
         prev = dir;
