@@ -382,6 +382,14 @@ def served_section(g26, roots26, n_queries: int = 2000, seed: int = 5151) -> dic
 
 # ------------------------------------------------------------------ our arm
 
+def metric_name(args, w) -> str:
+    what = {"do": "direction-optimizing", "td": "top-down only", "bu": "bottom-up only"}[args.mode]
+    graph = {"rmat": f"R-MAT scale {args.scale}", "er": f"Erdos-Renyi n=2^{args.scale} deg 16",
+             "torus": "4096x4096 torus"}[args.workload]
+    lay = ", DCSC tiles" if args.layout == "dcsc" else ""
+    return f"GTEPS harmonic mean, {graph}, 1 GB300 (single-source, {what}{lay})"
+
+
 def our_arm(args):
     import numpy as np
     import torch
@@ -398,17 +406,24 @@ def our_arm(args):
     bfs.build()
     bfs.load()
 
-    w = workloads.RMAT[args.scale]
+    if args.workload == "er":
+        w = workloads.Workload("er", args.scale)
+    elif args.workload == "torus":
+        w = workloads.TORUS4096
+    else:
+        w = workloads.RMAT[args.scale]
     t0 = time.time()
     e = w.edges()
     roots_all = w.roots(e, args.roots).tolist()
-    g = bfs.Graph.from_edges(e.src, e.dst, e.n)
+    g = bfs.Graph.from_edges(e.src, e.dst, e.n, dcsc=(args.layout == "dcsc"))
     n = e.n
     del e
     setup_s = time.time() - t0
     m = g.nnz // 2
     roots = roots_all[rank % len(roots_all):] + roots_all[:rank % len(roots_all)]
-    opts = bfs.options(mode=bfs.MODE_DO, alpha=14, beta=24)
+    mode = {"do": bfs.MODE_DO, "td": bfs.MODE_TD_ONLY, "bu": bfs.MODE_BU_ONLY}[args.mode]
+    layout = bfs.LAYOUT_DCSC_TILED if args.layout == "dcsc" else bfs.LAYOUT_CSR
+    opts = bfs.options(mode=mode, layout=layout, alpha=14, beta=24)
     level = torch.empty(n, dtype=torch.int32, device="cuda")
     parent = torch.empty(n, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -468,7 +483,8 @@ def our_arm(args):
     if os.path.exists(TRAFFIC_FILE):
         with open(TRAFFIC_FILE) as f:
             tr = json.load(f)
-        if tr.get("kernel_source_hash") == kernel_source_hash() and tr.get("scale") == args.scale:
+        if tr.get("kernel_source_hash") == kernel_source_hash() and tr.get("workload") == w.name \
+                and args.layout == "csr" and args.mode == "do":
             traffic = tr.get("dram_bytes_per_launch")
 
     batched = served = None
@@ -486,19 +502,21 @@ def our_arm(args):
 
     if rank == 0:
         line = {
-            "metric": f"GTEPS harmonic mean, R-MAT scale {args.scale}, 1 GB300 (single-source, direction-optimizing)",
+            "metric": metric_name(args, w),
             "value": value, "unit": "GTEPS", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": f"rmat-scale{args.scale}-ef16 single-source BFS, {len(roots)} roots cycled",
-                       "n": n, "nnz": g.nnz, "undirected_edges": m, "alpha": 14, "beta": 24, "layout": "csr",
+            "config": {"workload": f"{w.name} single-source BFS, {len(roots)} roots cycled",
+                       "n": n, "nnz": g.nnz, "undirected_edges": m, "alpha": 14, "beta": 24,
+                       "mode": args.mode, "layout": args.layout,
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                        "l2": "inputs larger than L2 (graph resident in HBM, %.1f GB)" % (g.device_bytes() / 1e9),
                        "levels_per_search": float(np.mean([levels_of[r] for r in roots])),
                        "setup_s": round(setup_s, 1)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                         "peak_source": peaks["source"], "kernel": "bfs_single_kernel",
+                         "peak_source": peaks["source"],
+                         "kernel": "bfs_dcsc_kernel" if args.layout == "dcsc" else "bfs_single_kernel",
                          "algorithmic_bytes_per_search": alg_bytes / args.steps},
             "e2e": {"value": e2e_value, "unit": "GTEPS", "h2d_bytes_per_step": 4, "d2h_bytes_per_step": 8 * n,
                     "steps": e2e_steps},
@@ -522,7 +540,10 @@ def main():
     ap.add_argument("--steps", type=int, default=256)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--scale", type=int, default=26)
+    ap.add_argument("--scale", type=int, default=26, help="R-MAT scale, or log2 n for --workload er")
+    ap.add_argument("--workload", default="rmat", choices=["rmat", "er", "torus"])
+    ap.add_argument("--layout", default="csr", choices=["csr", "dcsc"])
+    ap.add_argument("--mode", default="do", choices=["do", "td", "bu"])
     ap.add_argument("--roots", type=int, default=64)
     ap.add_argument("--cpu-scale", type=int, default=22)
     ap.add_argument("--no-cpu-baseline", action="store_true")

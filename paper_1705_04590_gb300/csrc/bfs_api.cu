@@ -91,8 +91,7 @@ static bfs_status new_graph(int64_t n, const bfs_allocator* alloc, bfs_graph** o
     return BFS_OK;
 }
 
-static bfs_status check_options(const bfs_options* in, bfs_options* out, const bfs_graph* g, bool need_level_for_min,
-                                const int32_t* level) {
+static bfs_status check_options(const bfs_options* in, bfs_options* out, const bfs_graph* g) {
     bfs_options_default(out);
     if (in) *out = *in;
     if (out->mode < 0 || out->mode > 3) return fail(BFS_ERR_INVALID, "options.mode must be a BFS_MODE_* value");
@@ -103,8 +102,6 @@ static bfs_status check_options(const bfs_options* in, bfs_options* out, const b
     if (out->alpha < 1 || out->beta < 1) return fail(BFS_ERR_INVALID, "options.alpha and options.beta must be >= 1");
     if (out->parent_mode != BFS_PARENT_ANY && out->parent_mode != BFS_PARENT_MIN_ID)
         return fail(BFS_ERR_INVALID, "options.parent_mode must be a BFS_PARENT_* value");
-    if (need_level_for_min && out->parent_mode == BFS_PARENT_MIN_ID && !level)
-        return fail(BFS_ERR_INVALID, "BFS_PARENT_MIN_ID needs a level output");
     if (out->timeout_ms < 0) return fail(BFS_ERR_INVALID, "options.timeout_ms must be >= 0");
     if (out->td_big_degree != 0 && out->td_big_degree < 64) out->td_big_degree = 64;
     if (out->debug_barrier_extra < 0) return fail(BFS_ERR_INVALID, "options.debug_barrier_extra must be >= 0");
@@ -256,7 +253,7 @@ static bfs_status run_common(bfs_graph* g, const int32_t* roots, int32_t k, int3
                              const bfs_options* opt, void* stream, bfs_stats* stats) {
     if (!g) return fail(BFS_ERR_INVALID, "graph handle is NULL");
     bfs_options o;
-    bfs_status st = check_options(opt, &o, g, true, level_dev);
+    bfs_status st = check_options(opt, &o, g);
     if (st != BFS_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     std::lock_guard<std::mutex> lk(g->run_mu);
@@ -299,7 +296,7 @@ bfs_status bfs_run_multi(bfs_graph* g, const int32_t* roots_host, int32_t k, int
     for (int32_t i = 0; i < k; i++)
         if (roots_host[i] < 0 || (int64_t)roots_host[i] >= g->n) return fail(BFS_ERR_INVALID, "a root lies outside [0, n)");
     bfs_options o;
-    bfs_status st = check_options(opt, &o, g, false, level_dev);
+    bfs_status st = check_options(opt, &o, g);
     if (st != BFS_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     std::lock_guard<std::mutex> lk(g->run_mu);
@@ -319,7 +316,7 @@ bfs_status bfs_autotune(bfs_graph* g, const int32_t* roots_host, int32_t k, cons
     for (int32_t i = 0; i < k; i++)
         if (roots_host[i] < 0 || (int64_t)roots_host[i] >= g->n) return fail(BFS_ERR_INVALID, "a root lies outside [0, n)");
     bfs_options o0;
-    bfs_status st = check_options(base, &o0, g, false, nullptr);
+    bfs_status st = check_options(base, &o0, g);
     if (st != BFS_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     // time with both outputs written, as a caller's search would

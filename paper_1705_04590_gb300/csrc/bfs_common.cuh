@@ -23,12 +23,16 @@ constexpr unsigned kDevTimeout = 1;
 constexpr unsigned kDevOverflow = 2;
 
 // Grid barrier + run status; the first member of every launch control block.
+// `count` only grows during a launch: barrier k is complete once it reaches
+// (k+1) * expected, so an arriving CTA needs one atomic and no separate
+// generation word.  Bit 63 is the abort flag: set together with `status`, it
+// releases every waiting CTA at once.
 struct BarrierState {
-    unsigned count;
-    unsigned gen;
+    unsigned long long count;
     unsigned status;
     unsigned pad;
 };
+constexpr unsigned long long kAbortBit = 1ull << 63;
 
 // Control block of one single-source launch: zeroed by the host
 // (cudaMemsetAsync) before every launch.  Counters indexed [slot] rotate over
@@ -41,6 +45,7 @@ struct Ctrl {
     unsigned long long scanned[3];   // bottom-up searchers of the level producing frontier `slot`
     unsigned long long examined[3];  // serial early-exit examinations of that level
     unsigned long long ntask[3];     // top-down edge-chunk tasks of that level
+    unsigned long long chunk[3];     // bottom-up work distribution: next 1024-vertex chunk
     long long num_levels;
     long long reached;
 };
@@ -60,6 +65,14 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
 __device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long* p) {
     unsigned long long v;
     asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Counter reads after a grid barrier: the barrier already ordered them, so
+// they need no acquire of their own and can be in flight together.
+__device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 
@@ -130,41 +143,45 @@ __device__ __forceinline__ void block_add4(unsigned long long a, unsigned long l
     }
 }
 
+// Record a launch failure for the host and release every CTA waiting at a
+// grid barrier (they then leave their loops).
+__device__ __forceinline__ void raise_status(BarrierState* c, unsigned code) {
+    atomicMax(&c->status, code);
+    atomicOr(&c->count, kAbortBit);
+}
+
 // Bounded grid barrier.  Every thread of every CTA calls it.  Returns false
-// when the run has failed (this wait or another CTA's ran out of time); the
-// caller then leaves its loop.  `expected` is the number of CTAs (plus any
-// deliberately missing arrivals in the timeout test).
+// when the run has failed (this wait or another CTA's ran out of time, or a
+// phase raised an error); the caller then leaves its loop.  `expected` is the
+// number of CTAs (plus any deliberately missing arrivals in the timeout test).
+// The arrival is one acquire-release atomic by thread 0 after the CTA barrier:
+// it publishes the CTA's writes and, for the last arriver, acquires everyone
+// else's; waiters acquire through their polling load.
 __device__ __forceinline__ bool grid_sync(BarrierState* c, unsigned expected, uint64_t timeout_ns) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        int ok = 1;
-        const unsigned g = ld_acquire(&c->gen);
-        __threadfence();
-        const unsigned arrived = atomicAdd(&c->count, 1u) + 1u;
-        if (arrived == expected) {
-            atomicExch(&c->count, 0u);
-            __threadfence();
-            st_release(&c->gen, g + 1u);
-        } else {
+        unsigned long long old;
+        asm volatile("atom.add.acq_rel.gpu.global.u64 %0, [%1], 1;" : "=l"(old) : "l"(&c->count) : "memory");
+        const unsigned long long target = ((old & ~kAbortBit) / expected + 1ull) * expected;
+        unsigned long long cur = old + 1ull;
+        if (!(cur & kAbortBit) && cur < target) {
             const uint64_t t0 = globaltimer_ns();
             unsigned spins = 0;
-            while (ld_acquire(&c->gen) == g) {
+            while (true) {
+                cur = ld_acquire64(&c->count);
+                if ((cur & kAbortBit) || cur >= target) break;
                 if (++spins > 32u) {
-                    __nanosleep(40);
-                    if ((spins & 63u) == 0u) {
-                        if (ld_acquire(&c->status) != kDevOk) { ok = 0; break; }
-                        if (globaltimer_ns() - t0 > timeout_ns) {
-                            atomicMax(&c->status, kDevTimeout);
-                            ok = 0;
-                            break;
-                        }
+                    __nanosleep(32);
+                    if ((spins & 63u) == 0u && globaltimer_ns() - t0 > timeout_ns) {
+                        raise_status(c, kDevTimeout);
+                        cur = kAbortBit;
+                        break;
                     }
                 }
             }
         }
-        if (ok && ld_acquire(&c->status) != kDevOk) ok = 0;
-        s_ok = ok;
+        s_ok = (cur & kAbortBit) ? 0 : 1;
     }
     __syncthreads();
     return s_ok != 0;

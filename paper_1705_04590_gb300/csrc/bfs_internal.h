@@ -40,6 +40,8 @@ struct SingleWork {
     unsigned* front1 = nullptr;    // [W]
     int* queue0 = nullptr;         // [n]
     int* queue1 = nullptr;         // [n]
+    unsigned char* lv8 = nullptr;  // [n rounded up to 16] staged levels
+    int* level_scratch = nullptr;  // [n] levels for MIN_ID parents when the caller wants none (lazy)
     void* tasks = nullptr;         // top-down edge-chunk descriptors
     long long task_cap = 0;
     void* ctrl = nullptr;          // bfsk::Ctrl

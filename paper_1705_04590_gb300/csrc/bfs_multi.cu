@@ -158,7 +158,7 @@ __device__ void ms_td_phase(const MultiParams& p, MCtrl* c, int slot, const int*
                     t.v = bv;
                     p.tasks[ti] = t;
                 } else {
-                    atomicMax(&c->b.status, kDevOverflow);
+                    raise_status(&c->b, kDevOverflow);
                 }
             }
         }
@@ -188,7 +188,7 @@ __device__ void ms_tasks_phase(const MultiParams& p, MCtrl* c, int slot, int* tq
     const int lane = lane_id();
     const long long gw = m_gtid() >> 5, nw = m_gthreads() >> 5;
     MStage st = m_stage();
-    const long long nt = min((long long)ld_acquire64(&c->ntask[slot]), p.task_cap);
+    const long long nt = min((long long)ld_relaxed64(&c->ntask[slot]), p.task_cap);
     for (long long t = gw; t < nt; t += nw) {
         const int4 raw = __ldcg(reinterpret_cast<const int4*>(p.tasks + t));
         const long long start = (long long)(unsigned)raw.x | ((long long)raw.y << 32);
@@ -419,19 +419,19 @@ __global__ void __launch_bounds__(kMBlock, 2) bfs_multi_kernel(MultiParams p) {
         if (blockIdx.x == 0 && threadIdx.x == 0) c->zero_slot(sfree);
         int* fq = qsel ? p.q1 : p.q0;
         int* tq = qsel ? p.q0 : p.q1;
-        const long long flen = (long long)ld_acquire64(&c->qlen[qsel]);
+        const long long flen = (long long)ld_relaxed64(&c->qlen[qsel]);
         unsigned long long* tlen = &c->qlen[qsel ^ 1];
         const int dir = ms_decide(p, prev, flen, mf, mu);
         if (dir == 0) {
             ms_td_phase(p, c, slot, fq, flen, tq, tlen);
             if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
-            if (ld_acquire64(&c->ntask[slot]) > 0) {
+            if (ld_relaxed64(&c->ntask[slot]) > 0) {
                 ms_tasks_phase(p, c, slot, tq, tlen);
                 if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
             }
             ms_retire_phase(p, fq, flen);
             if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
-            ms_apply_phase(p, c, slot, it, active, L, tq, (long long)ld_acquire64(tlen));
+            ms_apply_phase(p, c, slot, it, active, L, tq, (long long)ld_relaxed64(tlen));
         } else {
             ms_bu_phase(p, active);
             if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
@@ -439,14 +439,14 @@ __global__ void __launch_bounds__(kMBlock, 2) bfs_multi_kernel(MultiParams p) {
         }
         if (m_gtid() == 0) c->qlen[qsel] = 0;   // the old frontier's queue collects the next touched set
         if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
-        const long long nt = (long long)ld_acquire64(&c->accn[slot]);
+        const long long nt = (long long)ld_relaxed64(&c->accn[slot]);
         qsel ^= 1;
         if (nt == 0) {
             if (blockIdx.x == 0 && threadIdx.x == 0) c->iterations = it + 1;
             break;
         }
-        mu -= (long long)ld_acquire64(&c->mdone[slot]);
-        mf = (long long)ld_acquire64(&c->accm[slot]);
+        mu -= (long long)ld_relaxed64(&c->mdone[slot]);
+        mf = (long long)ld_relaxed64(&c->accm[slot]);
         prev = dir;
     }
 }
@@ -529,7 +529,7 @@ __global__ void __launch_bounds__(kMBlock, 2) bfs_serve_kernel(MultiParams p, in
         if (blockIdx.x == 0 && threadIdx.x == 0) c->zero_slot(sfree);
         int* fq = qsel ? p.q1 : p.q0;
         int* tq = qsel ? p.q0 : p.q1;
-        const long long flen = (long long)ld_acquire64(&c->qlen[qsel]);
+        const long long flen = (long long)ld_relaxed64(&c->qlen[qsel]);
         unsigned long long* tlen = &c->qlen[qsel ^ 1];
         int dir;
         if (p.mode == BFS_MODE_TD_ONLY) dir = 0;
@@ -539,13 +539,13 @@ __global__ void __launch_bounds__(kMBlock, 2) bfs_serve_kernel(MultiParams p, in
         if (dir == 0) {
             ms_td_phase(p, c, slot, fq, flen, tq, tlen);
             if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
-            if (ld_acquire64(&c->ntask[slot]) > 0) {
+            if (ld_relaxed64(&c->ntask[slot]) > 0) {
                 ms_tasks_phase(p, c, slot, tq, tlen);
                 if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
             }
             ms_retire_phase(p, fq, flen);
             if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
-            ms_apply_phase(p, c, slot, it, active, L, tq, (long long)ld_acquire64(tlen));
+            ms_apply_phase(p, c, slot, it, active, L, tq, (long long)ld_relaxed64(tlen));
         } else {
             ms_bu_phase(p, active);
             if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
@@ -553,12 +553,12 @@ __global__ void __launch_bounds__(kMBlock, 2) bfs_serve_kernel(MultiParams p, in
         }
         if (tid == 0) c->qlen[qsel] = 0;
         if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
-        nt = (long long)ld_acquire64(&c->accn[slot]);
+        nt = (long long)ld_relaxed64(&c->accn[slot]);
         qsel ^= 1;
         done++;
         prev = dir;
-        mf = (long long)ld_acquire64(&c->accm[slot]);
-        finished = active & ~ld_acquire64(&c->found[slot]);
+        mf = (long long)ld_relaxed64(&c->accm[slot]);
+        finished = active & ~ld_relaxed64(&c->found[slot]);
         if (finished || nt == 0) break;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -734,6 +734,11 @@ bfs_status ms_serve_launch(bfs_graph* g, MultiWork& w, const void* lane_table_ho
     p.expected = (unsigned)grid;
     if (newmask)
         BFS_CUDA_TRY(cudaMemcpyAsync(w.lanes, lane_table_host, sizeof(bfsk::LaneTable), cudaMemcpyHostToDevice, s));
+    // the barrier state (first member of the control block) restarts at zero for
+    // every launch, as the grid size varies between launches; the rest of the
+    // control block carries over
+    static_assert(offsetof(MCtrl, b) == 0, "barrier state leads the control block");
+    BFS_CUDA_TRY(cudaMemsetAsync(w.ctrl, 0, sizeof(bfsk::BarrierState), s));
     void* args[] = {&p, &iter0, &max_iters, &newmask, &drop};
     BFS_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)bfsk::bfs_serve_kernel, dim3(grid), dim3(w.block), args, 0, s));
     BFS_CUDA_TRY(cudaMemcpyAsync(ctrl_pinned, w.ctrl, sizeof(MCtrl), cudaMemcpyDeviceToHost, s));

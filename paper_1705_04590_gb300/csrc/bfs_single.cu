@@ -56,6 +56,7 @@ constexpr int kStage = 256;    // per-warp shared-memory staging of next-queue e
 #define BFS_MIN_BLOCKS 2
 #endif
 constexpr unsigned kFull = 0xffffffffu;
+constexpr size_t kSingleDynSmem = 0;   // the CSR kernel uses static shared memory only
 
 struct Task {
     long long start;
@@ -70,6 +71,10 @@ struct SingleParams {
     long long n, nnz, W;
     int* parent;
     int* level;
+    // level staging: one byte per vertex during the search (kLvUnseen / depth /
+    // kLvDeep), expanded into `level` after the last level; null = write `level`
+    // directly
+    unsigned char* lv8;
     unsigned* visited;
     unsigned* front0;
     unsigned* front1;
@@ -111,6 +116,93 @@ __device__ __forceinline__ int decide_dir(const SingleParams& p, int prev, long 
     }
 }
 
+#ifndef BFS_BU_WIN
+#define BFS_BU_WIN 8     // ids in the first bottom-up window: 4 (one int4) or 8 (two)
+#endif
+constexpr int kWin = BFS_BU_WIN;
+static_assert(kWin == 4 || kWin == 8, "window is one or two int4");
+
+#ifndef BFS_BU_DYN
+#define BFS_BU_DYN 0     // 1: bottom-up chunks from a counter; 0: round-robin
+#endif
+
+#ifndef BFS_EVICT
+#define BFS_EVICT 1      // 1: bottom-up graph reads marked evict-first in L2
+#endif
+
+// Bottom-up reads of the graph stream through L2 once per level; marking them
+// evict-first leaves L2 to the bitmaps and the output sectors being filled.
+#if BFS_EVICT
+__device__ __forceinline__ unsigned long long evict_first_policy() {
+    unsigned long long pol;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+#endif
+
+__device__ __forceinline__ int4 ld_stream4(const int4* a) {
+#if BFS_EVICT
+    int4 v;
+    asm("ld.global.nc.L2::cache_hint.v4.s32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(a), "l"(evict_first_policy()));
+    return v;
+#else
+    return __ldg(a);
+#endif
+}
+
+__device__ __forceinline__ long long ld_stream64(const long long* a) {
+#if BFS_EVICT
+    long long v;
+    asm("ld.global.nc.L2::cache_hint.s64 %0, [%1], %2;" : "=l"(v) : "l"(a), "l"(evict_first_policy()));
+    return v;
+#else
+    return __ldg(a);
+#endif
+}
+
+// row u's bounds [s, e) in the column array
+__device__ __forceinline__ void row_of(const SingleParams& p, int u, long long& s, long long& e) {
+    s = __ldg(p.off + u);
+    e = __ldg(p.off + u + 1);
+}
+
+__device__ __forceinline__ void row_of_stream(const SingleParams& p, int u, long long& s, long long& e) {
+    s = ld_stream64(p.off + u);
+    e = ld_stream64(p.off + u + 1);
+}
+
+__device__ __forceinline__ long long deg_of(const SingleParams& p, int u) {
+    long long s, e;
+    row_of(p, u, s, e);
+    return e - s;
+}
+
+constexpr unsigned char kLvUnseen = 255;   // not reached (yet)
+constexpr unsigned char kLvDeep = 254;     // depth >= 254: the int32 level holds it
+
+__device__ __forceinline__ void set_level(const SingleParams& p, int v, int lev) {
+    if (!p.level) return;
+    if (p.lv8) {
+        if (lev < kLvDeep) {
+            p.lv8[v] = (unsigned char)lev;
+            return;
+        }
+        p.lv8[v] = kLvDeep;
+    }
+    p.level[v] = lev;
+}
+
+// level of u as far as the search has got (-1 = not reached), for readers inside the launch
+__device__ __forceinline__ int get_level(const SingleParams& p, int u) {
+    if (p.lv8) {
+        const unsigned b = __ldcg(p.lv8 + u);
+        if (b == kLvUnseen) return -1;
+        if (b != kLvDeep) return (int)b;
+    }
+    return __ldcg(p.level + u);
+}
+
 __device__ __forceinline__ long long gtid() { return (long long)blockIdx.x * blockDim.x + threadIdx.x; }
 __device__ __forceinline__ long long gthreads() { return (long long)gridDim.x * blockDim.x; }
 
@@ -130,12 +222,65 @@ __device__ void fill_minus_one(int* a, long long n) {
 // parent/level fill, completed bitmap = isolated vertices (+ root), clear both
 // frontier bitmaps.  The root's own entries are written after the barrier
 // that ends this phase.
+// lv8 is 16-byte aligned (work buffer)
+__device__ void fill_bytes(unsigned char* a, long long n, unsigned char b) {
+    const long long tid = gtid(), nth = gthreads();
+    const unsigned w = 0x01010101u * b;
+    const uint4 v4 = make_uint4(w, w, w, w);
+    const long long body = n / 16;
+    for (long long i = tid; i < body; i += nth) reinterpret_cast<uint4*>(a)[i] = v4;
+    for (long long i = body * 16 + tid; i < n; i += nth) a[i] = b;
+}
+
+// After the last level: level[v] from the staged bytes, whole sectors at a
+// time (vertices at depth >= 254 already hold their int32 level).
+__device__ __forceinline__ int lv_decode(unsigned b) { return b == kLvUnseen ? -1 : (int)b; }
+
+__device__ void expand_levels(const SingleParams& p) {
+    const long long tid = gtid(), nth = gthreads();
+    if (((unsigned long long)p.level & 15) == 0) {
+        const long long groups = p.n / 16;
+        for (long long i = tid; i < groups; i += nth) {
+            const uint4 b = __ldcg(reinterpret_cast<const uint4*>(p.lv8) + i);
+            const unsigned w[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const unsigned x = w[q];
+                const long long v0 = i * 16 + q * 4;
+                int o[4];
+#pragma unroll
+                for (int k = 0; k < 4; k++) o[k] = lv_decode((x >> (8 * k)) & 0xFFu);
+                bool deep = false;
+#pragma unroll
+                for (int k = 0; k < 4; k++) deep |= ((x >> (8 * k)) & 0xFFu) == kLvDeep;
+                if (!deep) {
+                    reinterpret_cast<int4*>(p.level + v0)[0] = make_int4(o[0], o[1], o[2], o[3]);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 4; k++)
+                        if (((x >> (8 * k)) & 0xFFu) != kLvDeep) p.level[v0 + k] = o[k];
+                }
+            }
+        }
+        for (long long v = groups * 16 + tid; v < p.n; v += nth) {
+            const unsigned b = __ldcg(p.lv8 + v);
+            if (b != kLvDeep) p.level[v] = lv_decode(b);
+        }
+    } else {
+        for (long long v = tid; v < p.n; v += nth) {
+            const unsigned b = __ldcg(p.lv8 + v);
+            if (b != kLvDeep) p.level[v] = lv_decode(b);
+        }
+    }
+}
+
 __device__ void init_phase(const SingleParams& p) {
     const long long tid = gtid(), nth = gthreads();
     const bool single = p.nroots == 1;
     const long long r = p.root0;
     if (p.parent) fill_minus_one(p.parent, p.n);
-    if (p.level) fill_minus_one(p.level, p.n);
+    if (p.level && p.lv8) fill_bytes(p.lv8, p.n, kLvUnseen);
+    else if (p.level) fill_minus_one(p.level, p.n);
     const long long rw = single ? (r >> 5) : -1;
     const unsigned rb = single ? (1u << (r & 31)) : 0u;
     for (long long w = tid; w < p.W; w += nth) {
@@ -148,7 +293,7 @@ __device__ void init_phase(const SingleParams& p) {
     if (single && tid == 0) {
         p.queue0[0] = (int)r;
         p.ctrl->tail[0] = 1ull;
-        p.ctrl->accm[0] = (unsigned long long)(__ldg(p.off + r + 1) - __ldg(p.off + r));
+        p.ctrl->accm[0] = (unsigned long long)deg_of(p, r);
     }
 }
 
@@ -160,8 +305,8 @@ __device__ void seed_roots_phase(const SingleParams& p) {
         const int r = __ldcg(p.queue0 + i);
         atomicOr(p.visited + (r >> 5), 1u << (r & 31));
         if (p.parent) p.parent[r] = r;
-        if (p.level) p.level[r] = 0;
-        m += (unsigned long long)(__ldg(p.off + r + 1) - __ldg(p.off + r));
+        set_level(p, r, 0);
+        m += (unsigned long long)deg_of(p, r);
     }
     block_add4(m, 0, 0, 0, &p.ctrl->accm[0], nullptr, nullptr, nullptr);
     if (tid == 0) p.ctrl->tail[0] = (unsigned long long)p.nroots;
@@ -189,10 +334,25 @@ __device__ __forceinline__ void stage_flush(const SingleParams& p, WarpStage& st
         qnext[base + i] = v;
         // degree sum of the next frontier (the switch rule's m_f), read here in
         // batches rather than on the claim path
-        acc_m += (unsigned long long)(__ldg(p.off + v + 1) - __ldg(p.off + v));
+        acc_m += (unsigned long long)deg_of(p, v);
     }
     __syncwarp();
     st.cnt = 0;
+}
+
+// Record the claims of one warp step: winners write parent/level and stage v.
+__device__ __forceinline__ void td_stage(const SingleParams& p, int d, int u, int v, bool claimed, WarpStage& st,
+                                         int* qnext, unsigned long long* tail, unsigned long long& acc_m) {
+    const unsigned cm = __ballot_sync(kFull, claimed);
+    if (cm) {
+        if (claimed) {
+            st.buf[st.cnt + __popc(cm & lanemask_lt())] = v;
+            if (p.parent) p.parent[v] = u;
+            set_level(p, v, d + 1);
+        }
+        st.cnt += __popc(cm);
+        if (st.cnt > kStage - 32) stage_flush(p, st, qnext, tail, acc_m);
+    }
 }
 
 // Visit edge (u, v) for the whole warp (every lane calls; `act` masks): claim
@@ -204,18 +364,12 @@ __device__ __forceinline__ void td_visit(const SingleParams& p, int d, int u, in
     if (act) {
         const unsigned bit = 1u << (v & 31);
         unsigned* wp = p.visited + (v >> 5);
-        claimed = !(atomicOr(wp, bit) & bit);
+        // read before claiming: most edges of a dense level meet vertices already
+        // taken, and a plain L2 read does not serialise on a popular word the way
+        // an atomic does
+        if (!(__ldcg(wp) & bit)) claimed = !(atomicOr(wp, bit) & bit);
     }
-    const unsigned cm = __ballot_sync(kFull, claimed);
-    if (cm) {
-        if (claimed) {
-            st.buf[st.cnt + __popc(cm & lanemask_lt())] = v;
-            if (p.parent) p.parent[v] = u;
-            if (p.level) p.level[v] = d + 1;
-        }
-        st.cnt += __popc(cm);
-        if (st.cnt > kStage - 32) stage_flush(p, st, qnext, tail, acc_m);
-    }
+    td_stage(p, d, u, v, claimed, st, qnext, tail, acc_m);
 }
 
 __device__ __forceinline__ WarpStage warp_stage() {
@@ -238,8 +392,7 @@ __device__ void td_phase(const SingleParams& p, int d, const int* qcur, long lon
         long long s = 0, e = 0;
         if (i < nf) {
             u = __ldcg(qcur + i);
-            s = __ldg(p.off + u);
-            e = __ldg(p.off + u + 1);
+            row_of(p, u, s, e);
         }
         const long long deg = e - s;
         const bool big = deg > p.big_deg;
@@ -265,7 +418,7 @@ __device__ void td_phase(const SingleParams& p, int d, const int* qcur, long lon
                     t.u = bu;
                     p.tasks[ti] = t;
                 } else {
-                    atomicMax(&p.ctrl->b.status, kDevOverflow);
+                    raise_status(&p.ctrl->b, kDevOverflow);
                 }
             }
         }
@@ -312,8 +465,21 @@ __device__ void task_phase(const SingleParams& p, int d, long long ntask, int* q
                 act[q] = k < len;
                 v[q] = act[q] ? __ldg(p.cols + start + k) : 0;
             }
+            // all four reads in flight, then all four claims, then the staging
+            unsigned seen[4];
 #pragma unroll
-            for (int q = 0; q < 4; q++) td_visit(p, d, u, v[q], act[q], st, qnext, tail, acc_m);
+            for (int q = 0; q < 4; q++) seen[q] = act[q] ? __ldcg(p.visited + (v[q] >> 5)) : kFull;
+            bool claimed[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const unsigned bit = 1u << (v[q] & 31);
+                if (!(seen[q] & bit)) seen[q] = atomicOr(p.visited + (v[q] >> 5), bit);
+                else seen[q] = bit;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; q++) claimed[q] = act[q] && !(seen[q] & (1u << (v[q] & 31)));
+#pragma unroll
+            for (int q = 0; q < 4; q++) td_stage(p, d, u, v[q], claimed[q], st, qnext, tail, acc_m);
         }
     }
     stage_flush(p, st, qnext, tail, acc_m);
@@ -325,10 +491,11 @@ __device__ void td_min_parent(const SingleParams& p, int d, const int* qnext, lo
     const long long tid = gtid(), nth = gthreads();
     for (long long i = tid; i < nn; i += nth) {
         const int v = __ldcg(qnext + i);
-        const long long s = __ldg(p.off + v), e = __ldg(p.off + v + 1);
+        long long s, e;
+        row_of(p, v, s, e);
         for (long long k = s; k < e; k++) {
             const int u = __ldg(p.cols + k);
-            if (__ldcg(p.level + u) == d) {
+            if (get_level(p, u) == d) {
                 p.parent[v] = u;
                 break;
             }
@@ -381,6 +548,18 @@ __device__ __forceinline__ bool in_frontier(const unsigned* f, int v) {
     return (__ldcg(f + (v >> 5)) >> (v & 31)) & 1u;
 }
 
+// Append a warp's staged long-list entries with one atomicAdd.
+__device__ __forceinline__ void long_flush(WarpStage& st, int* longlist, unsigned long long* longcnt) {
+    if (st.cnt == 0) return;
+    __syncwarp();
+    unsigned long long base = 0;
+    if (lane_id() == 0) base = atomicAdd(longcnt, (unsigned long long)st.cnt);
+    base = __shfl_sync(kFull, base, 0);
+    for (int i = lane_id(); i < st.cnt; i += 32) longlist[base + i] = st.buf[i];
+    __syncwarp();
+    st.cnt = 0;
+}
+
 // Bottom-up, phase A.  A warp takes 32 completed-bitmap words (1024
 // vertices) at a time and compacts the unvisited ones with a warp prefix sum;
 // each lane then handles one searcher per round: its row offsets, one aligned
@@ -405,16 +584,27 @@ __device__ __forceinline__ int bu_locate(int k, int T, int incl, int excl, unsig
 }
 
 __device__ void bu_phase_a(const SingleParams& p, int d, const unsigned* fcur, unsigned* fnext, int* longlist,
-                           unsigned long long* longcnt, unsigned long long& acc_n, unsigned long long& acc_m,
-                           unsigned long long& acc_sc, unsigned long long& acc_ex) {
+                           unsigned long long* longcnt, unsigned long long* chunkctr, unsigned long long& acc_n,
+                           unsigned long long& acc_m, unsigned long long& acc_sc, unsigned long long& acc_ex) {
     __shared__ unsigned s_next[kWarps][32];
     const int lane = lane_id(), wib = threadIdx.x >> 5;
-    const long long gw = gtid() >> 5, nw = gthreads() >> 5;
     const long long nchunk = (p.W + 31) / 32;
     const int4 z4 = make_int4(0, 0, 0, 0);
     s_next[wib][lane] = 0u;
+    WarpStage lst = warp_stage();   // long-list entries, appended in batches
     __syncwarp();
+#if BFS_BU_DYN
+    // chunks handed out by a counter (the next one is claimed while this one runs)
+    unsigned long long grab = 0;
+    if (lane == 0) grab = atomicAdd(chunkctr, 1ull);
+    long long ch = (long long)__shfl_sync(kFull, grab, 0);
+    while (ch < nchunk) {
+        if (lane == 0) grab = atomicAdd(chunkctr, 1ull);
+#else
+    (void)chunkctr;
+    const long long gw = gtid() >> 5, nw = gthreads() >> 5;
     for (long long ch = gw; ch < nchunk; ch += nw) {
+#endif
         const long long w = ch * 32 + lane;
         const unsigned cw = (w < p.W) ? __ldcg(p.visited + w) : kFull;
         const unsigned todo = ~cw;
@@ -426,35 +616,32 @@ __device__ void bu_phase_a(const SingleParams& p, int d, const unsigned* fcur, u
         int u0 = bu_locate(lane, T, incl, excl, todo, ch);
         long long s0 = 0, e0 = 0;
         if (u0 >= 0) {
-            s0 = __ldg(p.off + u0);
-            e0 = __ldg(p.off + u0 + 1);
+            row_of_stream(p, u0, s0, e0);
         }
         int4 xa0 = z4, xb0 = z4;
         if (u0 >= 0 && e0 > s0) {
             const int4* src = reinterpret_cast<const int4*>(p.cols + (s0 & ~3LL));
-            xa0 = __ldg(src);
-            if ((s0 & ~3LL) + 4 < e0) xb0 = __ldg(src + 1);
+            xa0 = ld_stream4(src);
+            if (kWin == 8 && (s0 & ~3LL) + 4 < e0) xb0 = ld_stream4(src + 1);
         }
         int u1 = bu_locate(32 + lane, T, incl, excl, todo, ch);
         long long s1 = 0, e1 = 0;
         if (u1 >= 0) {
-            s1 = __ldg(p.off + u1);
-            e1 = __ldg(p.off + u1 + 1);
+            row_of_stream(p, u1, s1, e1);
         }
         for (int base = 0; base < T; base += 32) {
             // round r+2: offsets
             const int u2 = bu_locate(base + 64 + lane, T, incl, excl, todo, ch);
             long long s2 = 0, e2 = 0;
             if (u2 >= 0) {
-                s2 = __ldg(p.off + u2);
-                e2 = __ldg(p.off + u2 + 1);
+                row_of_stream(p, u2, s2, e2);
             }
             // round r+1: window
             int4 xa1 = z4, xb1 = z4;
             if (u1 >= 0 && e1 > s1) {
                 const int4* src = reinterpret_cast<const int4*>(p.cols + (s1 & ~3LL));
-                xa1 = __ldg(src);
-                if ((s1 & ~3LL) + 4 < e1) xb1 = __ldg(src + 1);
+                xa1 = ld_stream4(src);
+                if (kWin == 8 && (s1 & ~3LL) + 4 < e1) xb1 = ld_stream4(src + 1);
             }
             // round r: probes
             bool to_long = false;
@@ -470,7 +657,7 @@ __device__ void bu_phase_a(const SingleParams& p, int d, const unsigned* fcur, u
                     hb = 1u << t0;
                 } else {
 #pragma unroll
-                    for (int t = 0; t < 8; t++) {
+                    for (int t = 0; t < kWin; t++) {
                         const long long q = rb + t;
                         if (t > t0 && q < e0 && in_frontier(fcur, ids[t])) hb |= 1u << t;
                     }
@@ -481,9 +668,9 @@ __device__ void bu_phase_a(const SingleParams& p, int d, const unsigned* fcur, u
                     acc_ex += (unsigned long long)(rb + t - s0 + 1);
                     acc_m += (unsigned long long)(e0 - s0);
                     if (p.parent) p.parent[u0] = ids[t];
-                    if (p.level) p.level[u0] = d + 1;
+                    set_level(p, u0, d + 1);
                     atomicOr(&s_next[wib][(u0 >> 5) - ch * 32], 1u << (u0 & 31));
-                } else if (rb + 8 < e0) {
+                } else if (rb + kWin < e0) {
                     to_long = true;       // examinations counted by phase B
                 } else {
                     acc_ex += (unsigned long long)(e0 - s0);
@@ -491,10 +678,9 @@ __device__ void bu_phase_a(const SingleParams& p, int d, const unsigned* fcur, u
             }
             const unsigned lm = __ballot_sync(kFull, to_long);
             if (lm) {
-                unsigned long long lb = 0;
-                if (lane == 0) lb = atomicAdd(longcnt, (unsigned long long)__popc(lm));
-                lb = __shfl_sync(kFull, lb, 0);
-                if (to_long) longlist[lb + __popc(lm & lanemask_lt())] = u0;
+                if (to_long) lst.buf[lst.cnt + __popc(lm & lanemask_lt())] = u0;
+                lst.cnt += __popc(lm);
+                if (lst.cnt > kStage - 32) long_flush(lst, longlist, longcnt);
             }
             u0 = u1;
             s0 = s1;
@@ -514,7 +700,11 @@ __device__ void bu_phase_a(const SingleParams& p, int d, const unsigned* fcur, u
         acc_n += (unsigned long long)__popc(nx);
         s_next[wib][lane] = 0u;
         __syncwarp();
+#if BFS_BU_DYN
+        ch = (long long)__shfl_sync(kFull, grab, 0);
+#endif
     }
+    long_flush(lst, longlist, longcnt);
 }
 
 // Bottom-up, phase B: the long list.  Groups of 4 lanes take one searcher
@@ -531,8 +721,9 @@ __device__ void bu_phase_b(const SingleParams& p, int d, const unsigned* fcur, u
     const int4 z4 = make_int4(0, 0, 0, 0);
     for (long long i = tid; i < nlong; i += nth) {
         const int u = __ldcg(longlist + i);
-        const long long s0 = __ldg(p.off + u), e0 = __ldg(p.off + u + 1);
-        long long pos = (s0 & ~3LL) + 8;
+        long long s0, e0;
+        row_of(p, u, s0, e0);
+        long long pos = (s0 & ~3LL) + kWin;
         long long hitpos = -1;
         int pv = -1;
         while (pos < e0) {
@@ -557,7 +748,7 @@ __device__ void bu_phase_b(const SingleParams& p, int d, const unsigned* fcur, u
             acc_m += (unsigned long long)(e0 - s0);
             acc_n += 1;
             if (p.parent) p.parent[u] = pv;
-            if (p.level) p.level[u] = d + 1;
+            set_level(p, u, d + 1);
             atomicOr(fnext + (u >> 5), 1u << (u & 31));
             atomicOr(p.visited + (u >> 5), 1u << (u & 31));
         } else {
@@ -577,9 +768,8 @@ __device__ void bu_phase_b(const SingleParams& p, int d, const unsigned* fcur, u
         long long s0 = 0, e0 = 0, pos = 0;
         if (i < nlong) {
             u = __ldcg(longlist + i);
-            s0 = __ldg(p.off + u);
-            e0 = __ldg(p.off + u + 1);
-            pos = (s0 & ~3LL) + 8 + 4 * gl;
+            row_of(p, u, s0, e0);
+            pos = (s0 & ~3LL) + kWin + 4 * gl;
         }
         long long hitpos = -1;
         int pv = -1;
@@ -588,7 +778,7 @@ __device__ void bu_phase_b(const SingleParams& p, int d, const unsigned* fcur, u
             unsigned hb = 0;
             int4 x = make_int4(0, 0, 0, 0);
             if (live && pos < e0) {
-                x = __ldg(reinterpret_cast<const int4*>(p.cols + pos));
+                x = ld_stream4(reinterpret_cast<const int4*>(p.cols + pos));
                 const int ids[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
                 for (int t = 0; t < 4; t++)
@@ -621,7 +811,7 @@ __device__ void bu_phase_b(const SingleParams& p, int d, const unsigned* fcur, u
                 acc_m += (unsigned long long)(e0 - s0);
                 acc_n += 1;
                 if (p.parent) p.parent[u] = pv;
-                if (p.level) p.level[u] = d + 1;
+                set_level(p, u, d + 1);
                 atomicOr(fnext + (u >> 5), 1u << (u & 31));
                 atomicOr(p.visited + (u >> 5), 1u << (u & 31));
             } else {
@@ -640,14 +830,14 @@ __global__ void __launch_bounds__(kBlock, BFS_MIN_BLOCKS) bfs_single_kernel(Sing
     if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
     if (p.nroots == 1 && gtid() == 0) {
         if (p.parent) p.parent[p.root0] = p.root0;
-        if (p.level) p.level[p.root0] = 0;
+        set_level(p, p.root0, 0);
     }
     if (p.nroots > 1) {
         seed_roots_phase(p);
         if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
     }
     long long nf = p.nroots;
-    long long mf = (long long)ld_acquire64(&c->accm[0]);
+    long long mf = (long long)ld_relaxed64(&c->accm[0]);
     long long mu = p.nnz - mf;
     long long reached = nf;
     int prev = TD, qsel = 0, bsel = 0, d = 0;
@@ -663,6 +853,7 @@ __global__ void __launch_bounds__(kBlock, BFS_MIN_BLOCKS) bfs_single_kernel(Sing
             c->scanned[sfree] = 0;
             c->examined[sfree] = 0;
             c->ntask[sfree] = 0;
+            c->chunk[sfree] = 0;
         }
         long long nf_next, scanned = 0, examined = mf, aux = 0;
         uint64_t t_mid = 0;
@@ -679,7 +870,7 @@ __global__ void __launch_bounds__(kBlock, BFS_MIN_BLOCKS) bfs_single_kernel(Sing
             td_phase(p, d, qcur, nf, qnext, snext, am);
             block_add4(0, am, 0, 0, nullptr, &c->accm[snext], nullptr, nullptr);
             if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
-            const long long nt = (long long)ld_acquire64(&c->ntask[snext]);
+            const long long nt = (long long)ld_relaxed64(&c->ntask[snext]);
             aux = nt;
             if (lead) t_mid = globaltimer_ns();
             if (nt > 0) {
@@ -688,7 +879,7 @@ __global__ void __launch_bounds__(kBlock, BFS_MIN_BLOCKS) bfs_single_kernel(Sing
                 block_add4(0, am2, 0, 0, nullptr, &c->accm[snext], nullptr, nullptr);
                 if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
             }
-            nf_next = (long long)ld_acquire64(&c->tail[snext]);
+            nf_next = (long long)ld_relaxed64(&c->tail[snext]);
             if (p.parent_mode == BFS_PARENT_MIN_ID && p.parent && p.level) td_min_parent(p, d, qnext, nf_next);
             qsel ^= 1;
         } else {
@@ -698,11 +889,11 @@ __global__ void __launch_bounds__(kBlock, BFS_MIN_BLOCKS) bfs_single_kernel(Sing
             }
             unsigned long long an = 0, am = 0, asc = 0, aex = 0;
             int* longlist = qnext;   // the queues are idle during bottom-up levels
-            bu_phase_a(p, d, fcur, fnext, longlist, &c->ntask[snext], an, am, asc, aex);
+            bu_phase_a(p, d, fcur, fnext, longlist, &c->ntask[snext], &c->chunk[snext], an, am, asc, aex);
             block_add4(an, am, asc, aex, &c->accn[snext], &c->accm[snext], &c->scanned[snext],
                        &c->examined[snext]);
             if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
-            const long long nlong = (long long)ld_acquire64(&c->ntask[snext]);
+            const long long nlong = (long long)ld_relaxed64(&c->ntask[snext]);
             aux = nlong;
             if (lead) t_mid = globaltimer_ns();
             if (nlong > 0) {
@@ -711,12 +902,12 @@ __global__ void __launch_bounds__(kBlock, BFS_MIN_BLOCKS) bfs_single_kernel(Sing
                 block_add4(bn, bm, 0, bex, &c->accn[snext], &c->accm[snext], nullptr, &c->examined[snext]);
                 if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
             }
-            nf_next = (long long)ld_acquire64(&c->accn[snext]);
-            scanned = (long long)ld_acquire64(&c->scanned[snext]);
-            examined = (long long)ld_acquire64(&c->examined[snext]);
+            nf_next = (long long)ld_relaxed64(&c->accn[snext]);
+            scanned = (long long)ld_relaxed64(&c->scanned[snext]);
+            examined = (long long)ld_relaxed64(&c->examined[snext]);
             bsel ^= 1;
         }
-        const long long mf_next = (long long)ld_acquire64(&c->accm[snext]);
+        const long long mf_next = (long long)ld_relaxed64(&c->accm[snext]);
         if (lead && d < p.rec_cap) {
             bfs_level_record r;
             r.dir = dir;
@@ -744,6 +935,8 @@ __global__ void __launch_bounds__(kBlock, BFS_MIN_BLOCKS) bfs_single_kernel(Sing
         c->num_levels = d + 1;
         c->reached = reached;
     }
+    // every level ended at a grid barrier, so all staged bytes are visible here
+    if (p.lv8 && p.level) expand_levels(p);
 }
 
 // ------------------------------------------------------------------ DCSC tiles
@@ -885,7 +1078,7 @@ __device__ void bu_dcsc_phase(const SingleParams& p, int d, const unsigned* fcur
             const int bt = __ffs(bits) - 1;
             bits &= bits - 1;
             const long long u = (wbase + w) * 32 + bt;
-            acc_m += (unsigned long long)(__ldg(p.off + u + 1) - __ldg(p.off + u));
+            acc_m += (unsigned long long)deg_of(p, u);
         }
     }
 }
@@ -906,7 +1099,7 @@ __global__ void __launch_bounds__(kDBlock, 1) bfs_dcsc_kernel(SingleParams p) {
         if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
     }
     long long nf = p.nroots;
-    long long mf = (long long)ld_acquire64(&c->accm[0]);
+    long long mf = (long long)ld_relaxed64(&c->accm[0]);
     long long mu = p.nnz - mf;
     long long reached = nf;
     int prev = TD, qsel = 0, bsel = 0, d = 0;
@@ -937,7 +1130,7 @@ __global__ void __launch_bounds__(kDBlock, 1) bfs_dcsc_kernel(SingleParams p) {
             td_dcsc_phase(p, d, qcur, nf, qnext, snext, s_own, am);
             block_add4(0, am, 0, 0, nullptr, &c->accm[snext], nullptr, nullptr);
             if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
-            nf_next = (long long)ld_acquire64(&c->tail[snext]);
+            nf_next = (long long)ld_relaxed64(&c->tail[snext]);
             if (p.parent_mode == BFS_PARENT_MIN_ID && p.parent && p.level) td_min_parent(p, d, qnext, nf_next);
             qsel ^= 1;
         } else {
@@ -949,12 +1142,12 @@ __global__ void __launch_bounds__(kDBlock, 1) bfs_dcsc_kernel(SingleParams p) {
             bu_dcsc_phase(p, d, fcur, fnext, s_own, s_seg, an, am, asc, aex);
             block_add4(an, am, asc, aex, &c->accn[snext], &c->accm[snext], &c->scanned[snext], &c->examined[snext]);
             if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
-            nf_next = (long long)ld_acquire64(&c->accn[snext]);
-            scanned = (long long)ld_acquire64(&c->scanned[snext]);
-            examined = (long long)ld_acquire64(&c->examined[snext]);
+            nf_next = (long long)ld_relaxed64(&c->accn[snext]);
+            scanned = (long long)ld_relaxed64(&c->scanned[snext]);
+            examined = (long long)ld_relaxed64(&c->examined[snext]);
             bsel ^= 1;
         }
-        const long long mf_next = (long long)ld_acquire64(&c->accm[snext]);
+        const long long mf_next = (long long)ld_relaxed64(&c->accm[snext]);
         if (lead && d < p.rec_cap) {
             bfs_level_record r;
             r.dir = dir;
@@ -1046,6 +1239,7 @@ bfs_status single_prepare(bfs_graph* g, cudaStream_t s) {
         {(void**)&w.front1, sizeof(unsigned) * (size_t)W},
         {(void**)&w.queue0, sizeof(int) * (size_t)(n + 32)},
         {(void**)&w.queue1, sizeof(int) * (size_t)(n + 32)},
+        {(void**)&w.lv8, (size_t)((n + 15) / 16 * 16)},
         {(void**)&w.tasks, sizeof(Task) * (size_t)task_cap},
         {(void**)&w.ctrl, sizeof(Ctrl)},
         {(void**)&w.records, sizeof(bfs_level_record) * (size_t)rec_cap},
@@ -1064,7 +1258,10 @@ bfs_status single_prepare(bfs_graph* g, cudaStream_t s) {
     w.rec_cap = rec_cap;
     w.bytes = total;
     int nb = 0;
-    BFS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, bfsk::bfs_single_kernel, bfsk::kBlock, 0));
+    BFS_CUDA_TRY(cudaFuncSetAttribute(bfsk::bfs_single_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)bfsk::kSingleDynSmem));
+    BFS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, bfsk::bfs_single_kernel, bfsk::kBlock,
+                                                               bfsk::kSingleDynSmem));
     if (nb < 1) return fail(BFS_ERR_UNSUPPORTED, "BFS kernel cannot be resident on this device");
     w.block = bfsk::kBlock;
     w.grid = nb * g->sm_count;
@@ -1082,6 +1279,8 @@ void single_release(bfs_graph* g) {
     g->mem.release(w.front1, sizeof(unsigned) * (size_t)W, nullptr);
     g->mem.release(w.queue0, sizeof(int) * (size_t)(n + 32), nullptr);
     g->mem.release(w.queue1, sizeof(int) * (size_t)(n + 32), nullptr);
+    g->mem.release(w.lv8, (size_t)((n + 15) / 16 * 16), nullptr);
+    if (w.level_scratch) g->mem.release(w.level_scratch, sizeof(int) * (size_t)n, nullptr);
     g->mem.release(w.tasks, sizeof(Task) * (size_t)w.task_cap, nullptr);
     g->mem.release(w.ctrl, sizeof(Ctrl), nullptr);
     g->mem.release(w.records, sizeof(bfs_level_record) * (size_t)w.rec_cap, nullptr);
@@ -1091,6 +1290,14 @@ void single_release(bfs_graph* g) {
 bfs_status single_launch(bfs_graph* g, const int32_t* roots_host, int32_t k, int32_t* parent,
                          int32_t* level, const bfs_options& opt, cudaStream_t s) {
     SingleWork& w = g->single;
+    if (opt.parent_mode == BFS_PARENT_MIN_ID && parent && !level) {
+        // minimum-id parents are picked by level; keep them in a private array
+        if (!w.level_scratch) {
+            w.level_scratch = (int*)g->mem.alloc(sizeof(int) * (size_t)g->n, s);
+            if (!w.level_scratch) return fail(BFS_ERR_OOM, "MIN_ID parents: level scratch allocation failed");
+        }
+        level = w.level_scratch;
+    }
     SingleParams p;
     p.off = reinterpret_cast<const long long*>(g->offsets);
     p.cols = g->cols;
@@ -1100,6 +1307,7 @@ bfs_status single_launch(bfs_graph* g, const int32_t* roots_host, int32_t k, int
     p.W = g->W;
     p.parent = parent;
     p.level = level;
+    p.lv8 = (opt.layout == BFS_LAYOUT_DCSC_TILED) ? nullptr : w.lv8;
     p.visited = w.visited;
     p.front0 = w.front0;
     p.front1 = w.front1;
@@ -1130,7 +1338,7 @@ bfs_status single_launch(bfs_graph* g, const int32_t* roots_host, int32_t k, int
     p.Bw = 0;
     const bool dcsc = opt.layout == BFS_LAYOUT_DCSC_TILED;
     int grid = w.grid, block = w.block;
-    size_t dyn = 0;
+    size_t dyn = bfsk::kSingleDynSmem;
     if (dcsc) {
         const DcscTiles& D = g->dcsc;
         p.tile_ptr = reinterpret_cast<const long long*>(D.tile_ptr);
@@ -1222,7 +1430,10 @@ extern "C" bfs_status bfs_run_csr_noalloc(const int64_t* row_offsets, const int3
             BFS_CUDA_TRY(cudaGetSymbolAddress(&ptr, bfsk::g_noalloc_scratch));
             int sms = 0, occ = 0;
             BFS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-            BFS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bfsk::bfs_single_kernel, bfsk::kBlock, 0));
+            BFS_CUDA_TRY(cudaFuncSetAttribute(bfsk::bfs_single_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)bfsk::kSingleDynSmem));
+            BFS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bfsk::bfs_single_kernel, bfsk::kBlock,
+                                                                       bfsk::kSingleDynSmem));
             if (occ < 1) return fail(BFS_ERR_UNSUPPORTED, "BFS kernel cannot be resident on this device");
             g_noalloc_sms[dev] = sms;
             g_noalloc_grid[dev] = occ * sms;
@@ -1244,6 +1455,7 @@ extern "C" bfs_status bfs_run_csr_noalloc(const int64_t* row_offsets, const int3
     p.W = W;
     p.parent = parent_dev;
     p.level = level_dev;
+    p.lv8 = nullptr;
     p.visited = reinterpret_cast<unsigned*>(b + bfsk::kStaticVisOff);
     p.front0 = reinterpret_cast<unsigned*>(b + bfsk::kStaticF0Off);
     p.front1 = reinterpret_cast<unsigned*>(b + bfsk::kStaticF1Off);
@@ -1269,6 +1481,6 @@ extern "C" bfs_status bfs_run_csr_noalloc(const int64_t* row_offsets, const int3
     BFS_CUDA_TRY(cudaMemsetAsync(p.ctrl, 0, sizeof(bfsk::Ctrl), s));
     void* args[] = {&p};
     BFS_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)bfsk::bfs_single_kernel, dim3(grid), dim3(bfsk::kBlock),
-                                             args, 0, s));
+                                             args, bfsk::kSingleDynSmem, s));
     return BFS_OK;
 }

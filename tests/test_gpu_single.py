@@ -128,9 +128,14 @@ def test_min_id_parents_bit_exact(gpu_lib):
         want = oracle.levels(case.ref, root)
         pmin = oracle.min_parent(case.ref, want)
         for mode in (bfs.MODE_DO, bfs.MODE_TD_ONLY, bfs.MODE_BU_ONLY, bfs.MODE_RANDOM):
-            lv, pa, _ = case.run(root, bfs.options(mode=mode, parent_mode=bfs.PARENT_MIN_ID, seed=3))
+            opts = bfs.options(mode=mode, parent_mode=bfs.PARENT_MIN_ID, seed=3)
+            lv, pa, _ = case.run(root, opts)
             assert np.array_equal(lv, want)
             assert np.array_equal(pa, pmin), (root, mode)
+            # parent only: the library keeps the levels it needs privately
+            case.parent.fill_(-7)
+            case.g.run(root, parent=case.parent, opts=opts)
+            assert np.array_equal(case.parent.cpu().numpy(), pmin), (root, mode, "parent only")
 
 
 def test_torus_closed_form(gpu_lib):
@@ -159,6 +164,36 @@ def test_path_bottom_up_only_same_level_discovery(gpu_lib):
         lv, pa, info = case.run(root, bfs.options(mode=bfs.MODE_BU_ONLY), stats=True)
         assert np.array_equal(lv, np.abs(np.arange(n) - root))
         assert oracle.certify(case.ref, root, lv, pa, case.labels) == (0, -1)
+
+
+def test_deep_levels_and_partial_outputs(gpu_lib):
+    """Depths past 253 (levels are staged one byte per vertex up to depth 253,
+    written directly beyond it), with both outputs, level only and parent only, in
+    every direction mode and both parent modes; a level-only run followed by a
+    parent-only one must not leave stale values."""
+    import torch
+    bfs = gpu_lib
+    n = 700
+    case = Case(bfs, graphgen.path(n))
+    lv_only = torch.empty(n, dtype=torch.int32, device="cuda")
+    pa_only = torch.empty(n, dtype=torch.int32, device="cuda")
+    for root in (0, 350, n - 1):
+        want = np.abs(np.arange(n) - root)
+        pwant = np.where(np.arange(n) < root, np.arange(n) + 1, np.arange(n) - 1)
+        pwant[root] = root
+        for mode in (bfs.MODE_DO, bfs.MODE_TD_ONLY, bfs.MODE_BU_ONLY):
+            for pm in (bfs.PARENT_ANY, bfs.PARENT_MIN_ID):
+                opts = bfs.options(mode=mode, parent_mode=pm)
+                lv, pa, info = case.run(root, opts, stats=True)
+                assert np.array_equal(lv, want), (root, mode, pm)
+                assert np.array_equal(pa, pwant), (root, mode, pm)
+                assert info["num_levels"] == want.max() + 1
+                lv_only.fill_(-7)
+                case.g.run(root, level=lv_only, opts=opts)
+                assert np.array_equal(lv_only.cpu().numpy(), want), (root, mode, pm)
+                pa_only.fill_(-7)
+                case.g.run(root, parent=pa_only, opts=opts)
+                assert np.array_equal(pa_only.cpu().numpy(), pwant), (root, mode, pm)
 
 
 def test_degree_zero_root_and_empty_graph(gpu_lib):
@@ -243,7 +278,7 @@ def test_invalid_arguments(gpu_lib):
         case.g.run(-1)
     assert ex.value.status == 1
     with pytest.raises(bfs.BfsError):
-        case.g.run(0, parent=case.parent, opts=bfs.options(parent_mode=bfs.PARENT_MIN_ID))
+        case.g.run(0, parent=case.parent, opts=bfs.options(parent_mode=7))
     with pytest.raises(bfs.BfsError):
         bfs.Graph.from_edges(np.array([0, 5], np.int32), np.array([1, 300], np.int32), 10)
     # CSR validation
