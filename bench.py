@@ -289,7 +289,8 @@ def served_section(g26, roots26, n_queries: int = 2000, seed: int = 5151) -> dic
         graphs.append(g)
         rootsets.append(rs)
         ms.append(g.nnz // 2)
-    pool_size = [64 if g.n < (1 << 24) else 16 for g in graphs]
+    # client-side result buffers per graph: enough that a graph's 64 lanes can all be busy
+    pool_size = [128 if g.n < (1 << 24) else 64 for g in graphs]
     pinned = [[torch.empty(g.n, dtype=torch.int32, pin_memory=True) for _ in range(k)]
               for g, k in zip(graphs, pool_size)]
     pools = [[t.numpy() for t in pl] for pl in pinned]

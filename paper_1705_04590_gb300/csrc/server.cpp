@@ -34,6 +34,8 @@ namespace {
 
 enum TicketState { kQueued = 0, kRunning = 1, kDone = 2, kFailed = 3 };
 
+constexpr int kMinCtas = 8;   // smallest grid of a slot's launch
+
 struct Ticket {
     int slot = 0;
     int root = 0;
@@ -146,6 +148,8 @@ void worker_main(bfs_server* sv) {
             if (sv->stop) break;
             snap = sv->slots;   // slots are only appended
         }
+        // slots with work share the device's co-resident CTAs equally, so that
+        // their cooperative launches always fit side by side
         int busy = 0;
         for (Slot* sp : snap) busy += (sp->running || sp->active || !sp->queue.empty()) ? 1 : 0;
         for (Slot* sp : snap) {
@@ -244,8 +248,8 @@ void worker_main(bfs_server* sv) {
             const unsigned long long drop = s.stale & newmask;
             s.stale &= ~newmask;
             s.active |= newmask;
-            const int share = std::max(8, sv->total_ctas / std::max(1, busy));
-            const int by_size = (int)std::max<long long>(8, s.g->n >> 15);
+            const int share = std::max(kMinCtas, sv->total_ctas / std::max(1, busy));
+            const int by_size = (int)std::max<long long>(kMinCtas, s.g->n >> 15);
             const int grid = std::min(share, by_size);
             bfs_status st = ms_serve_launch(s.g, s.w, s.table.data(), newmask, drop, s.active, s.iter, s.max_iters,
                                             grid, s.ctrl_pinned, s.stream);
