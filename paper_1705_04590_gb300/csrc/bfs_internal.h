@@ -40,7 +40,7 @@ struct SingleWork {
     unsigned* front1 = nullptr;    // [W]
     int* queue0 = nullptr;         // [n]
     int* queue1 = nullptr;         // [n]
-    unsigned char* lv8 = nullptr;  // [n rounded up to 16] staged levels
+    unsigned char* lv8 = nullptr;  // [W * 32] staged levels (one byte per vertex, whole words)
     int* level_scratch = nullptr;  // [n] levels for MIN_ID parents when the caller wants none (lazy)
     void* tasks = nullptr;         // top-down edge-chunk descriptors
     long long task_cap = 0;
@@ -63,6 +63,7 @@ struct MultiWork {
     unsigned long long* next = nullptr;   // [n]
     void* ctrl = nullptr;                 // bfsk::MCtrl
     void* tasks = nullptr;                // bfsk::MTask[task_cap]
+    void* hubmask = nullptr;              // uint64[task_cap] lane masks of chunked rows
     long long task_cap = 0;
     void* lanes = nullptr;                // bfsk::LaneTable
     int* q0 = nullptr;                    // [n+64] vertex queues (frontier / touched)

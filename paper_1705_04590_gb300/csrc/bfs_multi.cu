@@ -18,8 +18,9 @@
 // Two drivers share these phases:
 //  * bfs_multi_kernel: one persistent cooperative launch for a batch of <= 64
 //    roots (bfs_run_multi), bounded grid barriers between phases;
-//  * ms_*_kernel: one regular launch per phase, stepped by the server so that
-//    new lanes can join at a level boundary (continuous batching).
+//  * bfs_serve_kernel: one persistent launch per server step that runs levels
+//    until a lane finishes (or an iteration cap), so that new lanes can join
+//    at a level boundary (continuous batching).
 #include <algorithm>
 #include <cstring>
 
@@ -123,15 +124,20 @@ __device__ void ms_td_phase(const MultiParams& p, MCtrl* c, int slot, const int*
     const int lane = lane_id();
     const long long gw = m_gtid() >> 5, nw = m_gthreads() >> 5;
     MStage st = m_stage();
-    for (long long base = gw * 32; base < flen; base += nw * 32) {
+    // a small frontier is spread over every warp (one gather round each)
+    const long long per = flen >= nw * 32 ? 32 : max(1LL, (flen + nw - 1) / nw);
+    for (long long base = gw * per; base < flen; base += nw * per) {
         const long long i = base + lane;
         int v = 0;
         unsigned long long f = 0;
         long long s = 0, e = 0;
-        if (i < flen) {
+        if (lane < per && i < flen) {
             v = __ldcg(fq + i);
             f = ldcg64(p.front + v);
             if (f) {
+                // v leaves the frontier here (its mask travels in registers, or
+                // with its chunk tasks); nothing else reads front[v] this phase
+                p.front[v] = 0ull;
                 s = __ldg(p.off + v);
                 e = __ldg(p.off + v + 1);
             }
@@ -144,18 +150,20 @@ __device__ void ms_td_phase(const MultiParams& p, MCtrl* c, int slot, const int*
             const int L = __ffs(bm) - 1;
             bm &= bm - 1;
             const long long bs = __shfl_sync(kMFull, s, L), be = __shfl_sync(kMFull, e, L);
-            const int bv = __shfl_sync(kMFull, v, L);
+            const unsigned long long bf = __shfl_sync(kMFull, f, L);
             const long long nch = (be - bs + kMChunk - 1) / kMChunk;
             unsigned long long t0 = 0;
             if (lane == 0) t0 = atomicAdd(&c->ntask[slot], (unsigned long long)nch);
             t0 = __shfl_sync(kMFull, t0, 0);
+            // the row's lane mask is kept at the slot of its first chunk
+            if (lane == 0 && (long long)t0 < p.task_cap) p.hubmask[t0] = bf;
             for (long long k = lane; k < nch; k += 32) {
                 const long long ti = (long long)t0 + k;
                 if (ti < p.task_cap) {
                     MTask t;
                     t.start = bs + k * kMChunk;
                     t.len = (int)min((long long)kMChunk, be - t.start);
-                    t.v = bv;
+                    t.v = (int)t0;
                     p.tasks[ti] = t;
                 } else {
                     raise_status(&c->b, kDevOverflow);
@@ -192,8 +200,8 @@ __device__ void ms_tasks_phase(const MultiParams& p, MCtrl* c, int slot, int* tq
     for (long long t = gw; t < nt; t += nw) {
         const int4 raw = __ldcg(reinterpret_cast<const int4*>(p.tasks + t));
         const long long start = (long long)(unsigned)raw.x | ((long long)raw.y << 32);
-        const int len = raw.z, v = raw.w;
-        const unsigned long long f = ldcg64(p.front + v);
+        const int len = raw.z, h = raw.w;
+        const unsigned long long f = ldcg64(p.hubmask + h);
         for (int k0 = 0; k0 < len; k0 += 32) {
             const int k = k0 + lane;
             const bool act = k < len;
@@ -255,13 +263,8 @@ __device__ void ms_bu_phase(const MultiParams& p, unsigned long long active) {
     }
 }
 
-// Apply, part 1: the old frontier leaves front (its vertices are listed in fq).
-__device__ void ms_retire_phase(const MultiParams& p, const int* fq, long long flen) {
-    const long long tid = m_gtid(), nth = m_gthreads();
-    for (long long i = tid; i < flen; i += nth) p.front[__ldcg(fq + i)] = 0ull;
-}
-
-// Apply, part 2, over the touched vertices: seen |= next, front = next, next = 0,
+// Apply over the touched vertices (after a top-down level, whose phase already
+// removed the old frontier from front): seen |= next, front = next, next = 0,
 // per-lane levels; counts the new frontier (n_f, m_f), the degree of vertices
 // every active lane has now seen (subtracted from m_u) and which lanes found
 // anything.
@@ -429,8 +432,6 @@ __global__ void __launch_bounds__(kMBlock, 2) bfs_multi_kernel(MultiParams p) {
                 ms_tasks_phase(p, c, slot, tq, tlen);
                 if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
             }
-            ms_retire_phase(p, fq, flen);
-            if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
             ms_apply_phase(p, c, slot, it, active, L, tq, (long long)ld_relaxed64(tlen));
         } else {
             ms_bu_phase(p, active);
@@ -543,8 +544,6 @@ __global__ void __launch_bounds__(kMBlock, 2) bfs_serve_kernel(MultiParams p, in
                 ms_tasks_phase(p, c, slot, tq, tlen);
                 if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
             }
-            ms_retire_phase(p, fq, flen);
-            if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
             ms_apply_phase(p, c, slot, it, active, L, tq, (long long)ld_relaxed64(tlen));
         } else {
             ms_bu_phase(p, active);
@@ -592,16 +591,17 @@ bfs_status multi_alloc(bfs_graph* g, MultiWork& w, cudaStream_t s) {
     w.next = (unsigned long long*)g->mem.alloc(nb, s);
     w.ctrl = g->mem.alloc(sizeof(MCtrl), s);
     w.tasks = g->mem.alloc(sizeof(MTask) * (size_t)task_cap, s);
+    w.hubmask = g->mem.alloc(sizeof(unsigned long long) * (size_t)task_cap, s);
     w.lanes = g->mem.alloc(sizeof(bfsk::LaneTable), s);
     w.q0 = (int*)g->mem.alloc(sizeof(int) * (size_t)(g->n + 64), s);
     w.q1 = (int*)g->mem.alloc(sizeof(int) * (size_t)(g->n + 64), s);
     w.task_cap = task_cap;
-    if (!w.seen || !w.front || !w.next || !w.ctrl || !w.tasks || !w.lanes || !w.q0 || !w.q1) {
+    if (!w.seen || !w.front || !w.next || !w.ctrl || !w.tasks || !w.hubmask || !w.lanes || !w.q0 || !w.q1) {
         w.ready = true;
         multi_free(g, w);
         return fail(BFS_ERR_OOM, "multi-source work buffers: device allocation failed");
     }
-    w.bytes = 3 * nb + sizeof(MCtrl) + sizeof(MTask) * (size_t)task_cap + sizeof(bfsk::LaneTable) +
+    w.bytes = 3 * nb + sizeof(MCtrl) + (sizeof(MTask) + 8) * (size_t)task_cap + sizeof(bfsk::LaneTable) +
               2 * sizeof(int) * (size_t)(g->n + 64);
     int occ = 0;
     BFS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bfsk::bfs_multi_kernel, bfsk::kMBlock, 0));
@@ -622,6 +622,7 @@ void multi_free(bfs_graph* g, MultiWork& w) {
     g->mem.release(w.next, nb, nullptr);
     g->mem.release(w.ctrl, sizeof(MCtrl), nullptr);
     g->mem.release(w.tasks, sizeof(MTask) * (size_t)w.task_cap, nullptr);
+    g->mem.release(w.hubmask, sizeof(unsigned long long) * (size_t)w.task_cap, nullptr);
     g->mem.release(w.lanes, sizeof(bfsk::LaneTable), nullptr);
     g->mem.release(w.q0, sizeof(int) * (size_t)(g->n + 64), nullptr);
     g->mem.release(w.q1, sizeof(int) * (size_t)(g->n + 64), nullptr);
@@ -645,6 +646,7 @@ static MultiParams multi_params(bfs_graph* g, MultiWork& w, const bfs_options& o
     p.q0 = w.q0;
     p.q1 = w.q1;
     p.tasks = reinterpret_cast<MTask*>(w.tasks);
+    p.hubmask = reinterpret_cast<unsigned long long*>(w.hubmask);
     p.task_cap = w.task_cap;
     bfsk::LaneTable* lt = reinterpret_cast<bfsk::LaneTable*>(w.lanes);
     p.rows = lt->rows;

@@ -9,7 +9,7 @@ namespace bfsk {
 struct MTask {
     long long start;
     int len;
-    int v;
+    int v;        // index of the row's first chunk task: its lane mask is hubmask[v]
 };
 
 // Control block of a multi-source launch / server slot.
@@ -54,6 +54,7 @@ struct MultiParams {
     unsigned long long* next;
     MCtrl* ctrl;
     MTask* tasks;
+    unsigned long long* hubmask;   // [task_cap] lane masks of chunked rows
     long long task_cap;
     int* q0;                       // vertex queues, n + 64 entries each
     int* q1;

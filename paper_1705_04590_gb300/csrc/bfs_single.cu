@@ -49,6 +49,10 @@ constexpr int kDBlock = 1024;   // DCSC kernel (one CTA per vertex block)
 constexpr int kWarps = 32;      // shared-memory per-warp arrays sized for up to 1024 threads
 constexpr int kChunk = 256;    // edges per top-down chunk task
 constexpr int kStage = 256;    // per-warp shared-memory staging of next-queue entries
+constexpr long long kPrefetchNf = 1 << 16;   // top-down levels below this prefetch the next rows
+#ifndef BFS_TD_CHECK
+#define BFS_TD_CHECK 0   // 1: top-down gather reads the visited word before claiming (hub chunks always do)
+#endif
 #ifndef BFS_BU_PHASEB
 #define BFS_BU_PHASEB 1   // bottom-up long list: 1 = 4-lane groups, 2 = one thread per searcher
 #endif
@@ -320,6 +324,7 @@ __device__ void seed_roots_phase(const SingleParams& p) {
 struct WarpStage {
     int* buf;   // kStage entries of this warp's shared-memory slice
     int cnt;    // warp-uniform fill level
+    bool pf;    // prefetch the rows of flushed vertices into L2 (small levels)
 };
 
 __device__ __forceinline__ void stage_flush(const SingleParams& p, WarpStage& st, int* qnext,
@@ -334,7 +339,12 @@ __device__ __forceinline__ void stage_flush(const SingleParams& p, WarpStage& st
         qnext[base + i] = v;
         // degree sum of the next frontier (the switch rule's m_f), read here in
         // batches rather than on the claim path
-        acc_m += (unsigned long long)deg_of(p, v);
+        long long rs, re;
+        row_of(p, v, rs, re);
+        acc_m += (unsigned long long)(re - rs);
+        // on small levels the next level is latency-bound: start its column
+        // reads now (its offsets are now in L2 as well)
+        if (st.pf && re > rs) asm volatile("prefetch.global.L2 [%0];" ::"l"(p.cols + rs));
     }
     __syncwarp();
     st.cnt = 0;
@@ -367,7 +377,11 @@ __device__ __forceinline__ void td_visit(const SingleParams& p, int d, int u, in
         // read before claiming: most edges of a dense level meet vertices already
         // taken, and a plain L2 read does not serialise on a popular word the way
         // an atomic does
+#if BFS_TD_CHECK
         if (!(__ldcg(wp) & bit)) claimed = !(atomicOr(wp, bit) & bit);
+#else
+        claimed = !(atomicOr(wp, bit) & bit);
+#endif
     }
     td_stage(p, d, u, v, claimed, st, qnext, tail, acc_m);
 }
@@ -377,6 +391,7 @@ __device__ __forceinline__ WarpStage warp_stage() {
     WarpStage st;
     st.buf = s_stage[threadIdx.x >> 5];
     st.cnt = 0;
+    st.pf = false;
     return st;
 }
 
@@ -386,11 +401,15 @@ __device__ void td_phase(const SingleParams& p, int d, const int* qcur, long lon
     const long long gw = gtid() >> 5, nw = gthreads() >> 5;
     unsigned long long* tail = &p.ctrl->tail[snext];
     WarpStage st = warp_stage();
-    for (long long base = gw * 32; base < nf; base += nw * 32) {
+    st.pf = nf < kPrefetchNf;
+    // A small frontier is spread over every warp (fewer vertices per warp, so
+    // each warp's edges take one gather round instead of several dependent ones).
+    const long long per = nf >= nw * 32 ? 32 : max(1LL, (nf + nw - 1) / nw);
+    for (long long base = gw * per; base < nf; base += nw * per) {
         const long long i = base + lane;
         int u = 0;
         long long s = 0, e = 0;
-        if (i < nf) {
+        if (lane < per && i < nf) {
             u = __ldcg(qcur + i);
             row_of(p, u, s, e);
         }
@@ -592,6 +611,9 @@ __device__ void bu_phase_a(const SingleParams& p, int d, const unsigned* fcur, u
     const int4 z4 = make_int4(0, 0, 0, 0);
     s_next[wib][lane] = 0u;
     WarpStage lst = warp_stage();   // long-list entries, appended in batches
+    // staged levels of a chunk's finds go out per completed-bitmap word: the
+    // word's 32 level bytes are one sector, read, merged and written whole
+    const bool lv_words = p.level && p.lv8 && d + 1 < kLvDeep;
     __syncwarp();
 #if BFS_BU_DYN
     // chunks handed out by a counter (the next one is claimed while this one runs)
@@ -668,7 +690,7 @@ __device__ void bu_phase_a(const SingleParams& p, int d, const unsigned* fcur, u
                     acc_ex += (unsigned long long)(rb + t - s0 + 1);
                     acc_m += (unsigned long long)(e0 - s0);
                     if (p.parent) p.parent[u0] = ids[t];
-                    set_level(p, u0, d + 1);
+                    if (!lv_words) set_level(p, u0, d + 1);
                     atomicOr(&s_next[wib][(u0 >> 5) - ch * 32], 1u << (u0 & 31));
                 } else if (rb + kWin < e0) {
                     to_long = true;       // examinations counted by phase B
@@ -696,6 +718,22 @@ __device__ void bu_phase_a(const SingleParams& p, int d, const unsigned* fcur, u
         if (w < p.W) {
             fnext[w] = nx;
             if (nx) p.visited[w] = cw | nx;
+        }
+        if (lv_words && nx) {
+            uint4* lw = reinterpret_cast<uint4*>(p.lv8 + w * 32);
+            uint4 a = __ldcg(lw), b = __ldcg(lw + 1);
+            unsigned q[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+            const unsigned lev = (unsigned)(d + 1);
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                const unsigned m4 = (nx >> (4 * k)) & 0xFu;
+                // byte mask of the found vertices among these four
+                const unsigned bm = (m4 & 1u ? 0xFFu : 0u) | (m4 & 2u ? 0xFF00u : 0u) | (m4 & 4u ? 0xFF0000u : 0u) |
+                                    (m4 & 8u ? 0xFF000000u : 0u);
+                q[k] = (q[k] & ~bm) | ((lev * 0x01010101u) & bm);
+            }
+            __stcg(lw, make_uint4(q[0], q[1], q[2], q[3]));
+            __stcg(lw + 1, make_uint4(q[4], q[5], q[6], q[7]));
         }
         acc_n += (unsigned long long)__popc(nx);
         s_next[wib][lane] = 0u;
@@ -1239,7 +1277,7 @@ bfs_status single_prepare(bfs_graph* g, cudaStream_t s) {
         {(void**)&w.front1, sizeof(unsigned) * (size_t)W},
         {(void**)&w.queue0, sizeof(int) * (size_t)(n + 32)},
         {(void**)&w.queue1, sizeof(int) * (size_t)(n + 32)},
-        {(void**)&w.lv8, (size_t)((n + 15) / 16 * 16)},
+        {(void**)&w.lv8, (size_t)W * 32},   // whole bitmap words: phase A writes 32 bytes per word
         {(void**)&w.tasks, sizeof(Task) * (size_t)task_cap},
         {(void**)&w.ctrl, sizeof(Ctrl)},
         {(void**)&w.records, sizeof(bfs_level_record) * (size_t)rec_cap},
@@ -1279,7 +1317,7 @@ void single_release(bfs_graph* g) {
     g->mem.release(w.front1, sizeof(unsigned) * (size_t)W, nullptr);
     g->mem.release(w.queue0, sizeof(int) * (size_t)(n + 32), nullptr);
     g->mem.release(w.queue1, sizeof(int) * (size_t)(n + 32), nullptr);
-    g->mem.release(w.lv8, (size_t)((n + 15) / 16 * 16), nullptr);
+    g->mem.release(w.lv8, (size_t)W * 32, nullptr);
     if (w.level_scratch) g->mem.release(w.level_scratch, sizeof(int) * (size_t)n, nullptr);
     g->mem.release(w.tasks, sizeof(Task) * (size_t)w.task_cap, nullptr);
     g->mem.release(w.ctrl, sizeof(Ctrl), nullptr);
