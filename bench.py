@@ -121,6 +121,31 @@ def dist_env():
     return ws, rank, local
 
 
+# ------------------------------------------------------------------ replicas (multi-GPU, no data-path collective)
+
+def replica_roots(roots_all: list, rank: int) -> list:
+    """Rank r cycles through the same roots starting at root r, so replicas search
+    different roots at any moment while every rank's steps cover the same set."""
+    k = rank % len(roots_all)
+    return roots_all[k:] + roots_all[:k]
+
+
+def max_over_ranks(ms: float, ws: int, device: str = "cuda") -> float:
+    """Timed-region length of the job: the slowest rank's (all_reduce MAX)."""
+    if ws <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_gteps(ws: int, steps: int, m: int, total_ms: float) -> float:
+    """Whole-job throughput: every rank ran `steps` searches of m edges in total_ms."""
+    return ws * steps * m / (total_ms / 1e3) / 1e9
+
+
 # ------------------------------------------------------------------ CPU oracle (baseline / reference arm)
 
 def oracle_sample(scale: int, nroots: int, repeats: int = 1):
@@ -148,6 +173,10 @@ def reference_arm(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
+    if args.workload != "rmat" or args.layout != "csr" or args.mode != "do":
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times the default workload "
+                          "(R-MAT, CSR, direction-optimizing) only"}), flush=True)
+        return 0
     import oracle
     from graphgen import workloads
     oracle.build()
@@ -173,12 +202,12 @@ def reference_arm(args):
     sample = (f"serial Algorithm 1 (oracle) on R-MAT scale {scale} (same generator, edge factor 16; "
               f"1/{2 ** (args.scale - scale)} of the scale-{args.scale} graph), one search per step, "
               f"{len(roots)} roots cycled")
-    line = {"impl": "reference", "metric": f"GTEPS harmonic mean, R-MAT scale {args.scale}, 1 GB300", "value": value,
+    line = {"impl": "reference", "metric": metric_name(args, workloads.RMAT[args.scale]), "value": value,
             "unit": "GTEPS", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": f"rmat-scale{args.scale}-ef16 single-source BFS", "sample_scale": scale,
-                       "roots": len(roots), "undirected_edges": m},
+            "config": {"workload": f"{workloads.RMAT[args.scale].name} single-source BFS, 64 roots cycled",
+                       "sample_scale": scale, "sample_roots": len(roots), "sample_undirected_edges": m},
             "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -421,7 +450,7 @@ def our_arm(args):
     del e
     setup_s = time.time() - t0
     m = g.nnz // 2
-    roots = roots_all[rank % len(roots_all):] + roots_all[:rank % len(roots_all)]
+    roots = replica_roots(roots_all, rank)
     mode = {"do": bfs.MODE_DO, "td": bfs.MODE_TD_ONLY, "bu": bfs.MODE_BU_ONLY}[args.mode]
     layout = bfs.LAYOUT_DCSC_TILED if args.layout == "dcsc" else bfs.LAYOUT_CSR
     opts = bfs.options(mode=mode, layout=layout, alpha=14, beta=24)
@@ -455,11 +484,8 @@ def our_arm(args):
     g.sync()
     step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
     total_ms = evs[0].elapsed_time(evs[-1])
-    if ws > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = ws * args.steps * m / (total_ms / 1e3) / 1e9
+    total_ms = max_over_ranks(total_ms, ws)
+    value = aggregate_gteps(ws, args.steps, m, total_ms)
     alg_bytes = sum(bytes_of[roots[i % len(roots)]] for i in range(args.steps))
     achieved = alg_bytes / (sum(step_ms) / 1e3) / 1e9
     peaks = measured_peaks()
