@@ -95,6 +95,30 @@ __device__ __forceinline__ void m_flush(MStage& st, int* q, unsigned long long* 
     st.cnt = 0;
 }
 
+// Final flush of a phase, every thread of the CTA calls it: the warps'
+// remaining entries go out with one atomicAdd per CTA (block scan of counts).
+__device__ void m_block_flush(MStage& st, int* q, unsigned long long* len) {
+    __shared__ int s_wcnt[kMBlock / 32];
+    __shared__ unsigned long long s_base;
+    const int lane = lane_id(), wib = threadIdx.x >> 5, nwb = blockDim.x >> 5;
+    if (lane == 0) s_wcnt[wib] = st.cnt;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int c = lane < nwb ? s_wcnt[lane] : 0;
+        const int incl = warp_inclusive_scan(c);
+        const int total = __shfl_sync(kMFull, incl, 31);
+        unsigned long long b = 0;
+        if (lane == 0 && total) b = atomicAdd(len, (unsigned long long)total);
+        if (lane < nwb) s_wcnt[lane] = incl - c;
+        if (lane == 0) s_base = b;
+    }
+    __syncthreads();
+    const unsigned long long b = s_base + (unsigned long long)s_wcnt[wib];
+    for (int i = lane; i < st.cnt; i += 32) q[b + i] = st.buf[i];
+    __syncwarp();
+    st.cnt = 0;
+}
+
 // Stage `v` (where `want`) for queue q; all lanes call.
 __device__ __forceinline__ void m_append(MStage& st, int* q, unsigned long long* len, bool want, int v) {
     const unsigned m = __ballot_sync(kMFull, want);
@@ -189,7 +213,7 @@ __device__ void ms_td_phase(const MultiParams& p, MCtrl* c, int slot, const int*
             ms_push(p, fj, u, act, st, tq, tlen);
         }
     }
-    m_flush(st, tq, tlen);
+    m_block_flush(st, tq, tlen);
 }
 
 __device__ void ms_tasks_phase(const MultiParams& p, MCtrl* c, int slot, int* tq, unsigned long long* tlen) {
@@ -209,7 +233,7 @@ __device__ void ms_tasks_phase(const MultiParams& p, MCtrl* c, int slot, int* tq
             ms_push(p, f, u, act, st, tq, tlen);
         }
     }
-    m_flush(st, tq, tlen);
+    m_block_flush(st, tq, tlen);
 }
 
 // Bottom-up pull: a warp owns 32 consecutive vertices; each lane ORs the
@@ -331,7 +355,7 @@ __device__ void ms_apply_all_phase(const MultiParams& p, MCtrl* c, int slot, int
         }
         m_append(st, nq, nlen, x != 0ull, (int)v);
     }
-    m_flush(st, nq, nlen);
+    m_block_flush(st, nq, nlen);
     found = warp_or64(found);
     if (lane_id() == 0 && found) atomicOr(&c->found[slot], found);
     block_add4(an, am, adone, 0, &c->accn[slot], &c->accm[slot], &c->mdone[slot], nullptr);

@@ -50,6 +50,9 @@ constexpr int kWarps = 32;      // shared-memory per-warp arrays sized for up to
 constexpr int kChunk = 256;    // edges per top-down chunk task
 constexpr int kStage = 256;    // per-warp shared-memory staging of next-queue entries
 constexpr long long kPrefetchNf = 1 << 16;   // top-down levels below this prefetch the next rows
+#ifndef BFS_LV_WORDS
+#define BFS_LV_WORDS 1   // bottom-up: staged level bytes merged per bitmap word (else one byte store per find)
+#endif
 #ifndef BFS_TD_CHECK
 #define BFS_TD_CHECK 0   // 1: top-down gather reads the visited word before claiming (hub chunks always do)
 #endif
@@ -350,6 +353,40 @@ __device__ __forceinline__ void stage_flush(const SingleParams& p, WarpStage& st
     st.cnt = 0;
 }
 
+// End of a top-down phase: every warp's remaining staged entries are appended
+// with one atomicAdd per CTA (a block scan of the warps' counts).  On small
+// levels most warps hold a few entries each, and one queue-tail atomic per
+// warp would serialise thousands of arrivals on one word.  All threads call.
+__device__ void block_flush(const SingleParams& p, WarpStage& st, int* qnext, unsigned long long* tail,
+                            unsigned long long& acc_m) {
+    __shared__ int s_wcnt[kWarps];
+    __shared__ unsigned long long s_bbase;
+    const int lane = lane_id(), wib = threadIdx.x >> 5, nwb = blockDim.x >> 5;
+    if (lane == 0) s_wcnt[wib] = st.cnt;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int c = lane < nwb ? s_wcnt[lane] : 0;
+        const int incl = warp_inclusive_scan(c);
+        const int total = __shfl_sync(kFull, incl, 31);
+        unsigned long long b = 0;
+        if (lane == 0 && total) b = atomicAdd(tail, (unsigned long long)total);
+        if (lane < nwb) s_wcnt[lane] = incl - c;
+        if (lane == 0) s_bbase = b;
+    }
+    __syncthreads();
+    const unsigned long long base = s_bbase + (unsigned long long)s_wcnt[wib];
+    for (int i = lane; i < st.cnt; i += 32) {
+        const int v = st.buf[i];
+        qnext[base + i] = v;
+        long long rs, re;
+        row_of(p, v, rs, re);
+        acc_m += (unsigned long long)(re - rs);
+        if (st.pf && re > rs) asm volatile("prefetch.global.L2 [%0];" ::"l"(p.cols + rs));
+    }
+    __syncwarp();
+    st.cnt = 0;
+}
+
 // Record the claims of one warp step: winners write parent/level and stage v.
 __device__ __forceinline__ void td_stage(const SingleParams& p, int d, int u, int v, bool claimed, WarpStage& st,
                                          int* qnext, unsigned long long* tail, unsigned long long& acc_m) {
@@ -460,7 +497,7 @@ __device__ void td_phase(const SingleParams& p, int d, const int* qcur, long lon
             td_visit(p, d, uj, v, act, st, qnext, tail, acc_m);
         }
     }
-    stage_flush(p, st, qnext, tail, acc_m);
+    block_flush(p, st, qnext, tail, acc_m);
 }
 
 __device__ void task_phase(const SingleParams& p, int d, long long ntask, int* qnext, int snext,
@@ -501,7 +538,7 @@ __device__ void task_phase(const SingleParams& p, int d, long long ntask, int* q
             for (int q = 0; q < 4; q++) td_stage(p, d, u, v[q], claimed[q], st, qnext, tail, acc_m);
         }
     }
-    stage_flush(p, st, qnext, tail, acc_m);
+    block_flush(p, st, qnext, tail, acc_m);
 }
 
 // parent_mode MIN_ID after a top-down level: each newly found v takes the
@@ -536,10 +573,14 @@ __device__ void queue_to_bitmap(const SingleParams& p, const int* q, long long n
 // frontier bitmaps are zero for a later queue -> bitmap conversion.
 __device__ void bitmap_to_queue(const SingleParams& p, unsigned* f, unsigned* other, int* q,
                                 unsigned long long* tail) {
-    const int lane = lane_id();
+    // grid-stride rounds that are uniform across the CTA: per round the CTA
+    // claims its queue range with one atomicAdd (a block scan of its words' counts)
+    __shared__ int s_wtot[kWarps];
+    __shared__ unsigned long long s_qb;
+    const int lane = lane_id(), wib = threadIdx.x >> 5, nwb = blockDim.x >> 5;
     const long long nth = gthreads();
-    for (long long base = gtid() - lane; base < p.W; base += nth) {
-        const long long w = base + lane;
+    for (long long r0 = (long long)blockIdx.x * blockDim.x; r0 < p.W; r0 += nth) {
+        const long long w = r0 + threadIdx.x;
         unsigned x = 0;
         if (w < p.W) {
             x = __ldcg(f + w);
@@ -548,16 +589,25 @@ __device__ void bitmap_to_queue(const SingleParams& p, unsigned* f, unsigned* ot
         }
         const int cnt = __popc(x);
         const int incl = warp_inclusive_scan(cnt);
-        const int tot = __shfl_sync(kFull, incl, 31);
-        unsigned long long b = 0;
-        if (lane == 31 && tot) b = atomicAdd(tail, (unsigned long long)tot);
-        b = __shfl_sync(kFull, b, 31);
-        long long pos = (long long)b + incl - cnt;
+        if (lane == 31) s_wtot[wib] = incl;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            const int c = lane < nwb ? s_wtot[lane] : 0;
+            const int wi = warp_inclusive_scan(c);
+            const int total = __shfl_sync(kFull, wi, 31);
+            unsigned long long b = 0;
+            if (lane == 0 && total) b = atomicAdd(tail, (unsigned long long)total);
+            if (lane < nwb) s_wtot[lane] = wi - c;
+            if (lane == 0) s_qb = b;
+        }
+        __syncthreads();
+        long long pos = (long long)s_qb + s_wtot[wib] + incl - cnt;
         while (x) {
             const int bit = __ffs(x) - 1;
             x &= x - 1;
             q[pos++] = (int)(w * 32 + bit);
         }
+        __syncthreads();
     }
 }
 
@@ -613,7 +663,7 @@ __device__ void bu_phase_a(const SingleParams& p, int d, const unsigned* fcur, u
     WarpStage lst = warp_stage();   // long-list entries, appended in batches
     // staged levels of a chunk's finds go out per completed-bitmap word: the
     // word's 32 level bytes are one sector, read, merged and written whole
-    const bool lv_words = p.level && p.lv8 && d + 1 < kLvDeep;
+    const bool lv_words = BFS_LV_WORDS && p.level && p.lv8 && d + 1 < kLvDeep;
     __syncwarp();
 #if BFS_BU_DYN
     // chunks handed out by a counter (the next one is claimed while this one runs)
@@ -1227,7 +1277,7 @@ constexpr long long kStaticW = kStaticMaxN / 32;
 constexpr long long kStaticTasks = kStaticMaxNnz / kChunk + kStaticMaxNnz / 64 + 1024;
 constexpr int kStaticRec = 64;
 constexpr size_t kStaticCtrlOff = 0;
-constexpr size_t kStaticIsoOff = 256;
+constexpr size_t kStaticIsoOff = (sizeof(Ctrl) + 255) / 256 * 256;   // control block slot
 constexpr size_t kStaticVisOff = kStaticIsoOff + 4 * kStaticW;
 constexpr size_t kStaticF0Off = kStaticVisOff + 4 * kStaticW;
 constexpr size_t kStaticF1Off = kStaticF0Off + 4 * kStaticW;
@@ -1236,7 +1286,6 @@ constexpr size_t kStaticQ1Off = kStaticQ0Off + 4 * (kStaticMaxN + 64);
 constexpr size_t kStaticTaskOff = kStaticQ1Off + 4 * (kStaticMaxN + 64);
 constexpr size_t kStaticRecOff = kStaticTaskOff + sizeof(Task) * kStaticTasks;
 constexpr size_t kStaticBytes = kStaticRecOff + sizeof(bfs_level_record) * kStaticRec;
-static_assert(sizeof(Ctrl) <= 256, "control block must fit its slot");
 static_assert(kStaticQ1Off % 16 == 0 && kStaticTaskOff % 16 == 0 && kStaticRecOff % 8 == 0, "alignment");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kStaticBytes];
