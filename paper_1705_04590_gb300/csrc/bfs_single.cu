@@ -50,9 +50,6 @@ constexpr int kWarps = 32;      // shared-memory per-warp arrays sized for up to
 constexpr int kChunk = 256;    // edges per top-down chunk task
 constexpr int kStage = 256;    // per-warp shared-memory staging of next-queue entries
 constexpr long long kPrefetchNf = 1 << 16;   // top-down levels below this prefetch the next rows
-#ifndef BFS_LV_WORDS
-#define BFS_LV_WORDS 1   // bottom-up: staged level bytes merged per bitmap word (else one byte store per find)
-#endif
 #ifndef BFS_TD_CHECK
 #define BFS_TD_CHECK 0   // 1: top-down gather reads the visited word before claiming (hub chunks always do)
 #endif
@@ -661,9 +658,6 @@ __device__ void bu_phase_a(const SingleParams& p, int d, const unsigned* fcur, u
     const int4 z4 = make_int4(0, 0, 0, 0);
     s_next[wib][lane] = 0u;
     WarpStage lst = warp_stage();   // long-list entries, appended in batches
-    // staged levels of a chunk's finds go out per completed-bitmap word: the
-    // word's 32 level bytes are one sector, read, merged and written whole
-    const bool lv_words = BFS_LV_WORDS && p.level && p.lv8 && d + 1 < kLvDeep;
     __syncwarp();
 #if BFS_BU_DYN
     // chunks handed out by a counter (the next one is claimed while this one runs)
@@ -740,7 +734,7 @@ __device__ void bu_phase_a(const SingleParams& p, int d, const unsigned* fcur, u
                     acc_ex += (unsigned long long)(rb + t - s0 + 1);
                     acc_m += (unsigned long long)(e0 - s0);
                     if (p.parent) p.parent[u0] = ids[t];
-                    if (!lv_words) set_level(p, u0, d + 1);
+                    set_level(p, u0, d + 1);
                     atomicOr(&s_next[wib][(u0 >> 5) - ch * 32], 1u << (u0 & 31));
                 } else if (rb + kWin < e0) {
                     to_long = true;       // examinations counted by phase B
@@ -768,22 +762,6 @@ __device__ void bu_phase_a(const SingleParams& p, int d, const unsigned* fcur, u
         if (w < p.W) {
             fnext[w] = nx;
             if (nx) p.visited[w] = cw | nx;
-        }
-        if (lv_words && nx) {
-            uint4* lw = reinterpret_cast<uint4*>(p.lv8 + w * 32);
-            uint4 a = __ldcg(lw), b = __ldcg(lw + 1);
-            unsigned q[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-            const unsigned lev = (unsigned)(d + 1);
-#pragma unroll
-            for (int k = 0; k < 8; k++) {
-                const unsigned m4 = (nx >> (4 * k)) & 0xFu;
-                // byte mask of the found vertices among these four
-                const unsigned bm = (m4 & 1u ? 0xFFu : 0u) | (m4 & 2u ? 0xFF00u : 0u) | (m4 & 4u ? 0xFF0000u : 0u) |
-                                    (m4 & 8u ? 0xFF000000u : 0u);
-                q[k] = (q[k] & ~bm) | ((lev * 0x01010101u) & bm);
-            }
-            __stcg(lw, make_uint4(q[0], q[1], q[2], q[3]));
-            __stcg(lw + 1, make_uint4(q[4], q[5], q[6], q[7]));
         }
         acc_n += (unsigned long long)__popc(nx);
         s_next[wib][lane] = 0u;
@@ -1326,7 +1304,7 @@ bfs_status single_prepare(bfs_graph* g, cudaStream_t s) {
         {(void**)&w.front1, sizeof(unsigned) * (size_t)W},
         {(void**)&w.queue0, sizeof(int) * (size_t)(n + 32)},
         {(void**)&w.queue1, sizeof(int) * (size_t)(n + 32)},
-        {(void**)&w.lv8, (size_t)W * 32},   // whole bitmap words: phase A writes 32 bytes per word
+        {(void**)&w.lv8, (size_t)W * 32},   // one byte per vertex, rounded up to whole bitmap words
         {(void**)&w.tasks, sizeof(Task) * (size_t)task_cap},
         {(void**)&w.ctrl, sizeof(Ctrl)},
         {(void**)&w.records, sizeof(bfs_level_record) * (size_t)rec_cap},
