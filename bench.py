@@ -3,7 +3,9 @@
 
 Workload (default): R-MAT scale 26, edge factor 16, initiator .57/.19/.19/.05,
 symmetrised, self-loops and duplicates removed, ids relabelled from seed
-1026; 64 distinct seeded roots with degree > 0; CSR layout; alpha 14, beta 24.
+1026; 64 distinct seeded roots with degree > 0; CSR layout; alpha 14, beta 24;
+bottom-up steps scan the hub-first copy of the rows (neighbours by degree, highest
+first; --bu-rows id scans the id-sorted rows the paper stores).
 A step is one full search (the whole level loop: init, top-down / bottom-up
 levels, conversions, direction switches) from the next root, cycling through
 the 64 roots; inputs (the 9 GB graph) are resident and larger than L2.
@@ -263,7 +265,7 @@ def _events(stream):
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
 
-def batched_section(seed: int = 4242) -> dict:
+def batched_section(seed: int = 4242, hub: bool = True) -> dict:
     """Batched multi-source BFS against looping the plain search.
 
     (i)  R-MAT scale 22, 64 roots: one bfs_run_multi (64 lanes, one persistent
@@ -283,11 +285,13 @@ def batched_section(seed: int = 4242) -> dict:
     w = workloads.RMAT[22]
     e = w.edges()
     roots = w.roots(e, 64).tolist()
-    g = bfs.Graph.from_edges(e.src, e.dst, e.n)
+    g = bfs.Graph.from_edges(e.src, e.dst, e.n, hub_first=hub)
     n, m = e.n, g.nnz // 2
     del e
     lv1 = torch.empty(n, dtype=torch.int32, device="cuda")
     lvk = torch.empty(64 * n, dtype=torch.int32, device="cuda")
+    # both arms scan the same rows bottom-up
+    o = bfs.options(bu_rows=bfs.BU_ROWS_HUB_FIRST if hub else bfs.BU_ROWS_BY_ID)
 
     def best_ms(fn, reps=3):
         best = None
@@ -302,8 +306,8 @@ def batched_section(seed: int = 4242) -> dict:
             best = t if best is None else min(best, t)
         return best
 
-    t_multi = best_ms(lambda: g.run_multi(roots, lvk))
-    t_plain = best_ms(lambda: [g.run(r, level=lv1) for r in roots])
+    t_multi = best_ms(lambda: g.run_multi(roots, lvk, opts=o))
+    t_plain = best_ms(lambda: [g.run(r, level=lv1, opts=o) for r in roots])
     g.sync()
     out["rmat22_64roots"] = {"multi_ms": t_multi, "plain_ms": t_plain, "multi_gteps": 64 * m / t_multi / 1e6,
                              "plain_gteps": 64 * m / t_plain / 1e6, "speedup": t_plain / t_multi,
@@ -487,7 +491,8 @@ def our_arm(args):
     t0 = time.time()
     e = w.edges()
     roots_all = w.roots(e, args.roots).tolist()
-    g = bfs.Graph.from_edges(e.src, e.dst, e.n, dcsc=(args.layout == "dcsc"))
+    hub = args.bu_rows == "hub" and args.layout == "csr"
+    g = bfs.Graph.from_edges(e.src, e.dst, e.n, dcsc=(args.layout == "dcsc"), hub_first=hub)
     n = e.n
     del e
     setup_s = time.time() - t0
@@ -495,7 +500,8 @@ def our_arm(args):
     roots = replica_roots(roots_all, rank)
     mode = {"do": bfs.MODE_DO, "td": bfs.MODE_TD_ONLY, "bu": bfs.MODE_BU_ONLY}[args.mode]
     layout = bfs.LAYOUT_DCSC_TILED if args.layout == "dcsc" else bfs.LAYOUT_CSR
-    opts = bfs.options(mode=mode, layout=layout, alpha=14, beta=24)
+    opts = bfs.options(mode=mode, layout=layout, alpha=14, beta=24,
+                       bu_rows=bfs.BU_ROWS_HUB_FIRST if hub else bfs.BU_ROWS_BY_ID)
     level = torch.empty(n, dtype=torch.int32, device="cuda")
     parent = torch.empty(n, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -545,12 +551,12 @@ def our_arm(args):
         with open(TRAFFIC_FILE) as f:
             tr = json.load(f)
         if tr.get("kernel_source_hash") == kernel_source_hash() and tr.get("workload") == w.name \
-                and args.layout == "csr" and args.mode == "do":
+                and args.layout == "csr" and args.mode == "do" and tr.get("bu_rows", "id") == args.bu_rows:
             traffic = tr.get("dram_bytes_per_launch")
 
     batched = served = None
     if rank == 0 and not args.no_batched:
-        batched = batched_section()
+        batched = batched_section(hub=(args.bu_rows == "hub"))
     if rank == 0 and not args.no_served:
         served = served_section(g, roots, n_queries=args.served_queries)
 
@@ -570,6 +576,8 @@ def our_arm(args):
             "config": {"workload": f"{w.name} single-source BFS, {len(roots)} roots cycled",
                        "n": n, "nnz": g.nnz, "undirected_edges": m, "alpha": 14, "beta": 24,
                        "mode": args.mode, "layout": args.layout,
+                       "bu_rows": ("hub-first (bottom-up scans rows ordered by neighbour degree; "
+                                   "top-down uses the id-ordered rows)") if hub else "by id",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                        "l2": "inputs larger than L2 (graph resident in HBM, %.1f GB)" % (g.device_bytes() / 1e9),
                        "levels_per_search": float(np.mean([levels_of[r] for r in roots])),
@@ -605,6 +613,8 @@ def main():
     ap.add_argument("--workload", default="rmat", choices=["rmat", "er", "torus"])
     ap.add_argument("--layout", default="csr", choices=["csr", "dcsc"])
     ap.add_argument("--mode", default="do", choices=["do", "td", "bu"])
+    ap.add_argument("--bu-rows", default="hub", choices=["hub", "id"],
+                    help="row order of the bottom-up scans: hub-first copy (default) or the id-sorted rows")
     ap.add_argument("--roots", type=int, default=64)
     ap.add_argument("--cpu-scale", type=int, default=22)
     ap.add_argument("--no-cpu-baseline", action="store_true")

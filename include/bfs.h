@@ -69,6 +69,8 @@ typedef struct {
 #define BFS_FLAG_SYMMETRIZE    2u  /* store each edge in both rows (undirected); required for edge lists */
 #define BFS_FLAG_BUILD_DCSC    4u  /* also build the column-block DCSC tiles (layout BFS_LAYOUT_DCSC_TILED) */
 #define BFS_FLAG_CHECK_SYMMETRY 8u /* from_csr: verify that the CSR is symmetric (one extra pass) */
+#define BFS_FLAG_BUILD_HUB_FIRST 16u /* also store a copy of every row ordered by neighbour degree, highest
+                                        first, ties by id (bottom-up option BFS_BU_ROWS_HUB_FIRST) */
 
 /* search direction policy ("Parallel Direction-Optimizing BFS") */
 #define BFS_MODE_DO       0   /* per level: top-down or bottom-up by the alpha/beta rule */
@@ -102,8 +104,14 @@ typedef struct {
     uint64_t seed;         /* BFS_MODE_RANDOM only */
     int32_t debug_barrier_extra; /* testing only: every grid barrier waits for this many arrivals that
                                     never come, so each wait runs out after timeout_ms (0 = off) */
-    int32_t reserved;
+    int32_t bu_rows;       /* order in which bottom-up steps scan a row: BFS_BU_ROWS_BY_ID (stored order,
+                              the paper's) or BFS_BU_ROWS_HUB_FIRST (needs BFS_FLAG_BUILD_HUB_FIRST, the
+                              CSR layout and BFS_PARENT_ANY).  Levels are the same; the bottom-up
+                              examination counts and the parents chosen follow the order */
 } bfs_options;
+
+#define BFS_BU_ROWS_BY_ID     0
+#define BFS_BU_ROWS_HUB_FIRST 1
 
 void bfs_options_default(bfs_options* opt);
 
@@ -174,6 +182,15 @@ bfs_status bfs_graph_csr(const bfs_graph* g, const int64_t** row_offsets, const 
  * NULL).  Synchronises `stream`.
  */
 bfs_status bfs_graph_copy_csr(const bfs_graph* g, int64_t* offsets_out, int32_t* cols_out, void* stream);
+
+/*
+ * Copy the hub-first column ids (BFS_FLAG_BUILD_HUB_FIRST) into caller memory
+ * (host or device, int32[nnz]): row u holds the same neighbours as the CSR's
+ * row u, ordered by neighbour degree, highest first, ties by id ascending;
+ * row bounds are the CSR offsets.  Synchronises `stream`.  Errors: INVALID
+ * (NULL argument, graph built without the flag), CUDA.
+ */
+bfs_status bfs_graph_copy_hub_first(const bfs_graph* g, int32_t* cols_out, void* stream);
 
 /*
  * Device pointers of the DCSC tiles built with BFS_FLAG_BUILD_DCSC ("Graph

@@ -8,6 +8,8 @@ other.  The only module both sides use is ``graphgen`` (seeded inputs).
 Contents (each cites the passage of Bulu\\c{c} et al. 2015 it follows):
 
 * :func:`build_csr`       -- "Graph Representation" + "Data Sets" (numpy sort/unique)
+* :func:`hub_first`       -- the same rows, neighbours ordered by degree (the row order a
+                             bottom-up step may scan in; Algorithm 2 fixes none beyond "in order")
 * :func:`bfs_topdown`     -- Algorithm 1, serial FIFO (C)
 * :func:`bfs_bottomup`    -- Algorithm 2, serial (C)
 * :func:`min_parent`      -- (select2nd, min) semiring of the parallel top-down local discovery (C)
@@ -151,6 +153,19 @@ def build_csr(n: int, src: np.ndarray, dst: np.ndarray, chunk: int = 1 << 26) ->
 
 def csr_from_edges(g) -> CSR:
     return build_csr(g.n, g.src, g.dst)
+
+
+def hub_first(g: CSR) -> CSR:
+    """The same graph with every row reordered: neighbours by degree, highest
+    first, ties by id ascending.  Algorithm 2 scans a row "in order" and stops at
+    the first frontier neighbour; any order yields a valid parent one level
+    closer, and the per-level examination counts of the direction-optimizing
+    schedule (:func:`do_schedule`) follow the row order of the CSR passed in.
+    Written from the definition: one lexicographic sort of (row, -degree, id)."""
+    deg = g.degree()
+    rows = np.repeat(np.arange(g.n, dtype=np.int64), deg)
+    order = np.lexsort((g.cols, -deg[g.cols], rows))
+    return CSR(g.n, g.offsets.copy(), np.ascontiguousarray(g.cols[order], np.int32))
 
 
 def bfs_topdown(g: CSR, root: int):

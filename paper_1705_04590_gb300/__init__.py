@@ -15,8 +15,9 @@ column-block DCSC storage.  Hand-written CUDA for sm_103a behind a C ABI
 """
 from ._build import build, LIB
 from ._lib import (load, BfsError, MODE_DO, MODE_TD_ONLY, MODE_BU_ONLY, MODE_RANDOM, LAYOUT_CSR,
-                   LAYOUT_DCSC_TILED, PARENT_ANY, PARENT_MIN_ID, SIGNATURES)
+                   LAYOUT_DCSC_TILED, PARENT_ANY, PARENT_MIN_ID, BU_ROWS_BY_ID, BU_ROWS_HUB_FIRST, SIGNATURES)
 from .api import Graph, Server, options
 
 __all__ = ["build", "load", "Graph", "Server", "options", "BfsError", "LIB", "SIGNATURES", "MODE_DO", "MODE_TD_ONLY",
-           "MODE_BU_ONLY", "MODE_RANDOM", "LAYOUT_CSR", "LAYOUT_DCSC_TILED", "PARENT_ANY", "PARENT_MIN_ID"]
+           "MODE_BU_ONLY", "MODE_RANDOM", "LAYOUT_CSR", "LAYOUT_DCSC_TILED", "PARENT_ANY", "PARENT_MIN_ID",
+           "BU_ROWS_BY_ID", "BU_ROWS_HUB_FIRST"]

@@ -12,7 +12,8 @@ c_vp = ctypes.c_void_p
 BFS_OK, BFS_ERR_INVALID, BFS_ERR_OOM, BFS_ERR_CUDA, BFS_ERR_TIMEOUT, BFS_ERR_BUSY, BFS_ERR_NOT_READY, \
     BFS_ERR_UNSUPPORTED = range(8)
 
-FLAG_DEVICE_PTRS, FLAG_SYMMETRIZE, FLAG_BUILD_DCSC, FLAG_CHECK_SYMMETRY = 1, 2, 4, 8
+FLAG_DEVICE_PTRS, FLAG_SYMMETRIZE, FLAG_BUILD_DCSC, FLAG_CHECK_SYMMETRY, FLAG_BUILD_HUB_FIRST = 1, 2, 4, 8, 16
+BU_ROWS_BY_ID, BU_ROWS_HUB_FIRST = 0, 1
 MODE_DO, MODE_TD_ONLY, MODE_BU_ONLY, MODE_RANDOM = 0, 1, 2, 3
 LAYOUT_CSR, LAYOUT_DCSC_TILED = 0, 1
 PARENT_ANY, PARENT_MIN_ID = 0, 1
@@ -28,7 +29,7 @@ class Allocator(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("mode", c_i32), ("layout", c_i32), ("alpha", c_i32), ("beta", c_i32), ("parent_mode", c_i32),
                 ("td_big_degree", c_i32), ("timeout_ms", c_i64), ("seed", c_u64),
-                ("debug_barrier_extra", c_i32), ("reserved", c_i32)]
+                ("debug_barrier_extra", c_i32), ("bu_rows", c_i32)]
 
 
 class LevelRecord(ctypes.Structure):
@@ -57,6 +58,7 @@ SIGNATURES = [
     ("bfs_graph_info", c_i32, [c_vp, ctypes.POINTER(c_i64), ctypes.POINTER(c_i64), ctypes.POINTER(c_i64)]),
     ("bfs_graph_csr", c_i32, [c_vp, ctypes.POINTER(c_vp), ctypes.POINTER(c_vp)]),
     ("bfs_graph_copy_csr", c_i32, [c_vp, c_vp, c_vp, c_vp]),
+    ("bfs_graph_copy_hub_first", c_i32, [c_vp, c_vp, c_vp]),
     ("bfs_graph_dcsc", c_i32, [c_vp, ctypes.POINTER(DcscLayout)]),
     ("bfs_graph_copy_dcsc", c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     ("bfs_graph_destroy", None, [c_vp]),

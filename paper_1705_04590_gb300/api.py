@@ -67,12 +67,13 @@ class _TorchAllocator:
 
 def options(mode: int = L.MODE_DO, layout: int = L.LAYOUT_CSR, alpha: int = 14, beta: int = 24,
             parent_mode: int = L.PARENT_ANY, td_big_degree: int = 0, timeout_ms: int = 10000, seed: int = 0,
-            debug_barrier_extra: int = 0) -> L.Options:
+            debug_barrier_extra: int = 0, bu_rows: int = L.BU_ROWS_BY_ID) -> L.Options:
     o = L.Options()
     L.load().bfs_options_default(ctypes.byref(o))
     o.mode, o.layout, o.alpha, o.beta, o.parent_mode = mode, layout, alpha, beta, parent_mode
     o.td_big_degree, o.timeout_ms, o.seed, o.debug_barrier_extra = td_big_degree, timeout_ms, seed, \
         debug_barrier_extra
+    o.bu_rows = bu_rows
     return o
 
 
@@ -89,11 +90,13 @@ class Graph:
 
     # ---------------------------------------------------------------- creation
     @classmethod
-    def from_edges(cls, src, dst, n: int, dcsc: bool = False, stream=None, torch_allocator: bool = True) -> "Graph":
-        """src/dst: numpy int32 arrays (host) or int32 CUDA tensors (device)."""
+    def from_edges(cls, src, dst, n: int, dcsc: bool = False, stream=None, torch_allocator: bool = True,
+                   hub_first: bool = False) -> "Graph":
+        """src/dst: numpy int32 arrays (host) or int32 CUDA tensors (device).  hub_first also
+        stores rows ordered by neighbour degree (bottom-up option bu_rows=BU_ROWS_HUB_FIRST)."""
         lib = L.load()
         torch = _torch()
-        flags = L.FLAG_SYMMETRIZE | (L.FLAG_BUILD_DCSC if dcsc else 0)
+        flags = L.FLAG_SYMMETRIZE | (L.FLAG_BUILD_DCSC if dcsc else 0) | (L.FLAG_BUILD_HUB_FIRST if hub_first else 0)
         if isinstance(src, torch.Tensor):
             if src.numel() != dst.numel():
                 raise ValueError("src and dst differ in length")
@@ -117,10 +120,11 @@ class Graph:
 
     @classmethod
     def from_csr(cls, offsets, cols, n: int, check_symmetry: bool = False, dcsc: bool = False, stream=None,
-                 torch_allocator: bool = True) -> "Graph":
+                 torch_allocator: bool = True, hub_first: bool = False) -> "Graph":
         lib = L.load()
         torch = _torch()
-        flags = (L.FLAG_CHECK_SYMMETRY if check_symmetry else 0) | (L.FLAG_BUILD_DCSC if dcsc else 0)
+        flags = (L.FLAG_CHECK_SYMMETRY if check_symmetry else 0) | (L.FLAG_BUILD_DCSC if dcsc else 0) | \
+            (L.FLAG_BUILD_HUB_FIRST if hub_first else 0)
         if isinstance(offsets, torch.Tensor):
             po, pc = _dev_ptr(offsets, "int64", n + 1, "offsets"), _dev_ptr(cols, "int32", what="cols")
             nnz = cols.numel()
@@ -154,6 +158,12 @@ class Graph:
         cols = np.empty(max(self.nnz, 1), np.int32)
         L.check(L.load().bfs_graph_copy_csr(self._h, off.ctypes.data, cols.ctypes.data, None), "graph_copy_csr")
         return off, cols[: self.nnz]
+
+    def hub_first_host(self) -> np.ndarray:
+        """The hub-first column ids (graph built with hub_first=True) as a host array."""
+        cols = np.empty(max(self.nnz, 1), np.int32)
+        L.check(L.load().bfs_graph_copy_hub_first(self._h, cols.ctypes.data, None), "graph_copy_hub_first")
+        return cols[: self.nnz]
 
     def dcsc_layout(self) -> L.DcscLayout:
         d = L.DcscLayout()

@@ -57,6 +57,7 @@ static void destroy_graph(bfs_graph* g) {
     release_dcsc_tiles(g);
     g->mem.release(g->offsets, sizeof(int64_t) * (size_t)(g->n + 1), nullptr);
     g->mem.release(g->cols, sizeof(int32_t) * (size_t)(g->nnz + kColPad), nullptr);
+    if (g->cols_hf) g->mem.release(g->cols_hf, sizeof(int32_t) * (size_t)(g->nnz + kColPad), nullptr);
     g->mem.release(g->isolated, sizeof(uint32_t) * (size_t)g->W, nullptr);
     if (g->last_done) cudaEventDestroy(g->last_done);
     delete g;
@@ -105,6 +106,16 @@ static bfs_status check_options(const bfs_options* in, bfs_options* out, const b
     if (out->timeout_ms < 0) return fail(BFS_ERR_INVALID, "options.timeout_ms must be >= 0");
     if (out->td_big_degree != 0 && out->td_big_degree < 64) out->td_big_degree = 64;
     if (out->debug_barrier_extra < 0) return fail(BFS_ERR_INVALID, "options.debug_barrier_extra must be >= 0");
+    if (out->bu_rows != BFS_BU_ROWS_BY_ID && out->bu_rows != BFS_BU_ROWS_HUB_FIRST)
+        return fail(BFS_ERR_INVALID, "options.bu_rows must be a BFS_BU_ROWS_* value");
+    if (out->bu_rows == BFS_BU_ROWS_HUB_FIRST) {
+        if (!g->cols_hf)
+            return fail(BFS_ERR_UNSUPPORTED, "hub-first rows requested but the graph was built without "
+                                             "BFS_FLAG_BUILD_HUB_FIRST");
+        if (out->parent_mode != BFS_PARENT_ANY)
+            return fail(BFS_ERR_INVALID, "BFS_BU_ROWS_HUB_FIRST needs BFS_PARENT_ANY (minimum-id parents need id order)");
+        if (out->layout != BFS_LAYOUT_CSR) return fail(BFS_ERR_INVALID, "BFS_BU_ROWS_HUB_FIRST needs the CSR layout");
+    }
     return BFS_OK;
 }
 
@@ -152,6 +163,7 @@ bfs_status bfs_graph_create_from_edges(const int32_t* src, const int32_t* dst, i
     cudaStream_t s = (cudaStream_t)stream;
     st = build_csr_from_edges(g, src, dst, n_edges, (flags & BFS_FLAG_DEVICE_PTRS) != 0, s);
     if (st == BFS_OK && (flags & BFS_FLAG_BUILD_DCSC)) st = build_dcsc_tiles(g, s);
+    if (st == BFS_OK && (flags & BFS_FLAG_BUILD_HUB_FIRST)) st = build_hub_first_rows(g, s);
     if (st != BFS_OK) {
         std::string msg = bfs_last_error();
         destroy_graph(g);
@@ -176,6 +188,7 @@ bfs_status bfs_graph_create_from_csr(const int64_t* row_offsets, const int32_t* 
     st = build_csr_from_csr(g, row_offsets, col_ids, (flags & BFS_FLAG_DEVICE_PTRS) != 0,
                             (flags & BFS_FLAG_CHECK_SYMMETRY) != 0, s);
     if (st == BFS_OK && (flags & BFS_FLAG_BUILD_DCSC)) st = build_dcsc_tiles(g, s);
+    if (st == BFS_OK && (flags & BFS_FLAG_BUILD_HUB_FIRST)) st = build_hub_first_rows(g, s);
     if (st != BFS_OK) {
         std::string msg = bfs_last_error();
         destroy_graph(g);
@@ -209,6 +222,16 @@ bfs_status bfs_graph_copy_csr(const bfs_graph* g, int64_t* offsets_out, int32_t*
         BFS_CUDA_TRY(cudaMemcpyAsync(offsets_out, g->offsets, sizeof(int64_t) * (size_t)(g->n + 1), cudaMemcpyDefault, s));
     if (cols_out && g->nnz > 0)
         BFS_CUDA_TRY(cudaMemcpyAsync(cols_out, g->cols, sizeof(int32_t) * (size_t)g->nnz, cudaMemcpyDefault, s));
+    BFS_CUDA_TRY(cudaStreamSynchronize(s));
+    return BFS_OK;
+}
+
+bfs_status bfs_graph_copy_hub_first(const bfs_graph* g, int32_t* cols_out, void* stream) {
+    if (!g || !cols_out) return fail(BFS_ERR_INVALID, "NULL argument");
+    if (!g->cols_hf) return fail(BFS_ERR_INVALID, "graph was built without BFS_FLAG_BUILD_HUB_FIRST");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (g->nnz > 0)
+        BFS_CUDA_TRY(cudaMemcpyAsync(cols_out, g->cols_hf, sizeof(int32_t) * (size_t)g->nnz, cudaMemcpyDefault, s));
     BFS_CUDA_TRY(cudaStreamSynchronize(s));
     return BFS_OK;
 }

@@ -94,6 +94,7 @@ struct bfs_graph {
     int64_t* offsets = nullptr;     // [n+1]
     int32_t* cols = nullptr;        // [nnz + kColPad]
     uint32_t* isolated = nullptr;   // [W] bit v set when deg(v) = 0 or v >= n
+    int32_t* cols_hf = nullptr;     // [nnz + kColPad] rows ordered by neighbour degree (BFS_FLAG_BUILD_HUB_FIRST)
     int64_t W = 0;                  // bitmap words
     size_t graph_bytes = 0;
     bfsrt::DeviceAlloc mem;
@@ -119,6 +120,7 @@ bfs_status build_csr_from_csr(bfs_graph* g, const int64_t* off, const int32_t* c
                               bool check_symmetry, cudaStream_t s);
 bfs_status build_isolated_bitmap(bfs_graph* g, cudaStream_t s);
 bfs_status build_dcsc_tiles(bfs_graph* g, cudaStream_t s);
+bfs_status build_hub_first_rows(bfs_graph* g, cudaStream_t s);   // hub_first.cu
 void release_dcsc_tiles(bfs_graph* g);
 
 // bfs_single.cu

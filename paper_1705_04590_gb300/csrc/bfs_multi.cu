@@ -256,8 +256,8 @@ __device__ void ms_bu_phase(const MultiParams& p, unsigned long long active) {
         }
         if (miss && e > s) {
             const long long a = s & ~3LL;
-            const int4 x0 = __ldg(reinterpret_cast<const int4*>(p.cols + a));
-            const int4 x1 = __ldg(reinterpret_cast<const int4*>(p.cols + a + 4));
+            const int4 x0 = __ldg(reinterpret_cast<const int4*>(p.cols_bu + a));
+            const int4 x1 = __ldg(reinterpret_cast<const int4*>(p.cols_bu + a + 4));
             const int ids[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
 #pragma unroll
             for (int t = 0; t < 8; t++) {
@@ -276,7 +276,7 @@ __device__ void ms_bu_phase(const MultiParams& p, unsigned long long active) {
             for (long long q0 = ps; q0 < pe; q0 += 32) {
                 const long long q = q0 + lane;
                 unsigned long long x = 0;
-                if (q < pe) x = ldcg64(p.front + __ldg(p.cols + q));
+                if (q < pe) x = ldcg64(p.front + __ldg(p.cols_bu + q));
                 aL |= warp_or64(x);
                 if ((aL & mL) == mL) break;
             }
@@ -661,6 +661,7 @@ static MultiParams multi_params(bfs_graph* g, MultiWork& w, const bfs_options& o
     memset(&p, 0, sizeof p);
     p.off = reinterpret_cast<const long long*>(g->offsets);
     p.cols = g->cols;
+    p.cols_bu = (opt.bu_rows == BFS_BU_ROWS_HUB_FIRST && g->cols_hf) ? g->cols_hf : g->cols;
     p.n = g->n;
     p.nnz = g->nnz;
     p.seen = w.seen;
@@ -742,6 +743,7 @@ int ms_serve_max_grid(bfs_graph* g, MultiWork& w) { (void)g; return w.grid; }
 bfs_status ms_serve_reset(bfs_graph* g, MultiWork& w, cudaStream_t s) {
     bfs_options o;
     bfs_options_default(&o);
+    if (g->cols_hf) o.bu_rows = BFS_BU_ROWS_HUB_FIRST;
     MultiParams p = multi_params(g, w, o);
     bfsk::ms_clear_kernel<<<w.grid, w.block, 0, s>>>(p);
     BFS_CUDA_TRY(cudaGetLastError());
@@ -754,6 +756,7 @@ bfs_status ms_serve_launch(bfs_graph* g, MultiWork& w, const void* lane_table_ho
                            void* ctrl_pinned, cudaStream_t s) {
     bfs_options o;
     bfs_options_default(&o);
+    if (g->cols_hf) o.bu_rows = BFS_BU_ROWS_HUB_FIRST;   // levels do not depend on the row order
     MultiParams p = multi_params(g, w, o);
     p.active = active;
     grid = std::max(1, std::min(grid, w.grid));

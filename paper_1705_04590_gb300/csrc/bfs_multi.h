@@ -48,6 +48,7 @@ struct LaneTable {
 struct MultiParams {
     const long long* __restrict__ off;
     const int* __restrict__ cols;
+    const int* __restrict__ cols_bu;   // rows as the bottom-up pulls scan them (cols, or hub-first)
     long long n, nnz;
     unsigned long long* seen;
     unsigned long long* front;

@@ -71,6 +71,7 @@ struct Task {
 struct SingleParams {
     const long long* __restrict__ off;
     const int* __restrict__ cols;
+    const int* __restrict__ cols_bu;     // rows as the bottom-up steps scan them (cols, or hub-first)
     const unsigned* __restrict__ isolated;
     long long n, nnz, W;
     int* parent;
@@ -686,7 +687,7 @@ __device__ void bu_phase_a(const SingleParams& p, int d, const unsigned* fcur, u
         }
         int4 xa0 = z4, xb0 = z4;
         if (u0 >= 0 && e0 > s0) {
-            const int4* src = reinterpret_cast<const int4*>(p.cols + (s0 & ~3LL));
+            const int4* src = reinterpret_cast<const int4*>(p.cols_bu + (s0 & ~3LL));
             xa0 = ld_stream4(src);
             if (kWin == 8 && (s0 & ~3LL) + 4 < e0) xb0 = ld_stream4(src + 1);
         }
@@ -705,7 +706,7 @@ __device__ void bu_phase_a(const SingleParams& p, int d, const unsigned* fcur, u
             // round r+1: window
             int4 xa1 = z4, xb1 = z4;
             if (u1 >= 0 && e1 > s1) {
-                const int4* src = reinterpret_cast<const int4*>(p.cols + (s1 & ~3LL));
+                const int4* src = reinterpret_cast<const int4*>(p.cols_bu + (s1 & ~3LL));
                 xa1 = ld_stream4(src);
                 if (kWin == 8 && (s1 & ~3LL) + 4 < e1) xb1 = ld_stream4(src + 1);
             }
@@ -793,7 +794,7 @@ __device__ void bu_phase_b(const SingleParams& p, int d, const unsigned* fcur, u
         long long hitpos = -1;
         int pv = -1;
         while (pos < e0) {
-            const int4* src = reinterpret_cast<const int4*>(p.cols + pos);
+            const int4* src = reinterpret_cast<const int4*>(p.cols_bu + pos);
             const int4 xa = __ldg(src);
             const int4 xb = (pos + 4 < e0) ? __ldg(src + 1) : z4;
             const int ids[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
@@ -844,7 +845,7 @@ __device__ void bu_phase_b(const SingleParams& p, int d, const unsigned* fcur, u
             unsigned hb = 0;
             int4 x = make_int4(0, 0, 0, 0);
             if (live && pos < e0) {
-                x = ld_stream4(reinterpret_cast<const int4*>(p.cols + pos));
+                x = ld_stream4(reinterpret_cast<const int4*>(p.cols_bu + pos));
                 const int ids[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
                 for (int t = 0; t < 4; t++)
@@ -1366,6 +1367,7 @@ bfs_status single_launch(bfs_graph* g, const int32_t* roots_host, int32_t k, int
     SingleParams p;
     p.off = reinterpret_cast<const long long*>(g->offsets);
     p.cols = g->cols;
+    p.cols_bu = (opt.bu_rows == BFS_BU_ROWS_HUB_FIRST && g->cols_hf) ? g->cols_hf : g->cols;
     p.isolated = g->isolated;
     p.n = g->n;
     p.nnz = g->nnz;
@@ -1514,6 +1516,7 @@ extern "C" bfs_status bfs_run_csr_noalloc(const int64_t* row_offsets, const int3
     memset(&p, 0, sizeof p);
     p.off = reinterpret_cast<const long long*>(row_offsets);
     p.cols = col_ids;
+    p.cols_bu = col_ids;
     p.isolated = reinterpret_cast<const unsigned*>(b + bfsk::kStaticIsoOff);
     p.n = n;
     p.nnz = nnz;

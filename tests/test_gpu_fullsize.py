@@ -1,7 +1,9 @@
 """Full-size parity, in the launch configuration bench.py times (direction-optimizing,
 CSR, alpha 14, beta 24, one persistent launch per search).
 
-* R-MAT scale 26: the device CSR equals the oracle's bit for bit; levels of sampled
+* R-MAT scale 26 (built with the hub-first row copy, as bench.py builds it): the
+  device CSR equals the oracle's bit for bit; sampled hub-first rows equal the oracle's
+  definition; levels of sampled
   roots equal the oracle's serial Algorithm 1; every sampled root's levels and parents
   pass the oracle's certificate (a property that proves level = hop distance at any
   size); the per-level counters equal the oracle's direction-optimizing schedule.
@@ -28,7 +30,7 @@ def rmat26(gpu_lib):
     w = workloads.RMAT[26]
     e = w.edges()
     roots = w.roots(e, 64).tolist()
-    g = bfs.Graph.from_edges(e.src, e.dst, e.n)
+    g = bfs.Graph.from_edges(e.src, e.dst, e.n, hub_first=True)
     ref = oracle.build_csr(e.n, e.src, e.dst)
     del e
     yield w, g, ref, roots
@@ -63,6 +65,33 @@ def test_rmat26_levels_parents_schedule(gpu_lib, rmat26):
             rec = info["records"]
             for col, name in enumerate(["dir", "nf", "mf", "nnext", "mnext", "scanned", "examined"]):
                 assert np.array_equal(rec[:, col], getattr(s, name)), (root, name)
+
+
+def test_rmat26_hub_first_rows_and_searches(gpu_lib, rmat26):
+    """The bench's configuration (bottom-up over hub-first rows): sampled rows of the
+    device's reordered copy equal the oracle's definition; sampled roots' levels equal
+    the oracle's and pass the certificate with their parents."""
+    import torch
+    bfs = gpu_lib
+    _, g, ref, roots = rmat26
+    hf = g.hub_first_host()
+    deg = np.diff(ref.offsets)
+    rng = np.random.default_rng(2626)
+    for u in rng.choice(np.flatnonzero(deg > 0), 2000, replace=False).tolist() + [int(np.argmax(deg))]:
+        row = ref.cols[ref.offsets[u]:ref.offsets[u + 1]]
+        want = row[np.lexsort((row, -deg[row]))]
+        assert np.array_equal(hf[ref.offsets[u]:ref.offsets[u + 1]], want), u
+    del hf
+    labels = oracle.components(ref)
+    level = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    parent = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    opts = bfs.options(mode=bfs.MODE_DO, alpha=14, beta=24, bu_rows=bfs.BU_ROWS_HUB_FIRST)
+    for i, root in enumerate(roots[:4]):
+        g.run(root, parent=parent, level=level, opts=opts)
+        lv = level.cpu().numpy()
+        assert oracle.certify(ref, root, lv, parent.cpu().numpy(), labels) == (0, -1), root
+        if i < 1:
+            assert np.array_equal(lv, oracle.levels(ref, root)), root
 
 
 def test_torus4096_closed_form(gpu_lib):

@@ -90,3 +90,18 @@ def test_multi_torus_high_diameter(gpu_lib):
         dx = np.abs(x - x[r])
         dy = np.abs(y - y[r])
         assert np.array_equal(lv[i], np.minimum(dx, side - dx) + np.minimum(dy, side - dy))
+
+
+def test_multi_hub_first_rows(gpu_lib):
+    """Bottom-up pulls over hub-first rows give the same level rows (64 lanes, all
+    direction modes)."""
+    bfs = gpu_lib
+    w = workloads.RMAT[14]
+    e = w.edges()
+    ref = oracle.build_csr(e.n, e.src, e.dst)
+    g = bfs.Graph.from_edges(e.src, e.dst, e.n, hub_first=True)
+    roots = w.roots(e, 64).tolist()
+    want = np.stack([oracle.levels(ref, r) for r in roots])
+    for mode in (bfs.MODE_DO, bfs.MODE_BU_ONLY):
+        lv, _ = _run(bfs, g, roots, opts=bfs.options(mode=mode, bu_rows=bfs.BU_ROWS_HUB_FIRST))
+        assert np.array_equal(lv, want), mode

@@ -166,6 +166,47 @@ def test_path_bottom_up_only_same_level_discovery(gpu_lib):
         assert oracle.certify(case.ref, root, lv, pa, case.labels) == (0, -1)
 
 
+def test_hub_first_rows_and_searches(gpu_lib):
+    """BFS_FLAG_BUILD_HUB_FIRST: the device's reordered rows equal the oracle's
+    hub_first() bit for bit; searches scanning them bottom-up give exact levels,
+    valid parents, and per-level counters equal to the oracle's schedule over the
+    hub-first rows; the option is refused where it cannot apply."""
+    bfs = gpu_lib
+    graphs = [workloads.RMAT[14].edges(), graphgen.random_small(257, 600, 11), graphgen.torus(64, seed=3000),
+              graphgen.erdos_renyi(100_003, 800_000, seed=5), graphgen.path(700)]
+    modes = {bfs.MODE_DO: oracle.MODE_DO, bfs.MODE_TD_ONLY: oracle.MODE_TD, bfs.MODE_BU_ONLY: oracle.MODE_BU}
+    for e in graphs:
+        case = Case(bfs, e)
+        g = bfs.Graph.from_edges(e.src, e.dst, e.n, hub_first=True)
+        h = oracle.hub_first(case.ref)
+        assert np.array_equal(g.hub_first_host(), h.cols), e.name
+        case.g.close()
+        case.g = g
+        deg = np.diff(case.ref.offsets)
+        roots = [int(v) for v in np.flatnonzero(deg > 0)[[0, -1]]] + [int(np.argmax(deg))]
+        for root in roots:
+            want = oracle.levels(case.ref, root)
+            for mode, omode in modes.items():
+                opts = bfs.options(mode=mode, bu_rows=bfs.BU_ROWS_HUB_FIRST)
+                lv, pa, info = case.run(root, opts, stats=True)
+                assert np.array_equal(lv, want), (e.name, root, mode)
+                assert oracle.certify(case.ref, root, lv, pa, case.labels) == (0, -1), (e.name, root, mode)
+                s = oracle.do_schedule(h, want, omode, 14, 24)
+                rec = info["records"]
+                for col, name in enumerate(["dir", "nf", "mf", "nnext", "mnext", "scanned", "examined"]):
+                    assert np.array_equal(rec[:, col], getattr(s, name)), (e.name, root, mode, name)
+    plain = Case(bfs, graphgen.path(40))
+    with pytest.raises(bfs.BfsError) as ex:
+        plain.run(0, bfs.options(bu_rows=bfs.BU_ROWS_HUB_FIRST))
+    assert ex.value.status == 7          # BFS_ERR_UNSUPPORTED: graph built without the flag
+    g = bfs.Graph.from_edges(plain.e.src, plain.e.dst, plain.e.n, hub_first=True)
+    with pytest.raises(bfs.BfsError) as ex:
+        g.run(0, parent=plain.parent, opts=bfs.options(bu_rows=bfs.BU_ROWS_HUB_FIRST,
+                                                        parent_mode=bfs.PARENT_MIN_ID))
+    assert ex.value.status == 1          # BFS_ERR_INVALID: minimum-id parents need id order
+    g.close()
+
+
 def test_deep_levels_and_partial_outputs(gpu_lib):
     """Depths past 253 (levels are staged one byte per vertex up to depth 253,
     written directly beyond it), with both outputs, level only and parent only, in

@@ -348,3 +348,48 @@ def test_certificate_without_parents_needs_predecessors():
     zero = lv.copy()
     zero[np.flatnonzero(lv == 1)[0]] = 0                   # a second vertex at level 0
     assert oracle.certify(c, root, zero, None, lab)[0] == 2
+
+
+# ------------------------------------------------------------------ hub-first row order
+
+@pytest.mark.parametrize("seed", range(3))
+def test_hub_first_rows_match_definition(seed):
+    """Each row of hub_first() is the same neighbour set, in the order given by a
+    plain Python sort on (-degree, id) of the set-built adjacency."""
+    g = graphgen.rmat(9, seed=700 + seed)
+    c = csr(g)
+    h = oracle.hub_first(c)
+    adj = _set_csr(g.n, g.src, g.dst)
+    deg = [len(a) for a in adj]
+    assert np.array_equal(h.offsets, c.offsets)
+    for u in range(g.n):
+        want = sorted(adj[u], key=lambda v: (-deg[v], v))
+        assert h.cols[h.offsets[u]:h.offsets[u + 1]].tolist() == want
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_hub_first_schedule_counts_follow_row_order(seed):
+    """Levels do not depend on the row order; the bottom-up examination counts of
+    the schedule equal a literal walk of Algorithm 2 over the hub-first rows; and
+    in that order each searcher stops at its frontier neighbour of highest degree."""
+    g = graphgen.rmat(8, seed=310 + seed)
+    c = csr(g)
+    h = oracle.hub_first(c)
+    root = int(graphgen.pick_roots(g, 1, seed)[0])
+    lv = oracle.levels(c, root)
+    assert np.array_equal(oracle.levels(h, root), lv)
+    s = oracle.do_schedule(h, lv, mode=oracle.MODE_BU)
+    for d in range(s.num_levels):
+        assert (s.scanned[d], s.examined[d]) == _alg2_walk(h, lv, d)
+    # a vertex reached at level d+1 examines, in hub-first order, up to and
+    # including its first level-d neighbour of highest degree
+    deg = np.diff(c.offsets)
+    for d in range(s.num_levels):
+        total = 0
+        for u in np.flatnonzero((lv > d) | (lv < 0)):
+            row = h.cols[h.offsets[u]:h.offsets[u + 1]]
+            hits = np.flatnonzero(lv[row] == d)
+            total += int(hits[0]) + 1 if hits.size else row.size
+            if hits.size:
+                assert deg[row[hits[0]]] == deg[row[lv[row] == d]].max()
+        assert total == s.examined[d]
