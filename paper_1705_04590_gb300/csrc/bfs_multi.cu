@@ -343,15 +343,18 @@ __device__ void ms_apply_all_phase(const MultiParams& p, MCtrl* c, int slot, int
                 an += 1;
                 am += (unsigned long long)deg;
                 if ((s & active) != active && ((s | x) & active) == active) adone += (unsigned long long)deg;
-                unsigned long long bits = x;
-                while (bits) {
-                    const int i2 = __ffsll((long long)bits) - 1;
-                    bits &= bits - 1;
-                    L.rows[i2][v] = iter + 1 - L.start[i2];
-                }
             } else if (ldcg64(p.front + v)) {
                 p.front[v] = 0ull;
             }
+        }
+        // level rows: the warp walks the lanes any of its 32 vertices gained, one
+        // lane at a time, so each store instruction writes consecutive vertices of
+        // one row (a lane-by-lane walk per thread would scatter every store)
+        unsigned long long ub = warp_or64(x);
+        while (ub) {
+            const int i2 = __ffsll((long long)ub) - 1;
+            ub &= ub - 1;
+            if ((x >> i2) & 1ull) L.rows[i2][v] = iter + 1 - L.start[i2];
         }
         m_append(st, nq, nlen, x != 0ull, (int)v);
     }
