@@ -129,6 +129,13 @@ bfs_status single_launch(bfs_graph* g, const int32_t* roots_host, int32_t k, int
                          int32_t* level, const bfs_options& opt, cudaStream_t s);
 bfs_status single_collect(bfs_graph* g, cudaStream_t s, bfs_stats* stats);
 void single_release(bfs_graph* g);
+// the same on a caller-held search state (the server's concurrent searches)
+bfs_status single_prepare_work(bfs_graph* g, SingleWork& w, cudaStream_t s, int grid);
+bfs_status single_launch_work(bfs_graph* g, SingleWork& w, const int32_t* roots_host, int32_t k, int32_t* parent,
+                              int32_t* level, const bfs_options& opt, cudaStream_t s);
+void single_release_work(bfs_graph* g, SingleWork& w);
+size_t single_ctrl_bytes();
+unsigned single_ctrl_status(const void* ctrl_host);
 
 // bfs_multi.cu
 bfs_status multi_prepare(bfs_graph* g, cudaStream_t s);

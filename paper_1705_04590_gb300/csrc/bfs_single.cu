@@ -1292,8 +1292,11 @@ using bfsk::Ctrl;
 using bfsk::SingleParams;
 using bfsk::Task;
 
-bfs_status single_prepare(bfs_graph* g, cudaStream_t s) {
-    SingleWork& w = g->single;
+bfs_status single_prepare(bfs_graph* g, cudaStream_t s) { return single_prepare_work(g, g->single, s, 0); }
+
+// Work buffers of one single-source search state on graph g; grid > 0 caps the
+// launch grid (a server runs several searches side by side with small grids).
+bfs_status single_prepare_work(bfs_graph* g, SingleWork& w, cudaStream_t s, int grid) {
     if (w.ready) return BFS_OK;
     const long long n = g->n, W = g->W;
     const long long task_cap = g->nnz / bfsk::kChunk + g->nnz / 64 + 1024;  // big degree is >= 64
@@ -1331,13 +1334,15 @@ bfs_status single_prepare(bfs_graph* g, cudaStream_t s) {
     if (nb < 1) return fail(BFS_ERR_UNSUPPORTED, "BFS kernel cannot be resident on this device");
     w.block = bfsk::kBlock;
     w.grid = nb * g->sm_count;
+    if (grid > 0 && grid < w.grid) w.grid = grid;
     BFS_CUDA_TRY(cudaMemsetAsync(w.ctrl, 0, sizeof(Ctrl), s));
     w.ready = true;
     return BFS_OK;
 }
 
-void single_release(bfs_graph* g) {
-    SingleWork& w = g->single;
+void single_release(bfs_graph* g) { single_release_work(g, g->single); }
+
+void single_release_work(bfs_graph* g, SingleWork& w) {
     if (!w.ready) return;
     const long long n = g->n, W = g->W;
     g->mem.release(w.visited, sizeof(unsigned) * (size_t)W, nullptr);
@@ -1355,7 +1360,11 @@ void single_release(bfs_graph* g) {
 
 bfs_status single_launch(bfs_graph* g, const int32_t* roots_host, int32_t k, int32_t* parent,
                          int32_t* level, const bfs_options& opt, cudaStream_t s) {
-    SingleWork& w = g->single;
+    return single_launch_work(g, g->single, roots_host, k, parent, level, opt, s);
+}
+
+bfs_status single_launch_work(bfs_graph* g, SingleWork& w, const int32_t* roots_host, int32_t k, int32_t* parent,
+                              int32_t* level, const bfs_options& opt, cudaStream_t s) {
     if (opt.parent_mode == BFS_PARENT_MIN_ID && parent && !level) {
         // minimum-id parents are picked by level; keep them in a private array
         if (!w.level_scratch) {
@@ -1432,6 +1441,9 @@ bfs_status single_launch(bfs_graph* g, const int32_t* roots_host, int32_t k, int
     BFS_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, dyn, s));
     return BFS_OK;
 }
+
+size_t single_ctrl_bytes() { return sizeof(Ctrl); }
+unsigned single_ctrl_status(const void* ctrl_host) { return reinterpret_cast<const Ctrl*>(ctrl_host)->b.status; }
 
 bfs_status single_collect(bfs_graph* g, cudaStream_t s, bfs_stats* stats) {
     SingleWork& w = g->single;

@@ -14,6 +14,13 @@
 //      is copied to the caller's host buffer and the ticket completes.
 // Level values of a lane count from its own start, so a query gets the same
 // levels whether it ran alone or in a mix (tested).
+//
+// Graphs of large diameter (a probe search at add time takes more than
+// kDeepLevels levels, e.g. a torus) gain little from lanes: their levels are
+// short and many, and every lane pays every level.  Such a slot instead runs
+// each query as its own single-source search with a small grid on one of
+// kDeepExecs streams; those cooperative launches proceed side by side, each
+// bound by its own level latency rather than by the device's throughput.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -35,6 +42,8 @@ namespace {
 enum TicketState { kQueued = 0, kRunning = 1, kDone = 2, kFailed = 3 };
 
 constexpr int kMinCtas = 8;   // smallest grid of a slot's launch
+constexpr int kDeepLevels = 128;   // probe levels above which a slot runs concurrent single searches
+constexpr int kDeepExecs = 8;      // concurrent single-source searches of such a slot
 
 struct Ticket {
     int slot = 0;
@@ -57,8 +66,21 @@ struct CopyBatch {
     std::vector<uint64_t> tickets;
 };
 
+// One single-source search in flight of a deep slot.
+struct Exec {
+    SingleWork w;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev = nullptr;
+    int32_t* dlevel = nullptr;    // device [n]
+    void* ctrl_pinned = nullptr;  // host copy of the search's control block (status)
+    uint64_t ticket = 0;
+    bool busy = false;
+};
+
 struct Slot {
     bfs_graph* g = nullptr;
+    bool deep = false;                   // queries run as concurrent single-source searches (execs)
+    std::vector<Exec*> execs;
     MultiWork w;
     cudaStream_t stream = nullptr;       // levels of this slot
     cudaStream_t copy_stream = nullptr;  // result rows to host
@@ -128,6 +150,73 @@ cudaEvent_t take_event(Slot& s) {
     return e;
 }
 
+// A deep slot: complete finished searches, start queued ones on free execs.
+bool step_deep(bfs_server* sv, Slot& s) {
+    bool progress = false;
+    for (Exec* ex : s.execs) {
+        if (ex->busy) {
+            const cudaError_t q = cudaEventQuery(ex->ev);
+            if (q == cudaErrorNotReady) continue;
+            const bool ok = q == cudaSuccess && single_ctrl_status(ex->ctrl_pinned) == 0;
+            if (q != cudaSuccess) (void)cudaGetLastError();
+            {
+                std::lock_guard<std::mutex> lk(sv->mu);
+                Ticket& t = sv->tickets[ex->ticket];
+                t.state = ok ? kDone : kFailed;
+                t.err = ok ? BFS_OK : (q != cudaSuccess ? BFS_ERR_CUDA : BFS_ERR_TIMEOUT);
+                t.t_done = Clock::now();
+                if (!ok) sv->fatal = q != cudaSuccess ? cudaGetErrorString(q) : "device status error (barrier timeout)";
+                sv->completed++;
+            }
+            ex->busy = false;
+            progress = true;
+            sv->cv_done.notify_all();
+        }
+        uint64_t tk = 0;
+        int root = 0;
+        int32_t* out = nullptr;
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            if (s.queue.empty()) continue;   // still look at the other searches in flight
+            tk = s.queue.front();
+            s.queue.pop_front();
+            sv->queued--;
+            Ticket& t = sv->tickets[tk];
+            t.state = kRunning;
+            root = t.root;
+            out = t.host_out;
+        }
+        bfs_options o;
+        bfs_options_default(&o);
+        if (s.g->cols_hf) o.bu_rows = BFS_BU_ROWS_HUB_FIRST;
+        bfs_status st = single_launch_work(s.g, ex->w, &root, 1, nullptr, ex->dlevel, o, ex->stream);
+        if (st == BFS_OK &&
+            (cudaMemcpyAsync(ex->ctrl_pinned, ex->w.ctrl, single_ctrl_bytes(), cudaMemcpyDeviceToHost, ex->stream) !=
+                 cudaSuccess ||
+             cudaMemcpyAsync(out, ex->dlevel, sizeof(int32_t) * (size_t)s.g->n, cudaMemcpyDeviceToHost, ex->stream) !=
+                 cudaSuccess ||
+             cudaEventRecord(ex->ev, ex->stream) != cudaSuccess))
+            st = BFS_ERR_CUDA;
+        if (st != BFS_OK) {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            Ticket& t = sv->tickets[tk];
+            t.state = kFailed;
+            t.err = st;
+            t.t_done = Clock::now();
+            sv->fatal = bfs_last_error();
+            sv->cv_done.notify_all();
+            continue;
+        }
+        ex->ticket = tk;
+        ex->busy = true;
+        progress = true;
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->launches++;
+        sv->lanes_filled++;
+    }
+    return progress;
+}
+
 // Worker loop.  Slots progress independently: a slot whose launch ended is
 // harvested (finished lanes -> rows copied out on the copy stream), refilled
 // from its queue (new lanes join at this level boundary) and relaunched; a
@@ -140,8 +229,11 @@ void worker_main(bfs_server* sv) {
         {
             std::unique_lock<std::mutex> lk(sv->mu);
             auto has_work = [&] {
-                for (Slot* s : sv->slots)
+                for (Slot* s : sv->slots) {
                     if (s->running || s->active || !s->queue.empty() || !s->copies.empty()) return true;
+                    for (Exec* ex : s->execs)
+                        if (ex->busy) return true;
+                }
                 return false;
             };
             sv->cv_work.wait(lk, [&] { return sv->stop || has_work(); });
@@ -154,6 +246,10 @@ void worker_main(bfs_server* sv) {
         for (Slot* sp : snap) busy += (sp->running || sp->active || !sp->queue.empty()) ? 1 : 0;
         for (Slot* sp : snap) {
             Slot& s = *sp;
+            if (s.deep) {
+                progress |= step_deep(sv, s);
+                continue;
+            }
             // ---------------------------------------------- harvest a finished launch
             if (s.running) {
                 const cudaError_t q = cudaEventQuery(s.ev);
@@ -268,6 +364,69 @@ void worker_main(bfs_server* sv) {
     }
 }
 
+// Levels of one search from the first vertex with neighbours (0 if the graph has none).
+bfs_status probe_levels(bfs_graph* g, int* levels) {
+    *levels = 0;
+    const long long words = std::min<long long>(g->W, 1 << 16);
+    std::vector<uint32_t> iso((size_t)words);
+    if (cudaMemcpy(iso.data(), g->isolated, sizeof(uint32_t) * (size_t)words, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return cuda_fail(cudaGetLastError(), "probe: isolated bitmap");
+    int root = -1;
+    for (long long w = 0; w < words && root < 0; w++)
+        if (iso[(size_t)w] != 0xFFFFFFFFu) root = (int)(w * 32 + __builtin_ctz(~iso[(size_t)w]));
+    if (root < 0) return BFS_OK;
+    int32_t* lv = nullptr;
+    if (cudaMalloc(&lv, sizeof(int32_t) * (size_t)g->n) != cudaSuccess) return fail(BFS_ERR_OOM, "probe: level buffer");
+    bfs_level_record recs[1];
+    bfs_stats st;
+    memset(&st, 0, sizeof st);
+    st.levels = recs;
+    st.levels_capacity = 1;
+    const bfs_status r = bfs_run(g, root, nullptr, lv, nullptr, nullptr, &st);
+    cudaFree(lv);
+    if (r != BFS_OK) return r;
+    *levels = st.num_levels;
+    return BFS_OK;
+}
+
+bfs_status add_execs(bfs_server* sv, Slot* s) {
+    const int grid = std::max(kMinCtas, 2 * s->g->sm_count / kDeepExecs);
+    for (int i = 0; i < kDeepExecs; i++) {
+        Exec* ex = new (std::nothrow) Exec();
+        if (!ex) return fail(BFS_ERR_OOM, "host allocation of a search executor");
+        s->execs.push_back(ex);
+        if (cudaStreamCreateWithFlags(&ex->stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ex->ev, cudaEventDisableTiming) != cudaSuccess)
+            return fail(BFS_ERR_CUDA, "search executor stream / event");
+        if (cudaMallocHost(&ex->ctrl_pinned, single_ctrl_bytes()) != cudaSuccess)
+            return fail(BFS_ERR_OOM, "search executor control copy");
+        const int64_t row = (int64_t)sizeof(int32_t) * s->g->n;
+        if (sv->used + row > sv->budget) return fail(BFS_ERR_OOM, "HBM budget too small for the search executors");
+        if (cudaMalloc(&ex->dlevel, (size_t)row) != cudaSuccess) {
+            ex->dlevel = nullptr;
+            return fail(BFS_ERR_OOM, "search executor level buffer");
+        }
+        bfs_status r = single_prepare_work(s->g, ex->w, ex->stream, grid);
+        if (r != BFS_OK) return r;
+        if (cudaStreamSynchronize(ex->stream) != cudaSuccess) return fail(BFS_ERR_CUDA, "search executor setup");
+        sv->used += row + (int64_t)ex->w.bytes;
+    }
+    return BFS_OK;
+}
+
+void free_execs(Slot* s) {
+    for (Exec* ex : s->execs) {
+        if (ex->stream) cudaStreamSynchronize(ex->stream);
+        single_release_work(s->g, ex->w);
+        if (ex->dlevel) cudaFree(ex->dlevel);
+        if (ex->ctrl_pinned) cudaFreeHost(ex->ctrl_pinned);
+        if (ex->ev) cudaEventDestroy(ex->ev);
+        if (ex->stream) cudaStreamDestroy(ex->stream);
+        delete ex;
+    }
+    s->execs.clear();
+}
+
 }  // namespace
 
 extern "C" {
@@ -297,6 +456,25 @@ bfs_status bfs_server_add_graph(bfs_server* sv, bfs_graph* g, int32_t* slot) {
     Slot* s = new (std::nothrow) Slot();
     if (!s) return fail(BFS_ERR_OOM, "host allocation of a slot");
     s->g = g;
+    int deep_levels = 0;
+    bfs_status pr = probe_levels(g, &deep_levels);
+    if (pr != BFS_OK) {
+        delete s;
+        return fail(pr, std::string("server: add_graph: probe search: ") + bfs_last_error());
+    }
+    if (deep_levels > kDeepLevels) {
+        s->deep = true;
+        bfs_status r = add_execs(sv, s);
+        if (r != BFS_OK) {
+            std::string msg = bfs_last_error();
+            free_execs(s);
+            delete s;
+            return fail(r, "server: add_graph: " + msg);
+        }
+        sv->slots.push_back(s);
+        if (slot) *slot = (int32_t)(sv->slots.size() - 1);
+        return BFS_OK;
+    }
     const int64_t need = (int64_t)(3 * sizeof(unsigned long long) * (size_t)g->n);
     if (sv->used + need > sv->budget) {
         delete s;
@@ -409,6 +587,11 @@ void bfs_server_destroy(bfs_server* sv) {
     sv->cv_work.notify_all();
     if (sv->worker.joinable()) sv->worker.join();
     for (Slot* s : sv->slots) {
+        if (s->deep) {
+            free_execs(s);
+            delete s;
+            continue;
+        }
         cudaStreamSynchronize(s->stream);
         cudaStreamSynchronize(s->copy_stream);
         for (auto& L : s->lanes)

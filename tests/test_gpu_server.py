@@ -77,3 +77,39 @@ def test_server_budget_limits_lanes(gpu_lib):
     with pytest.raises(bfs.BfsError):
         srv.poll(123456789)
     srv.close()
+
+
+def test_server_deep_graph_runs_concurrent_searches(gpu_lib):
+    """A graph of large diameter (256 x 256 torus: 257 levels) is served by concurrent
+    single-source searches instead of lanes; mixed with an R-MAT slot, every result
+    still equals the oracle / the torus closed form, alone and in a burst."""
+    bfs = gpu_lib
+    side = 256
+    et = graphgen.torus(side, seed=3000)
+    inv = graphgen.torus_coordinates(side, seed=3000)
+    x, y = inv % side, inv // side
+    er = workloads.RMAT[12].edges()
+    rref = oracle.build_csr(er.n, er.src, er.dst)
+    gt = bfs.Graph.from_edges(et.src, et.dst, et.n)
+    gr = bfs.Graph.from_edges(er.src, er.dst, er.n)
+    srv = bfs.Server(hbm_budget_bytes=4 << 30, max_lanes=64)
+    st_, sr_ = srv.add_graph(gt), srv.add_graph(gr)
+    rng = np.random.default_rng(21)
+    troots = rng.integers(0, et.n, 40).tolist()
+    rroots = graphgen.pick_roots(er, 40, 9).tolist()
+    outs = []
+    for a, b in zip(troots, rroots):
+        ot, orr = np.empty(et.n, np.int32), np.empty(er.n, np.int32)
+        outs.append(("t", a, ot, srv.submit(st_, a, ot)))
+        outs.append(("r", b, orr, srv.submit(sr_, b, orr)))
+    for kind, root, out, t in outs:
+        assert srv.wait(t, 120000)
+        if kind == "t":
+            dx, dy = np.abs(x - x[root]), np.abs(y - y[root])
+            want = np.minimum(dx, side - dx) + np.minimum(dy, side - dy)
+        else:
+            want = oracle.levels(rref, root)
+        assert np.array_equal(out, want), (kind, root)
+    srv.close()
+    gt.close()
+    gr.close()
