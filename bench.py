@@ -391,7 +391,8 @@ def served_section(g26, roots26, n_queries: int = 2000, seed: int = 5151) -> dic
                 # buffer pool of this graph exhausted: retire the oldest in-flight query of that graph
                 for idx, (tk, gj, bi) in enumerate(inflight):
                     if gj == gi:
-                        srv.wait(tk)
+                        if not srv.wait(tk, 300_000):
+                            raise RuntimeError("served query did not complete within 300 s")
                         lat.append(srv.latency_us(tk))
                         done_m += ms[gj]
                         free[gj].append(bi)
@@ -413,7 +414,8 @@ def served_section(g26, roots26, n_queries: int = 2000, seed: int = 5151) -> dic
                         keep.append((tk, gj, bj))
                 inflight = keep
         for tk, gj, bj in inflight:
-            srv.wait(tk)
+            if not srv.wait(tk, 300_000):
+                raise RuntimeError("served query did not complete within 300 s")
             lat.append(srv.latency_us(tk))
             done_m += ms[gj]
         wall = time.perf_counter() - t0

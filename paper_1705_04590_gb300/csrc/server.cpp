@@ -15,12 +15,17 @@
 // Level values of a lane count from its own start, so a query gets the same
 // levels whether it ran alone or in a mix (tested).
 //
-// Graphs of large diameter (a probe search at add time takes more than
-// kDeepLevels levels, e.g. a torus) gain little from lanes: their levels are
-// short and many, and every lane pays every level.  Such a slot instead runs
-// each query as its own single-source search with a small grid on one of
-// kDeepExecs streams; those cooperative launches proceed side by side, each
-// bound by its own level latency rather than by the device's throughput.
+// Lanes pay off only when many queries of a graph are in flight: a 64-lane
+// search with one or two lanes busy costs several plain searches.  Every slot
+// therefore also owns a few executors, each a single-source search state with
+// its own stream; while a slot's lanes are idle and its queue is short
+// (< kLaneBatch), queued queries run as plain searches on free executors, and
+// once the queue grows they join lanes again.  Graphs of large diameter (a
+// probe search at add time takes more than kDeepLevels levels, e.g. a torus)
+// gain nothing from lanes -- their levels are short and many, and every lane
+// pays every level -- so their slots use kDeepExecs executors with small grids
+// only; those cooperative launches run side by side, each bound by its own
+// level latency rather than by the device's throughput.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -44,6 +49,8 @@ enum TicketState { kQueued = 0, kRunning = 1, kDone = 2, kFailed = 3 };
 constexpr int kMinCtas = 8;   // smallest grid of a slot's launch
 constexpr int kDeepLevels = 128;   // probe levels above which a slot runs concurrent single searches
 constexpr int kDeepExecs = 8;      // concurrent single-source searches of such a slot
+constexpr int kExecs = 2;          // executors of every other slot
+constexpr size_t kLaneBatch = 8;   // a queue this long (or busy lanes) sends queries to lanes
 
 struct Ticket {
     int slot = 0;
@@ -150,8 +157,9 @@ cudaEvent_t take_event(Slot& s) {
     return e;
 }
 
-// A deep slot: complete finished searches, start queued ones on free execs.
-bool step_deep(bfs_server* sv, Slot& s) {
+// Executors of a slot: complete finished searches and, if `start`, put queued
+// queries on the free ones.
+bool step_execs(bfs_server* sv, Slot& s, bool start) {
     bool progress = false;
     for (Exec* ex : s.execs) {
         if (ex->busy) {
@@ -172,6 +180,7 @@ bool step_deep(bfs_server* sv, Slot& s) {
             progress = true;
             sv->cv_done.notify_all();
         }
+        if (!start || ex->busy) continue;
         uint64_t tk = 0;
         int root = 0;
         int32_t* out = nullptr;
@@ -247,9 +256,17 @@ void worker_main(bfs_server* sv) {
         for (Slot* sp : snap) {
             Slot& s = *sp;
             if (s.deep) {
-                progress |= step_deep(sv, s);
+                progress |= step_execs(sv, s, true);
                 continue;
             }
+            // short queue, idle lanes: plain searches on the executors
+            bool to_execs = false;
+            if (!s.running && !s.active && s.copies.empty()) {
+                std::lock_guard<std::mutex> lk(sv->mu);
+                to_execs = s.queue.size() < kLaneBatch;
+            }
+            progress |= step_execs(sv, s, to_execs);
+            if (to_execs) continue;
             // ---------------------------------------------- harvest a finished launch
             if (s.running) {
                 const cudaError_t q = cudaEventQuery(s.ev);
@@ -389,9 +406,17 @@ bfs_status probe_levels(bfs_graph* g, int* levels) {
     return BFS_OK;
 }
 
-bfs_status add_execs(bfs_server* sv, Slot* s) {
-    const int grid = std::max(kMinCtas, 2 * s->g->sm_count / kDeepExecs);
-    for (int i = 0; i < kDeepExecs; i++) {
+// Up to `count` executors with launch grid `grid`, as many as the HBM budget
+// leaves room for; fewer than `min_count` is an error.
+bfs_status add_execs(bfs_server* sv, Slot* s, int count, int grid, int min_count) {
+    const int64_t row = (int64_t)sizeof(int32_t) * s->g->n;
+    // a search state holds two vertex queues, the level staging, the hub tasks and bitmaps
+    const int64_t state = 9 * s->g->n + 20 * s->g->nnz / 64 + (1 << 22);
+    for (int i = 0; i < count; i++) {
+        if (sv->used + row + state > sv->budget) {
+            if (i >= min_count) return BFS_OK;
+            return fail(BFS_ERR_OOM, "HBM budget too small for the search executors");
+        }
         Exec* ex = new (std::nothrow) Exec();
         if (!ex) return fail(BFS_ERR_OOM, "host allocation of a search executor");
         s->execs.push_back(ex);
@@ -400,8 +425,6 @@ bfs_status add_execs(bfs_server* sv, Slot* s) {
             return fail(BFS_ERR_CUDA, "search executor stream / event");
         if (cudaMallocHost(&ex->ctrl_pinned, single_ctrl_bytes()) != cudaSuccess)
             return fail(BFS_ERR_OOM, "search executor control copy");
-        const int64_t row = (int64_t)sizeof(int32_t) * s->g->n;
-        if (sv->used + row > sv->budget) return fail(BFS_ERR_OOM, "HBM budget too small for the search executors");
         if (cudaMalloc(&ex->dlevel, (size_t)row) != cudaSuccess) {
             ex->dlevel = nullptr;
             return fail(BFS_ERR_OOM, "search executor level buffer");
@@ -464,7 +487,7 @@ bfs_status bfs_server_add_graph(bfs_server* sv, bfs_graph* g, int32_t* slot) {
     }
     if (deep_levels > kDeepLevels) {
         s->deep = true;
-        bfs_status r = add_execs(sv, s);
+        bfs_status r = add_execs(sv, s, kDeepExecs, std::max(kMinCtas, 2 * g->sm_count / kDeepExecs), 1);
         if (r != BFS_OK) {
             std::string msg = bfs_last_error();
             free_execs(s);
@@ -505,6 +528,22 @@ bfs_status bfs_server_add_graph(bfs_server* sv, bfs_graph* g, int32_t* slot) {
         return fail(r, "server: add_graph: " + msg);
     }
     if (sv->total_ctas == 0) sv->total_ctas = ms_serve_max_grid(g, s->w);
+    {
+        // plain searches of this graph: about one CTA per 32K vertices, up to half the device
+        const int grid = (int)std::min<long long>(std::max<long long>(kMinCtas, g->n >> 15), sv->total_ctas / 2);
+        bfs_status r = add_execs(sv, s, kExecs, grid, 0);
+        if (r != BFS_OK) {
+            std::string msg = bfs_last_error();
+            free_execs(s);
+            multi_free(g, s->w);
+            cudaEventDestroy(s->ev);
+            cudaFreeHost(s->ctrl_pinned);
+            cudaStreamDestroy(s->stream);
+            cudaStreamDestroy(s->copy_stream);
+            delete s;
+            return fail(r, "server: add_graph: " + msg);
+        }
+    }
     memset(s->ctrl_pinned, 0, sizeof(bfsk::MCtrl));
     s->table.assign(ms_lane_table_bytes(), 0);
     sv->used += (int64_t)s->w.bytes;
@@ -592,6 +631,7 @@ void bfs_server_destroy(bfs_server* sv) {
             delete s;
             continue;
         }
+        free_execs(s);
         cudaStreamSynchronize(s->stream);
         cudaStreamSynchronize(s->copy_stream);
         for (auto& L : s->lanes)
