@@ -318,8 +318,14 @@ bfs_status bfs_graph_sync(bfs_graph* g, void* stream);
  * running multi-source search; a query is admitted into a free slot at the
  * next level boundary (its lane starts at the current iteration, and its
  * levels count from there), so queries that arrive while others run share
- * the device work.  Admission is bounded by hbm_budget_bytes for per-query
- * state.  A host thread drives the device; outputs land in caller memory.
+ * the device work.  Each graph also keeps up to two plain single-source
+ * search states: while its lanes are idle and fewer than 8 queries wait, a
+ * query runs as a plain search on one of them.  A graph whose probe search at
+ * add time needs more than 128 levels (large diameter, e.g. a torus) is served
+ * by up to 8 plain searches running side by side with small grids instead of
+ * lanes.  Levels are the same on every path.  Admission is bounded by
+ * hbm_budget_bytes for per-query state and search states.  A host thread
+ * drives the device; outputs land in caller memory.
  */
 bfs_status bfs_server_create(int64_t hbm_budget_bytes, int32_t max_lanes, bfs_server** out);
 
