@@ -319,8 +319,9 @@ bfs_status bfs_graph_sync(bfs_graph* g, void* stream);
  * next level boundary (its lane starts at the current iteration, and its
  * levels count from there), so queries that arrive while others run share
  * the device work.  Each graph also keeps up to two plain single-source
- * search states: while its lanes are idle and fewer than 8 queries wait, a
- * query runs as a plain search on one of them.  A graph whose probe search at
+ * search states that take queued queries first (plain searches); lanes open
+ * for the overflow once 8 or more queries wait, and keep admitting while they
+ * run.  A graph whose probe search at
  * add time needs more than 128 levels (large diameter, e.g. a torus) is served
  * by up to 8 plain searches running side by side with small grids instead of
  * lanes.  Levels are the same on every path.  Admission is bounded by

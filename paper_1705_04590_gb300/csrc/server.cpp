@@ -18,9 +18,9 @@
 // Lanes pay off only when many queries of a graph are in flight: a 64-lane
 // search with one or two lanes busy costs several plain searches.  Every slot
 // therefore also owns a few executors, each a single-source search state with
-// its own stream; while a slot's lanes are idle and its queue is short
-// (< kLaneBatch), queued queries run as plain searches on free executors, and
-// once the queue grows they join lanes again.  Graphs of large diameter (a
+// its own stream; free executors take queued queries first (plain searches),
+// and lanes take the overflow: a slot opens lanes once kLaneBatch queries wait
+// (and keeps admitting into them while they run).  Graphs of large diameter (a
 // probe search at add time takes more than kDeepLevels levels, e.g. a torus)
 // gain nothing from lanes -- their levels are short and many, and every lane
 // pays every level -- so their slots use kDeepExecs executors with small grids
@@ -259,14 +259,9 @@ void worker_main(bfs_server* sv) {
                 progress |= step_execs(sv, s, true);
                 continue;
             }
-            // short queue, idle lanes: plain searches on the executors
-            bool to_execs = false;
-            if (!s.running && !s.active && s.copies.empty()) {
-                std::lock_guard<std::mutex> lk(sv->mu);
-                to_execs = s.queue.size() < kLaneBatch;
-            }
-            progress |= step_execs(sv, s, to_execs);
-            if (to_execs) continue;
+            // free executors take queued queries first (plain searches); lanes take the
+            // overflow: new lanes open only when kLaneBatch queries wait or lanes are running
+            progress |= step_execs(sv, s, true);
             // ---------------------------------------------- harvest a finished launch
             if (s.running) {
                 const cudaError_t q = cudaEventQuery(s.ev);
@@ -332,7 +327,8 @@ void worker_main(bfs_server* sv) {
             {
                 std::lock_guard<std::mutex> lk(sv->mu);
                 const size_t row_bytes = sizeof(int32_t) * (size_t)s.g->n;
-                for (int i = 0; i < sv->max_lanes && !s.queue.empty(); i++) {
+                const bool open_lanes = s.active || s.queue.size() >= kLaneBatch || s.execs.empty();
+                for (int i = 0; open_lanes && i < sv->max_lanes && !s.queue.empty(); i++) {
                     Lane& L = s.lanes[i];
                     if (L.busy) continue;
                     if (!L.row) {

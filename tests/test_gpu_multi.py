@@ -105,3 +105,19 @@ def test_multi_hub_first_rows(gpu_lib):
     for mode in (bfs.MODE_DO, bfs.MODE_BU_ONLY):
         lv, _ = _run(bfs, g, roots, opts=bfs.options(mode=mode, bu_rows=bfs.BU_ROWS_HUB_FIRST))
         assert np.array_equal(lv, want), mode
+
+
+def test_multi_deep_levels_past_byte_staging(gpu_lib):
+    """Levels are staged one byte per (lane, vertex) up to depth 253 and written
+    to the int32 rows directly beyond; a 700-vertex path crosses that boundary
+    from several roots at once (min-id parents too)."""
+    bfs = gpu_lib
+    e = graphgen.path(700)
+    ref = oracle.build_csr(e.n, e.src, e.dst)
+    g = bfs.Graph.from_edges(e.src, e.dst, e.n)
+    roots = [0, 350, 699, 1, 698, 200]
+    lv, pa = _run(bfs, g, roots, want_parent=True)
+    for i, r in enumerate(roots):
+        want = oracle.levels(ref, r)
+        assert np.array_equal(lv[i], want), r
+        assert np.array_equal(pa[i], oracle.min_parent(ref, want)), r
