@@ -70,7 +70,9 @@ typedef struct {
 #define BFS_FLAG_BUILD_DCSC    4u  /* also build the column-block DCSC tiles (layout BFS_LAYOUT_DCSC_TILED) */
 #define BFS_FLAG_CHECK_SYMMETRY 8u /* from_csr: verify that the CSR is symmetric (one extra pass) */
 #define BFS_FLAG_BUILD_HUB_FIRST 16u /* also store a copy of every row ordered by neighbour degree, highest
-                                        first, ties by id (bottom-up option BFS_BU_ROWS_HUB_FIRST) */
+                                        first, ties by id (bottom-up option BFS_BU_ROWS_HUB_FIRST), and
+                                        per vertex a 32-byte head (its degree and the first 7 ids of
+                                        that row): 4*nnz + 32*n more device bytes */
 
 /* search direction policy ("Parallel Direction-Optimizing BFS") */
 #define BFS_MODE_DO       0   /* per level: top-down or bottom-up by the alpha/beta rule */

@@ -103,7 +103,7 @@ int32_t or_bfs_bottomup(int64_t n, const int64_t* off, const int32_t* cols, int3
             }
         }
         uint8_t* t = frontier; frontier = next; next = t;   /* frontier <- next */
-        memset(next, 0, (size_t)n);
+        for (int64_t v = 0; v < n; v++) next[v] = 0;
         fsize = nsize;
         d++;
     }

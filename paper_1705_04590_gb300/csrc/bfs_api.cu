@@ -58,6 +58,7 @@ static void destroy_graph(bfs_graph* g) {
     g->mem.release(g->offsets, sizeof(int64_t) * (size_t)(g->n + 1), nullptr);
     g->mem.release(g->cols, sizeof(int32_t) * (size_t)(g->nnz + kColPad), nullptr);
     if (g->cols_hf) g->mem.release(g->cols_hf, sizeof(int32_t) * (size_t)(g->nnz + kColPad), nullptr);
+    if (g->bu_heads) g->mem.release(g->bu_heads, sizeof(int32_t) * 8 * (size_t)g->n, nullptr);
     g->mem.release(g->isolated, sizeof(uint32_t) * (size_t)g->W, nullptr);
     if (g->last_done) cudaEventDestroy(g->last_done);
     delete g;

@@ -95,6 +95,9 @@ struct bfs_graph {
     int32_t* cols = nullptr;        // [nnz + kColPad]
     uint32_t* isolated = nullptr;   // [W] bit v set when deg(v) = 0 or v >= n
     int32_t* cols_hf = nullptr;     // [nnz + kColPad] rows ordered by neighbour degree (BFS_FLAG_BUILD_HUB_FIRST)
+    // [8n] heads of the hub-first rows, one 32-byte record per vertex:
+    // [8u..8u+7] = {deg(u), r0 .. r6} with r the row's first ids (0 past its end)
+    int32_t* bu_heads = nullptr;
     int64_t W = 0;                  // bitmap words
     size_t graph_bytes = 0;
     bfsrt::DeviceAlloc mem;

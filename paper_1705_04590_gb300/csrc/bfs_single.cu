@@ -72,6 +72,9 @@ struct SingleParams {
     const long long* __restrict__ off;
     const int* __restrict__ cols;
     const int* __restrict__ cols_bu;     // rows as the bottom-up steps scan them (cols, or hub-first)
+    // heads of the hub-first rows (null: bottom-up reads offsets and rows):
+    // heads[8u .. 8u+7] = {deg(u), r0 .. r6}, 32-byte aligned
+    const int* __restrict__ heads;
     const unsigned* __restrict__ isolated;
     long long n, nnz, W;
     int* parent;
@@ -131,6 +134,10 @@ static_assert(kWin == 4 || kWin == 8, "window is one or two int4");
 #define BFS_BU_DYN 0     // 1: bottom-up chunks from a counter; 0: round-robin
 #endif
 
+#ifndef BFS_BU_HEADS
+#define BFS_BU_HEADS 1   // 1: bottom-up over hub-first rows starts from the row heads
+#endif
+
 #ifndef BFS_EVICT
 #define BFS_EVICT 1      // 1: bottom-up graph reads marked evict-first in L2
 #endif
@@ -153,6 +160,19 @@ __device__ __forceinline__ int4 ld_stream4(const int4* a) {
     return v;
 #else
     return __ldg(a);
+#endif
+}
+
+// one 32-byte record (a 256-bit load; the address is 32-byte aligned)
+__device__ __forceinline__ void ld_stream8(const int* a, int4& lo, int4& hi) {
+#if BFS_EVICT
+    asm("ld.global.nc.L2::cache_hint.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8], %9;"
+        : "=r"(lo.x), "=r"(lo.y), "=r"(lo.z), "=r"(lo.w), "=r"(hi.x), "=r"(hi.y), "=r"(hi.z), "=r"(hi.w)
+        : "l"(a), "l"(evict_first_policy()));
+#else
+    asm("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=r"(lo.x), "=r"(lo.y), "=r"(lo.z), "=r"(lo.w), "=r"(hi.x), "=r"(hi.y), "=r"(hi.z), "=r"(hi.w)
+        : "l"(a));
 #endif
 }
 
@@ -774,6 +794,103 @@ __device__ void bu_phase_a(const SingleParams& p, int d, const unsigned* fcur, u
     long_flush(lst, longlist, longcnt);
 }
 
+// Bottom-up, phase A over the row heads.  The same warp-per-1024-vertices
+// compaction, but a searcher's first probes need no offsets: round r reads
+// the 32-byte heads of its 32 searchers (consecutive vertices, so the warp's
+// loads are contiguous), probes the first id alone and the other six
+// only on a miss.  Heads are prefetched two rounds ahead.  Searchers with
+// more than kHead neighbours and no hit among the first kHead go on the long
+// list, whose scan resumes at row position kHead.
+constexpr int kHead = 7;
+
+__device__ void bu_phase_a_heads(const SingleParams& p, int d, const unsigned* fcur, unsigned* fnext,
+                                 int* longlist, unsigned long long* longcnt, unsigned long long& acc_n,
+                                 unsigned long long& acc_m, unsigned long long& acc_sc,
+                                 unsigned long long& acc_ex) {
+    __shared__ unsigned s_hnext[kWarps][32];
+    const int lane = lane_id(), wib = threadIdx.x >> 5;
+    const long long nchunk = (p.W + 31) / 32;
+    const int4 z4 = make_int4(0, 0, 0, 0);
+    s_hnext[wib][lane] = 0u;
+    WarpStage lst = warp_stage();
+    __syncwarp();
+    const long long gw = gtid() >> 5, nw = gthreads() >> 5;
+    for (long long ch = gw; ch < nchunk; ch += nw) {
+        const long long w = ch * 32 + lane;
+        const unsigned cw = (w < p.W) ? __ldcg(p.visited + w) : kFull;
+        const unsigned todo = ~cw;
+        const int cnt = __popc(todo);
+        const int incl = warp_inclusive_scan(cnt);
+        const int T = __shfl_sync(kFull, incl, 31);
+        const int excl = incl - cnt;
+        int u0 = bu_locate(lane, T, incl, excl, todo, ch);
+        int4 a0 = z4, b0 = z4;
+        if (u0 >= 0) {
+            ld_stream8(p.heads + 8 * (long long)u0, a0, b0);
+        }
+        int u1 = bu_locate(32 + lane, T, incl, excl, todo, ch);
+        int4 a1 = z4, b1 = z4;
+        if (u1 >= 0) {
+            ld_stream8(p.heads + 8 * (long long)u1, a1, b1);
+        }
+        for (int base = 0; base < T; base += 32) {
+            const int u2 = bu_locate(base + 64 + lane, T, incl, excl, todo, ch);
+            int4 a2 = z4, b2 = z4;
+            if (u2 >= 0) {
+                ld_stream8(p.heads + 8 * (long long)u2, a2, b2);
+            }
+            bool to_long = false;
+            if (u0 >= 0) {
+                const int deg = a0.x;
+                const int ids[kHead] = {a0.y, a0.z, a0.w, b0.x, b0.y, b0.z, b0.w};
+                unsigned hit = 0;
+                if (deg > 0 && in_frontier(fcur, ids[0])) {
+                    hit = 1u;
+                } else {
+#pragma unroll
+                    for (int t = 1; t < kHead; t++)
+                        if (t < deg && in_frontier(fcur, ids[t])) hit |= 1u << t;
+                }
+                acc_sc += 1;
+                if (hit) {
+                    const int t = __ffs(hit) - 1;
+                    acc_ex += (unsigned long long)(t + 1);
+                    acc_m += (unsigned long long)deg;
+                    if (p.parent) p.parent[u0] = ids[t];
+                    set_level(p, u0, d + 1);
+                    atomicOr(&s_hnext[wib][(u0 >> 5) - ch * 32], 1u << (u0 & 31));
+                } else if (deg > kHead) {
+                    to_long = true;       // examinations counted by phase B
+                } else {
+                    acc_ex += (unsigned long long)deg;
+                }
+            }
+            const unsigned lm = __ballot_sync(kFull, to_long);
+            if (lm) {
+                if (to_long) lst.buf[lst.cnt + __popc(lm & lanemask_lt())] = u0;
+                lst.cnt += __popc(lm);
+                if (lst.cnt > kStage - 32) long_flush(lst, longlist, longcnt);
+            }
+            u0 = u1;
+            a0 = a1;
+            b0 = b1;
+            u1 = u2;
+            a1 = a2;
+            b1 = b2;
+        }
+        __syncwarp();
+        const unsigned nx = s_hnext[wib][lane];
+        if (w < p.W) {
+            fnext[w] = nx;
+            if (nx) p.visited[w] = cw | nx;
+        }
+        acc_n += (unsigned long long)__popc(nx);
+        s_hnext[wib][lane] = 0u;
+        __syncwarp();
+    }
+    long_flush(lst, longlist, longcnt);
+}
+
 // Bottom-up, phase B: the long list.  Groups of 4 lanes take one searcher
 // each (8 per warp); a group reads 16 ids per step (one int4 per lane, in row
 // order) and stops at the first frontier neighbour: the lowest lane of the
@@ -782,7 +899,7 @@ __device__ void bu_phase_a(const SingleParams& p, int d, const unsigned* fcur, u
 // atomicOr.
 #if BFS_BU_PHASEB == 2
 __device__ void bu_phase_b(const SingleParams& p, int d, const unsigned* fcur, unsigned* fnext, const int* longlist,
-                           long long nlong, unsigned long long& acc_n, unsigned long long& acc_m,
+                           long long nlong, int skip, unsigned long long& acc_n, unsigned long long& acc_m,
                            unsigned long long& acc_ex) {
     const long long tid = gtid(), nth = gthreads();
     const int4 z4 = make_int4(0, 0, 0, 0);
@@ -790,7 +907,7 @@ __device__ void bu_phase_b(const SingleParams& p, int d, const unsigned* fcur, u
         const int u = __ldcg(longlist + i);
         long long s0, e0;
         row_of(p, u, s0, e0);
-        long long pos = (s0 & ~3LL) + kWin;
+        long long pos = (s0 + skip) & ~3LL;
         long long hitpos = -1;
         int pv = -1;
         while (pos < e0) {
@@ -825,7 +942,7 @@ __device__ void bu_phase_b(const SingleParams& p, int d, const unsigned* fcur, u
 }
 #else
 __device__ void bu_phase_b(const SingleParams& p, int d, const unsigned* fcur, unsigned* fnext, const int* longlist,
-                           long long nlong, unsigned long long& acc_n, unsigned long long& acc_m,
+                           long long nlong, int skip, unsigned long long& acc_n, unsigned long long& acc_m,
                            unsigned long long& acc_ex) {
     const int lane = lane_id(), grp = lane >> 2, gl = lane & 3;
     const long long gw = gtid() >> 5, nw = gthreads() >> 5;
@@ -836,7 +953,7 @@ __device__ void bu_phase_b(const SingleParams& p, int d, const unsigned* fcur, u
         if (i < nlong) {
             u = __ldcg(longlist + i);
             row_of(p, u, s0, e0);
-            pos = (s0 & ~3LL) + kWin + 4 * gl;
+            pos = ((s0 + skip) & ~3LL) + 4 * gl;
         }
         long long hitpos = -1;
         int pv = -1;
@@ -956,7 +1073,10 @@ __global__ void __launch_bounds__(kBlock, BFS_MIN_BLOCKS) bfs_single_kernel(Sing
             }
             unsigned long long an = 0, am = 0, asc = 0, aex = 0;
             int* longlist = qnext;   // the queues are idle during bottom-up levels
-            bu_phase_a(p, d, fcur, fnext, longlist, &c->ntask[snext], &c->chunk[snext], an, am, asc, aex);
+            if (p.heads)
+                bu_phase_a_heads(p, d, fcur, fnext, longlist, &c->ntask[snext], an, am, asc, aex);
+            else
+                bu_phase_a(p, d, fcur, fnext, longlist, &c->ntask[snext], &c->chunk[snext], an, am, asc, aex);
             block_add4(an, am, asc, aex, &c->accn[snext], &c->accm[snext], &c->scanned[snext],
                        &c->examined[snext]);
             if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
@@ -965,7 +1085,7 @@ __global__ void __launch_bounds__(kBlock, BFS_MIN_BLOCKS) bfs_single_kernel(Sing
             if (lead) t_mid = globaltimer_ns();
             if (nlong > 0) {
                 unsigned long long bn = 0, bm = 0, bex = 0;
-                bu_phase_b(p, d, fcur, fnext, longlist, nlong, bn, bm, bex);
+                bu_phase_b(p, d, fcur, fnext, longlist, nlong, p.heads ? kHead : kWin, bn, bm, bex);
                 block_add4(bn, bm, 0, bex, &c->accn[snext], &c->accm[snext], nullptr, &c->examined[snext]);
                 if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
             }
@@ -1377,6 +1497,8 @@ bfs_status single_launch_work(bfs_graph* g, SingleWork& w, const int32_t* roots_
     p.off = reinterpret_cast<const long long*>(g->offsets);
     p.cols = g->cols;
     p.cols_bu = (opt.bu_rows == BFS_BU_ROWS_HUB_FIRST && g->cols_hf) ? g->cols_hf : g->cols;
+    p.heads = (BFS_BU_HEADS && opt.bu_rows == BFS_BU_ROWS_HUB_FIRST && g->cols_hf && g->bu_heads)
+                  ? g->bu_heads : nullptr;
     p.isolated = g->isolated;
     p.n = g->n;
     p.nnz = g->nnz;

@@ -12,6 +12,12 @@
 // Built with one stable radix sort of (row, ~degree(neighbour)) keys carrying
 // the neighbour ids: within a row, equal degrees keep the id order of the
 // input rows.
+//
+// Beside the rows sit their heads: per vertex its degree and the first seven
+// ids of its reordered row, one aligned 32-byte record (one DRAM sector).  A
+// bottom-up sweep reads them in vertex order (one coalesced stream, no offsets
+// lookup in front of a scattered row read) and goes to the full row only for
+// the few searchers whose first seven neighbours are all outside the frontier.
 #include <cub/device/device_radix_sort.cuh>
 
 #include "bfs_internal.h"
@@ -34,11 +40,45 @@ __global__ void k_hub_keys(const long long* __restrict__ off, const int32_t* __r
     }
 }
 
+// heads[2u] = {deg(u), r0, r1, r2}, heads[2u + 1] = {r3, r4, r5, r6}: the first
+// seven ids of u's reordered row, 0 past its end; one thread per vertex
+__global__ void k_hub_heads(const long long* __restrict__ off, const int32_t* __restrict__ cols_hf, long long n,
+                            int4* __restrict__ heads) {
+    const long long nth = (long long)gridDim.x * blockDim.x;
+    for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += nth) {
+        const long long s = off[u], dg = off[u + 1] - s;
+        int r[7];
+#pragma unroll
+        for (int t = 0; t < 7; t++) r[t] = t < dg ? cols_hf[s + t] : 0;
+        heads[2 * u] = make_int4((int)dg, r[0], r[1], r[2]);
+        heads[2 * u + 1] = make_int4(r[3], r[4], r[5], r[6]);
+    }
+}
+
 }  // namespace bfsk_hub
 
 namespace bfsrt {
 
 using namespace bfsk_hub;
+
+static bfs_status build_bu_heads(bfs_graph* g, cudaStream_t s) {
+    const long long n = g->n;
+    const size_t bytes = sizeof(int32_t) * 8 * (size_t)n;
+    g->bu_heads = (int32_t*)g->mem.alloc(bytes, s);
+    if (!g->bu_heads) return fail(BFS_ERR_OOM, "hub-first rows: row heads");
+    const int blocks = std::max(1, std::min<int>(g->sm_count * 8, (int)((n + 255) / 256)));
+    k_hub_heads<<<blocks, 256, 0, s>>>((const long long*)g->offsets, g->cols_hf, n,
+                                       reinterpret_cast<int4*>(g->bu_heads));
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        g->mem.release(g->bu_heads, bytes, s);
+        g->bu_heads = nullptr;
+        return cuda_fail(e, "hub-first rows: row heads");
+    }
+    g->graph_bytes += bytes;
+    return BFS_OK;
+}
 
 bfs_status build_hub_first_rows(bfs_graph* g, cudaStream_t s) {
     if (g->cols_hf) return BFS_OK;
@@ -48,7 +88,7 @@ bfs_status build_hub_first_rows(bfs_graph* g, cudaStream_t s) {
     BFS_CUDA_TRY(cudaMemsetAsync(g->cols_hf + nnz, 0, sizeof(int32_t) * kColPad, s));
     if (nnz == 0) {
         g->graph_bytes += sizeof(int32_t) * (size_t)(nnz + kColPad);
-        return BFS_OK;
+        return build_bu_heads(g, s);
     }
     int end_bit = 32;
     while ((1LL << (end_bit - 32)) < n) end_bit++;
@@ -93,7 +133,7 @@ bfs_status build_hub_first_rows(bfs_graph* g, cudaStream_t s) {
         return cuda_fail(e, "hub-first rows: sort");
     }
     g->graph_bytes += sizeof(int32_t) * (size_t)(nnz + kColPad);
-    return BFS_OK;
+    return build_bu_heads(g, s);
 }
 
 }  // namespace bfsrt
