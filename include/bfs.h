@@ -195,6 +195,17 @@ bfs_status bfs_graph_copy_csr(const bfs_graph* g, int64_t* offsets_out, int32_t*
 bfs_status bfs_graph_copy_hub_first(const bfs_graph* g, int32_t* cols_out, void* stream);
 
 /*
+ * Copy the row heads that BFS_FLAG_BUILD_HUB_FIRST stores beside the hub-first
+ * rows into caller memory (host or device, int32[8n]): record u is
+ * heads_out[8u .. 8u+7] = {deg(u), r0, .., r6}, where r0.. are the first
+ * min(deg(u), 7) ids of u's hub-first row and the rest 0.  Bottom-up steps
+ * over the hub-first rows (Algorithm 2 in that order) probe these ids first.
+ * Synchronises `stream`.  Errors: INVALID (NULL argument, graph built without
+ * the flag), CUDA.
+ */
+bfs_status bfs_graph_copy_row_heads(const bfs_graph* g, int32_t* heads_out, void* stream);
+
+/*
  * Device pointers of the DCSC tiles built with BFS_FLAG_BUILD_DCSC ("Graph
  * Representation": IR row ids, JC ids of non-empty columns, CP column
  * pointers).  Vertices are cut into num_blocks blocks of block_size

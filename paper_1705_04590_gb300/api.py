@@ -165,6 +165,13 @@ class Graph:
         L.check(L.load().bfs_graph_copy_hub_first(self._h, cols.ctypes.data, None), "graph_copy_hub_first")
         return cols[: self.nnz]
 
+    def row_heads_host(self) -> np.ndarray:
+        """The row heads (graph built with hub_first=True) as an (n, 8) host array:
+        row u = [deg(u), first 7 ids of u's hub-first row, 0 past its end]."""
+        heads = np.empty((self.n, 8), np.int32)
+        L.check(L.load().bfs_graph_copy_row_heads(self._h, heads.ctypes.data, None), "graph_copy_row_heads")
+        return heads
+
     def dcsc_layout(self) -> L.DcscLayout:
         d = L.DcscLayout()
         L.check(L.load().bfs_graph_dcsc(self._h, ctypes.byref(d)), "graph_dcsc")

@@ -237,6 +237,15 @@ bfs_status bfs_graph_copy_hub_first(const bfs_graph* g, int32_t* cols_out, void*
     return BFS_OK;
 }
 
+bfs_status bfs_graph_copy_row_heads(const bfs_graph* g, int32_t* heads_out, void* stream) {
+    if (!g || !heads_out) return fail(BFS_ERR_INVALID, "NULL argument");
+    if (!g->bu_heads) return fail(BFS_ERR_INVALID, "graph was built without BFS_FLAG_BUILD_HUB_FIRST");
+    cudaStream_t s = (cudaStream_t)stream;
+    BFS_CUDA_TRY(cudaMemcpyAsync(heads_out, g->bu_heads, sizeof(int32_t) * 8 * (size_t)g->n, cudaMemcpyDefault, s));
+    BFS_CUDA_TRY(cudaStreamSynchronize(s));
+    return BFS_OK;
+}
+
 bfs_status bfs_graph_dcsc(const bfs_graph* g, bfs_dcsc_layout* out) {
     if (!g || !out) return fail(BFS_ERR_INVALID, "NULL argument");
     if (!g->dcsc.built) return fail(BFS_ERR_INVALID, "graph was built without BFS_FLAG_BUILD_DCSC");

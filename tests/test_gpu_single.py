@@ -168,7 +168,8 @@ def test_path_bottom_up_only_same_level_discovery(gpu_lib):
 
 def test_hub_first_rows_and_searches(gpu_lib):
     """BFS_FLAG_BUILD_HUB_FIRST: the device's reordered rows equal the oracle's
-    hub_first() bit for bit; searches scanning them bottom-up give exact levels,
+    hub_first() bit for bit, and so do the row heads (degree + first 7 ids of each
+    reordered row); searches scanning them bottom-up give exact levels,
     valid parents, and per-level counters equal to the oracle's schedule over the
     hub-first rows; the option is refused where it cannot apply."""
     bfs = gpu_lib
@@ -180,6 +181,14 @@ def test_hub_first_rows_and_searches(gpu_lib):
         g = bfs.Graph.from_edges(e.src, e.dst, e.n, hub_first=True)
         h = oracle.hub_first(case.ref)
         assert np.array_equal(g.hub_first_host(), h.cols), e.name
+        # row heads: [deg(u), the first min(deg, 7) ids of u's hub-first row, 0 after them]
+        deg = np.diff(case.ref.offsets)
+        want = np.zeros((e.n, 8), np.int32)
+        want[:, 0] = deg
+        for t in range(7):
+            has = deg > t
+            want[has, 1 + t] = h.cols[case.ref.offsets[:-1][has] + t]
+        assert np.array_equal(g.row_heads_host(), want), e.name
         case.g.close()
         case.g = g
         deg = np.diff(case.ref.offsets)
@@ -199,6 +208,9 @@ def test_hub_first_rows_and_searches(gpu_lib):
     with pytest.raises(bfs.BfsError) as ex:
         plain.run(0, bfs.options(bu_rows=bfs.BU_ROWS_HUB_FIRST))
     assert ex.value.status == 7          # BFS_ERR_UNSUPPORTED: graph built without the flag
+    with pytest.raises(bfs.BfsError) as ex:
+        plain.g.row_heads_host()
+    assert ex.value.status == 1          # BFS_ERR_INVALID: no row heads without the flag
     g = bfs.Graph.from_edges(plain.e.src, plain.e.dst, plain.e.n, hub_first=True)
     with pytest.raises(bfs.BfsError) as ex:
         g.run(0, parent=plain.parent, opts=bfs.options(bu_rows=bfs.BU_ROWS_HUB_FIRST,
