@@ -631,6 +631,17 @@ __device__ void bitmap_to_queue(const SingleParams& p, unsigned* f, unsigned* ot
 
 // ------------------------------------------------------------------ bottom-up
 
+// ids[t] for a run-time t (0 <= t < N) as a chain of selects: indexing the
+// array at run time would move the whole window to the stack every round
+template <int N>
+__device__ __forceinline__ int pick(const int (&ids)[N], int t) {
+    int v = ids[0];
+#pragma unroll
+    for (int i = 1; i < N; i++)
+        if (t == i) v = ids[i];
+    return v;
+}
+
 __device__ __forceinline__ bool in_frontier(const unsigned* f, int v) {
     return (__ldcg(f + (v >> 5)) >> (v & 31)) & 1u;
 }
@@ -754,7 +765,7 @@ __device__ void bu_phase_a(const SingleParams& p, int d, const unsigned* fcur, u
                     const int t = __ffs(hb) - 1;
                     acc_ex += (unsigned long long)(rb + t - s0 + 1);
                     acc_m += (unsigned long long)(e0 - s0);
-                    if (p.parent) p.parent[u0] = ids[t];
+                    if (p.parent) p.parent[u0] = pick(ids, t);
                     set_level(p, u0, d + 1);
                     atomicOr(&s_next[wib][(u0 >> 5) - ch * 32], 1u << (u0 & 31));
                 } else if (rb + kWin < e0) {
@@ -856,7 +867,7 @@ __device__ void bu_phase_a_heads(const SingleParams& p, int d, const unsigned* f
                     const int t = __ffs(hit) - 1;
                     acc_ex += (unsigned long long)(t + 1);
                     acc_m += (unsigned long long)deg;
-                    if (p.parent) p.parent[u0] = ids[t];
+                    if (p.parent) p.parent[u0] = pick(ids, t);
                     set_level(p, u0, d + 1);
                     atomicOr(&s_hnext[wib][(u0 >> 5) - ch * 32], 1u << (u0 & 31));
                 } else if (deg > kHead) {
@@ -922,7 +933,7 @@ __device__ void bu_phase_b(const SingleParams& p, int d, const unsigned* fcur, u
             if (hb) {
                 const int t = __ffs(hb) - 1;
                 hitpos = pos + t;
-                pv = ids[t];
+                pv = pick(ids, t);
                 break;
             }
             pos += 8;
