@@ -93,7 +93,9 @@ class Graph:
     def from_edges(cls, src, dst, n: int, dcsc: bool = False, stream=None, torch_allocator: bool = True,
                    hub_first: bool = False) -> "Graph":
         """src/dst: numpy int32 arrays (host) or int32 CUDA tensors (device).  hub_first also
-        stores rows ordered by neighbour degree (bottom-up option bu_rows=BU_ROWS_HUB_FIRST)."""
+        stores rows ordered by neighbour degree and a 32-byte head per vertex (its degree and
+        first 7 reordered ids), 4*nnz + 32*n more device bytes, for bottom-up option
+        bu_rows=BU_ROWS_HUB_FIRST."""
         lib = L.load()
         torch = _torch()
         flags = L.FLAG_SYMMETRIZE | (L.FLAG_BUILD_DCSC if dcsc else 0) | (L.FLAG_BUILD_HUB_FIRST if hub_first else 0)
@@ -121,6 +123,9 @@ class Graph:
     @classmethod
     def from_csr(cls, offsets, cols, n: int, check_symmetry: bool = False, dcsc: bool = False, stream=None,
                  torch_allocator: bool = True, hub_first: bool = False) -> "Graph":
+        """offsets (int64, n+1) / cols (int32): a symmetric CSR on the host (numpy) or the
+        device (CUDA tensors); check_symmetry verifies it in one extra pass.  dcsc and
+        hub_first as in from_edges."""
         lib = L.load()
         torch = _torch()
         flags = (L.FLAG_CHECK_SYMMETRY if check_symmetry else 0) | (L.FLAG_BUILD_DCSC if dcsc else 0) | \
