@@ -120,7 +120,8 @@ void bfs_options_default(bfs_options* opt);
 /* One record per level of a search (device counters copied back). */
 typedef struct {
     int32_t dir;          /* 0 top-down, 1 bottom-up */
-    int32_t reserved;
+    int32_t misses;       /* bottom-up over the hub-first rows: searchers whose first neighbour was not
+                             in the frontier and that have more neighbours (0 otherwise) */
     int64_t nf;           /* frontier size at the start of the level */
     int64_t mf;           /* sum of degrees over the frontier */
     int64_t nnext;        /* vertices discovered by the level */
@@ -129,7 +130,8 @@ typedef struct {
     int64_t examined;     /* top-down: m_f; bottom-up: sum over searching vertices of the 1-based
                              position of the first frontier neighbour in sorted order, or the degree */
     int64_t t_ns;         /* device time from the end of initialisation to the end of this level */
-    int64_t aux;          /* top-down: edge-chunk tasks; bottom-up: searchers continued past their first window */
+    int64_t aux;          /* top-down: edge-chunk tasks; bottom-up: searchers continued past their first
+                             window (id-ordered rows) or row head (hub-first rows): the long list */
     int64_t t_mid_ns;     /* device time at the level's first internal barrier (0 if none) */
 } bfs_level_record;
 
@@ -204,6 +206,21 @@ bfs_status bfs_graph_copy_hub_first(const bfs_graph* g, int32_t* cols_out, void*
  * the flag), CUDA.
  */
 bfs_status bfs_graph_copy_row_heads(const bfs_graph* g, int32_t* heads_out, void* stream);
+
+/*
+ * Copy two per-vertex planes into caller memory (host or device); either
+ * pointer may be NULL to skip it.
+ *   first_out (int32[n], needs BFS_FLAG_BUILD_HUB_FIRST): bits 0-30 the first
+ *     id of each vertex's hub-first row, bit 31 set when the vertex has two or
+ *     more neighbours; 0 for a vertex of degree 0.  Algorithm 2 probes this
+ *     neighbour first (on R-MAT graphs it is the hit for most searchers), and a
+ *     bottom-up sweep streams this plane in vertex order.
+ *   deg8_out (uint8[n], every graph): min(deg(v), 255), read by top-down steps
+ *     for the degree sum of the next frontier.
+ * Synchronises `stream`.  Errors: INVALID (NULL graph, first_out on a graph
+ * built without the flag), CUDA.
+ */
+bfs_status bfs_graph_copy_bu_planes(const bfs_graph* g, int32_t* first_out, uint8_t* deg8_out, void* stream);
 
 /*
  * Device pointers of the DCSC tiles built with BFS_FLAG_BUILD_DCSC ("Graph
@@ -289,20 +306,26 @@ bfs_status bfs_run_multi(bfs_graph* g, const int32_t* roots_host, int32_t k, int
  * no counterpart; this is the direction-optimizing search of bfs_run with
  * default options over a caller-provided CSR, with every work buffer in one
  * fixed device array of about 14 MB compiled into the library.
- *   row_offsets: device int64[n+1]; col_ids: device int32[nnz] holding an
- *   undirected graph as bfs_graph_create_from_csr accepts it (rows strictly
- *   ascending, no self-loops, symmetric), readable for 32 entries past nnz
- *   (16-byte loads may run up to 28 bytes beyond the last row; those values
- *   are ignored).  parent_dev / level_dev: device int32[n], either may be
+ *   row_offsets: device int64[n+1], 8-byte aligned; col_ids: device
+ *   int32[nnz], 16-byte aligned, holding an undirected graph as
+ *   bfs_graph_create_from_csr accepts it (rows strictly ascending, no
+ *   self-loops, symmetric), readable for 32 entries past nnz (16-byte loads
+ *   may run up to 28 bytes beyond the last row; those values are ignored).
+ *   parent_dev / level_dev: device int32[n], 4-byte aligned, either may be
  *   NULL.  Limits: 1 <= n <= 1,048,576 and nnz <= 16,777,216, else
- *   BFS_ERR_INVALID with a message naming the limit.
+ *   BFS_ERR_INVALID with a message naming the limit; a misaligned pointer
+ *   also gives BFS_ERR_INVALID (checked on the host, nothing is launched).
  * Calls no cudaMalloc, cudaFree or allocating routine.  The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress, once per
  * device, with that device current); make that first call before any stream
  * capture.  Every call shares the array: calls whose work overlaps on the GPU
  * (on different streams) race and must be ordered by the caller.  Each call
  * re-initialises all of it that it reads.  Asynchronous on `stream`; no device
- * error is reported back (use bfs_run for that).
+ * error is reported back: a search whose grid-barrier wait ran out of time
+ * (10 s) leaves parent/level partly written with no status.  A caller that
+ * needs to know must check the outputs itself (level[root] == 0, and every
+ * reached v has level[parent[v]] == level[v] - 1) or use bfs_run, which
+ * returns BFS_ERR_TIMEOUT.
  */
 bfs_status bfs_run_csr_noalloc(const int64_t* row_offsets, const int32_t* col_ids, int64_t n, int64_t nnz,
                                int32_t root, int32_t* parent_dev, int32_t* level_dev, void* stream);

@@ -33,7 +33,7 @@ class Options(ctypes.Structure):
 
 
 class LevelRecord(ctypes.Structure):
-    _fields_ = [("dir", c_i32), ("reserved", c_i32), ("nf", c_i64), ("mf", c_i64), ("nnext", c_i64),
+    _fields_ = [("dir", c_i32), ("misses", c_i32), ("nf", c_i64), ("mf", c_i64), ("nnext", c_i64),
                 ("mnext", c_i64), ("scanned", c_i64), ("examined", c_i64), ("t_ns", c_i64), ("aux", c_i64),
                 ("t_mid_ns", c_i64)]
 
@@ -60,6 +60,7 @@ SIGNATURES = [
     ("bfs_graph_copy_csr", c_i32, [c_vp, c_vp, c_vp, c_vp]),
     ("bfs_graph_copy_hub_first", c_i32, [c_vp, c_vp, c_vp]),
     ("bfs_graph_copy_row_heads", c_i32, [c_vp, c_vp, c_vp]),
+    ("bfs_graph_copy_bu_planes", c_i32, [c_vp, c_vp, c_vp, c_vp]),
     ("bfs_graph_dcsc", c_i32, [c_vp, ctypes.POINTER(DcscLayout)]),
     ("bfs_graph_copy_dcsc", c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     ("bfs_graph_destroy", None, [c_vp]),

@@ -177,6 +177,16 @@ class Graph:
         L.check(L.load().bfs_graph_copy_row_heads(self._h, heads.ctypes.data, None), "graph_copy_row_heads")
         return heads
 
+    def bu_planes_host(self, first: bool = True):
+        """(first, deg8): per vertex the first id of its hub-first row with bit 31 set when
+        it has two or more neighbours (int32[n]; graph built with hub_first=True; None
+        when first=False) and min(deg, 255) (uint8[n])."""
+        f = np.empty(self.n, np.int32) if first else None
+        d8 = np.empty(self.n, np.uint8)
+        L.check(L.load().bfs_graph_copy_bu_planes(self._h, f.ctypes.data if first else None, d8.ctypes.data, None),
+                "graph_copy_bu_planes")
+        return f, d8
+
     def dcsc_layout(self) -> L.DcscLayout:
         d = L.DcscLayout()
         L.check(L.load().bfs_graph_dcsc(self._h, ctypes.byref(d)), "graph_dcsc")
@@ -250,9 +260,9 @@ class Graph:
             return None
         s, recs, cap = holder
         nrec = min(s.num_levels, cap)
-        rows = [(r.dir, r.nf, r.mf, r.nnext, r.mnext, r.scanned, r.examined, r.t_ns, r.aux, r.t_mid_ns)
+        rows = [(r.dir, r.nf, r.mf, r.nnext, r.mnext, r.scanned, r.examined, r.t_ns, r.aux, r.t_mid_ns, r.misses)
                 for r in recs[:nrec]]
-        arr = np.array(rows, dtype=np.int64).reshape(-1, 10)
+        arr = np.array(rows, dtype=np.int64).reshape(-1, 11)
         return {"num_levels": s.num_levels, "reached": s.vertices_reached, "edges_examined": s.edges_examined,
                 "records": arr}
 

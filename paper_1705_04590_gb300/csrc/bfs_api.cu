@@ -59,6 +59,8 @@ static void destroy_graph(bfs_graph* g) {
     g->mem.release(g->cols, sizeof(int32_t) * (size_t)(g->nnz + kColPad), nullptr);
     if (g->cols_hf) g->mem.release(g->cols_hf, sizeof(int32_t) * (size_t)(g->nnz + kColPad), nullptr);
     if (g->bu_heads) g->mem.release(g->bu_heads, sizeof(int32_t) * 8 * (size_t)g->n, nullptr);
+    if (g->bu_first) g->mem.release(g->bu_first, sizeof(int32_t) * (size_t)(g->n + 32), nullptr);
+    if (g->deg8) g->mem.release(g->deg8, (size_t)g->n + 32, nullptr);
     g->mem.release(g->isolated, sizeof(uint32_t) * (size_t)g->W, nullptr);
     if (g->last_done) cudaEventDestroy(g->last_done);
     delete g;
@@ -242,6 +244,18 @@ bfs_status bfs_graph_copy_row_heads(const bfs_graph* g, int32_t* heads_out, void
     if (!g->bu_heads) return fail(BFS_ERR_INVALID, "graph was built without BFS_FLAG_BUILD_HUB_FIRST");
     cudaStream_t s = (cudaStream_t)stream;
     BFS_CUDA_TRY(cudaMemcpyAsync(heads_out, g->bu_heads, sizeof(int32_t) * 8 * (size_t)g->n, cudaMemcpyDefault, s));
+    BFS_CUDA_TRY(cudaStreamSynchronize(s));
+    return BFS_OK;
+}
+
+bfs_status bfs_graph_copy_bu_planes(const bfs_graph* g, int32_t* first_out, uint8_t* deg8_out, void* stream) {
+    if (!g) return fail(BFS_ERR_INVALID, "NULL graph");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (first_out) {
+        if (!g->bu_first) return fail(BFS_ERR_INVALID, "graph was built without BFS_FLAG_BUILD_HUB_FIRST");
+        BFS_CUDA_TRY(cudaMemcpyAsync(first_out, g->bu_first, sizeof(int32_t) * (size_t)g->n, cudaMemcpyDefault, s));
+    }
+    if (deg8_out) BFS_CUDA_TRY(cudaMemcpyAsync(deg8_out, g->deg8, (size_t)g->n, cudaMemcpyDefault, s));
     BFS_CUDA_TRY(cudaStreamSynchronize(s));
     return BFS_OK;
 }

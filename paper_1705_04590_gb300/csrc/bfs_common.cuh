@@ -45,7 +45,7 @@ struct Ctrl {
     unsigned long long scanned[3];   // bottom-up searchers of the level producing frontier `slot`
     unsigned long long examined[3];  // serial early-exit examinations of that level
     unsigned long long ntask[3];     // top-down edge-chunk tasks of that level
-    unsigned long long chunk[3];     // bottom-up work distribution: next 1024-vertex chunk
+    unsigned long long nmiss[3];     // bottom-up searchers whose first probe missed (miss-list length)
     long long num_levels;
     long long reached;
 };

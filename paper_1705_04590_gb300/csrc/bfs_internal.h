@@ -41,6 +41,7 @@ struct SingleWork {
     int* queue0 = nullptr;         // [n]
     int* queue1 = nullptr;         // [n]
     unsigned char* lv8 = nullptr;  // [W * 32] staged levels (one byte per vertex, whole words)
+    unsigned* pfirst = nullptr;    // [W] bit v: v's parent is its first hub-first neighbour (bu_first[v])
     int* level_scratch = nullptr;  // [n] levels for MIN_ID parents when the caller wants none (lazy)
     void* tasks = nullptr;         // top-down edge-chunk descriptors
     long long task_cap = 0;
@@ -98,6 +99,9 @@ struct bfs_graph {
     // [8n] heads of the hub-first rows, one 32-byte record per vertex:
     // [8u..8u+7] = {deg(u), r0 .. r6} with r the row's first ids (0 past its end)
     int32_t* bu_heads = nullptr;
+    // [n + 32] first id of each hub-first row (0 for degree 0), built with the heads
+    int32_t* bu_first = nullptr;
+    uint8_t* deg8 = nullptr;        // [n + 32] min(deg(v), 255)
     int64_t W = 0;                  // bitmap words
     size_t graph_bytes = 0;
     bfsrt::DeviceAlloc mem;

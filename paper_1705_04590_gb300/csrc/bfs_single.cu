@@ -53,9 +53,6 @@ constexpr long long kPrefetchNf = 1 << 16;   // top-down levels below this prefe
 #ifndef BFS_TD_CHECK
 #define BFS_TD_CHECK 0   // 1: top-down gather reads the visited word before claiming (hub chunks always do)
 #endif
-#ifndef BFS_BU_PHASEB
-#define BFS_BU_PHASEB 1   // bottom-up long list: 1 = 4-lane groups, 2 = one thread per searcher
-#endif
 #ifndef BFS_MIN_BLOCKS
 #define BFS_MIN_BLOCKS 2
 #endif
@@ -72,17 +69,26 @@ struct SingleParams {
     const long long* __restrict__ off;
     const int* __restrict__ cols;
     const int* __restrict__ cols_bu;     // rows as the bottom-up steps scan them (cols, or hub-first)
-    // heads of the hub-first rows (null: bottom-up reads offsets and rows):
-    // heads[8u .. 8u+7] = {deg(u), r0 .. r6}, 32-byte aligned
+    // heads of the hub-first rows: heads[8u .. 8u+7] = {deg(u), r0 .. r6}, 32-byte aligned
     const int* __restrict__ heads;
+    // first[u] = r0 | (deg(u) >= 2) << 31: the first id of u's hub-first row and
+    // whether the row goes on (null: bottom-up scans the rows from their
+    // offsets); a bottom-up level over the hub-first rows streams it in vertex
+    // order
+    const int* __restrict__ first;
+    const unsigned char* __restrict__ deg8;   // min(deg(u), 255); null: degrees from the offsets
     const unsigned* __restrict__ isolated;
     long long n, nnz, W;
     int* parent;
     int* level;
     // level staging: one byte per vertex during the search (kLvUnseen / depth /
-    // kLvDeep), expanded into `level` after the last level; null = write `level`
-    // directly
+    // kLvDeep); after the last level a final pass writes `level` and `parent` in
+    // whole sectors from it.  null = write `level` and `parent` directly over a
+    // -1 fill
     unsigned char* lv8;
+    // with lv8: bit v set when v's parent is first[v] (a bottom-up hit on the
+    // first probe), so that no parent store is made for it during the search
+    unsigned* pfirst;
     unsigned* visited;
     unsigned* front0;
     unsigned* front1;
@@ -130,14 +136,6 @@ __device__ __forceinline__ int decide_dir(const SingleParams& p, int prev, long 
 constexpr int kWin = BFS_BU_WIN;
 static_assert(kWin == 4 || kWin == 8, "window is one or two int4");
 
-#ifndef BFS_BU_DYN
-#define BFS_BU_DYN 0     // 1: bottom-up chunks from a counter; 0: round-robin
-#endif
-
-#ifndef BFS_BU_HEADS
-#define BFS_BU_HEADS 1   // 1: bottom-up over hub-first rows starts from the row heads
-#endif
-
 #ifndef BFS_EVICT
 #define BFS_EVICT 1      // 1: bottom-up graph reads marked evict-first in L2
 #endif
@@ -176,6 +174,38 @@ __device__ __forceinline__ void ld_stream8(const int* a, int4& lo, int4& hi) {
 #endif
 }
 
+__device__ __forceinline__ int ld_stream32(const int* a) {
+#if BFS_EVICT
+    int v;
+    asm("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(evict_first_policy()));
+    return v;
+#else
+    return __ldg(a);
+#endif
+}
+
+__device__ __forceinline__ unsigned ld_stream_u8(const unsigned char* a) {
+#if BFS_EVICT
+    unsigned short v;
+    asm("ld.global.nc.L2::cache_hint.u8 %0, [%1], %2;" : "=h"(v) : "l"(a), "l"(evict_first_policy()));
+    return v;
+#else
+    return __ldg(a);
+#endif
+}
+
+// Bring a 128-byte line into L2 ahead of its use, marked evict-first like the
+// streamed loads that will read it.
+__device__ __forceinline__ void prefetch_l2_line(const void* a) {
+#if BFS_EVICT
+    asm volatile("cp.async.bulk.prefetch.L2.global.L2::cache_hint [%0], 128, %1;" ::"l"(a),
+                 "l"(evict_first_policy())
+                 : "memory");
+#else
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], 128;" ::"l"(a) : "memory");
+#endif
+}
+
 __device__ __forceinline__ long long ld_stream64(const long long* a) {
 #if BFS_EVICT
     long long v;
@@ -203,11 +233,15 @@ __device__ __forceinline__ long long deg_of(const SingleParams& p, int u) {
     return e - s;
 }
 
+// deg(u) given its byte d8 = min(deg(u), 255): the offsets only for 255
+__device__ __forceinline__ long long deg_from8(const SingleParams& p, int u, unsigned d8) {
+    return d8 < 255u ? (long long)d8 : deg_of(p, u);
+}
+
 constexpr unsigned char kLvUnseen = 255;   // not reached (yet)
 constexpr unsigned char kLvDeep = 254;     // depth >= 254: the int32 level holds it
 
 __device__ __forceinline__ void set_level(const SingleParams& p, int v, int lev) {
-    if (!p.level) return;
     if (p.lv8) {
         if (lev < kLvDeep) {
             p.lv8[v] = (unsigned char)lev;
@@ -215,7 +249,7 @@ __device__ __forceinline__ void set_level(const SingleParams& p, int v, int lev)
         }
         p.lv8[v] = kLvDeep;
     }
-    p.level[v] = lev;
+    if (p.level) p.level[v] = lev;
 }
 
 // level of u as far as the search has got (-1 = not reached), for readers inside the launch
@@ -257,44 +291,82 @@ __device__ void fill_bytes(unsigned char* a, long long n, unsigned char b) {
     for (long long i = body * 16 + tid; i < n; i += nth) a[i] = b;
 }
 
-// After the last level: level[v] from the staged bytes, whole sectors at a
-// time (vertices at depth >= 254 already hold their int32 level).
-__device__ __forceinline__ int lv_decode(unsigned b) { return b == kLvUnseen ? -1 : (int)b; }
-
-__device__ void expand_levels(const SingleParams& p) {
+// After the last level: the outputs in whole sectors, 8 vertices (one 32-byte
+// sector of each output) per thread.  level[v] = the staged byte (kLvUnseen ->
+// -1); vertices at depth >= 254 already hold their int32 level and are left
+// alone.  parent[v] = -1 when v was not reached, first[v] when its pfirst bit is
+// set (found bottom-up on its first probe), else the value written during the
+// search (the root, a top-down claim, a later bottom-up probe), read back so
+// that the sector is still written whole: a partial-sector store costs a read
+// of the sector from DRAM anyway.
+__device__ void materialise(const SingleParams& p) {
     const long long tid = gtid(), nth = gthreads();
-    if (((unsigned long long)p.level & 15) == 0) {
-        const long long groups = p.n / 16;
-        for (long long i = tid; i < groups; i += nth) {
-            const uint4 b = __ldcg(reinterpret_cast<const uint4*>(p.lv8) + i);
-            const unsigned w[4] = {b.x, b.y, b.z, b.w};
+    const long long groups = (p.n + 7) / 8;
+    const bool lvec = p.level && (((unsigned long long)p.level & 15) == 0);
+    const bool pvec = p.parent && (((unsigned long long)p.parent & 15) == 0);
+    for (long long gi = tid; gi < groups; gi += nth) {
+        const long long v0 = gi * 8;
+        const bool full = v0 + 8 <= p.n;
+        const unsigned valid = full ? 0xFFu : ((1u << (unsigned)(p.n - v0)) - 1u);
+        const uint2 lb = __ldcg(reinterpret_cast<const uint2*>(p.lv8 + v0));
+        unsigned reached = 0, deep = 0;
+        int lv[8];
 #pragma unroll
-            for (int q = 0; q < 4; q++) {
-                const unsigned x = w[q];
-                const long long v0 = i * 16 + q * 4;
-                int o[4];
+        for (int k = 0; k < 8; k++) {
+            const unsigned b = ((k < 4 ? lb.x : lb.y) >> (8 * (k & 3))) & 0xFFu;
+            lv[k] = b == kLvUnseen ? -1 : (int)b;
+            if (b != kLvUnseen) reached |= 1u << k;
+            if (b == kLvDeep) deep |= 1u << k;
+        }
+        reached &= valid;
+        if (p.level) {
+            if (lvec && full && !deep) {
+                int4* o = reinterpret_cast<int4*>(p.level + v0);
+                o[0] = make_int4(lv[0], lv[1], lv[2], lv[3]);
+                o[1] = make_int4(lv[4], lv[5], lv[6], lv[7]);
+            } else {
 #pragma unroll
-                for (int k = 0; k < 4; k++) o[k] = lv_decode((x >> (8 * k)) & 0xFFu);
-                bool deep = false;
-#pragma unroll
-                for (int k = 0; k < 4; k++) deep |= ((x >> (8 * k)) & 0xFFu) == kLvDeep;
-                if (!deep) {
-                    reinterpret_cast<int4*>(p.level + v0)[0] = make_int4(o[0], o[1], o[2], o[3]);
-                } else {
-#pragma unroll
-                    for (int k = 0; k < 4; k++)
-                        if (((x >> (8 * k)) & 0xFFu) != kLvDeep) p.level[v0 + k] = o[k];
-                }
+                for (int k = 0; k < 8; k++)
+                    if (((valid & ~deep) >> k) & 1u) p.level[v0 + k] = lv[k];
             }
         }
-        for (long long v = groups * 16 + tid; v < p.n; v += nth) {
-            const unsigned b = __ldcg(p.lv8 + v);
-            if (b != kLvDeep) p.level[v] = lv_decode(b);
-        }
-    } else {
-        for (long long v = tid; v < p.n; v += nth) {
-            const unsigned b = __ldcg(p.lv8 + v);
-            if (b != kLvDeep) p.level[v] = lv_decode(b);
+        if (p.parent) {
+            const unsigned pf = p.pfirst ? ((__ldcg(p.pfirst + (v0 >> 5)) >> (v0 & 31)) & reached) : 0u;
+            const unsigned direct = reached & ~pf;
+            int f[8], q[8];
+#pragma unroll
+            for (int k = 0; k < 8; k++) f[k] = q[k] = -1;
+            if (pf) {
+                const int4 a = ld_stream4(reinterpret_cast<const int4*>(p.first + v0));
+                const int4 b = ld_stream4(reinterpret_cast<const int4*>(p.first + v0) + 1);
+                const int m = 0x7FFFFFFF;   // bit 31 flags a row that goes on
+                f[0] = a.x & m; f[1] = a.y & m; f[2] = a.z & m; f[3] = a.w & m;
+                f[4] = b.x & m; f[5] = b.y & m; f[6] = b.z & m; f[7] = b.w & m;
+            }
+            if (direct) {
+                if (pvec && full) {
+                    const int4 a = __ldcg(reinterpret_cast<const int4*>(p.parent + v0));
+                    const int4 b = __ldcg(reinterpret_cast<const int4*>(p.parent + v0) + 1);
+                    q[0] = a.x; q[1] = a.y; q[2] = a.z; q[3] = a.w;
+                    q[4] = b.x; q[5] = b.y; q[6] = b.z; q[7] = b.w;
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 8; k++)
+                        if ((direct >> k) & 1u) q[k] = __ldcg(p.parent + v0 + k);
+                }
+            }
+            int o[8];
+#pragma unroll
+            for (int k = 0; k < 8; k++) o[k] = !((reached >> k) & 1u) ? -1 : ((pf >> k) & 1u) ? f[k] : q[k];
+            if (pvec && full) {
+                int4* po = reinterpret_cast<int4*>(p.parent + v0);
+                po[0] = make_int4(o[0], o[1], o[2], o[3]);
+                po[1] = make_int4(o[4], o[5], o[6], o[7]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 8; k++)
+                    if ((valid >> k) & 1u) p.parent[v0 + k] = o[k];
+            }
         }
     }
 }
@@ -303,9 +375,13 @@ __device__ void init_phase(const SingleParams& p) {
     const long long tid = gtid(), nth = gthreads();
     const bool single = p.nroots == 1;
     const long long r = p.root0;
-    if (p.parent) fill_minus_one(p.parent, p.n);
-    if (p.level && p.lv8) fill_bytes(p.lv8, p.n, kLvUnseen);
-    else if (p.level) fill_minus_one(p.level, p.n);
+    if (p.lv8) {
+        // the outputs are written once, by the final pass
+        fill_bytes(p.lv8, p.n, kLvUnseen);
+    } else {
+        if (p.parent) fill_minus_one(p.parent, p.n);
+        if (p.level) fill_minus_one(p.level, p.n);
+    }
     const long long rw = single ? (r >> 5) : -1;
     const unsigned rb = single ? (1u << (r & 31)) : 0u;
     for (long long w = tid; w < p.W; w += nth) {
@@ -314,6 +390,7 @@ __device__ void init_phase(const SingleParams& p) {
         p.visited[w] = x;
         p.front0[w] = 0u;
         p.front1[w] = 0u;
+        if (p.pfirst) p.pfirst[w] = 0u;
     }
     if (single && tid == 0) {
         p.queue0[0] = (int)r;
@@ -348,6 +425,20 @@ struct WarpStage {
     bool pf;    // prefetch the rows of flushed vertices into L2 (small levels)
 };
 
+// Degree of a vertex just appended to the next queue, into acc_m.  On small
+// levels the next level is latency-bound: start its column reads now.
+__device__ __forceinline__ void flush_degree(const SingleParams& p, int v, bool pf, unsigned long long& acc_m) {
+    const unsigned d8 = p.deg8 ? (unsigned)__ldg(p.deg8 + v) : 255u;
+    if (d8 < 255u && !pf) {
+        acc_m += d8;
+        return;
+    }
+    long long rs, re;
+    row_of(p, v, rs, re);
+    acc_m += (unsigned long long)(re - rs);
+    if (pf && re > rs) asm volatile("prefetch.global.L2 [%0];" ::"l"(p.cols + rs));
+}
+
 __device__ __forceinline__ void stage_flush(const SingleParams& p, WarpStage& st, int* qnext,
                                             unsigned long long* tail, unsigned long long& acc_m) {
     if (st.cnt == 0) return;
@@ -360,12 +451,7 @@ __device__ __forceinline__ void stage_flush(const SingleParams& p, WarpStage& st
         qnext[base + i] = v;
         // degree sum of the next frontier (the switch rule's m_f), read here in
         // batches rather than on the claim path
-        long long rs, re;
-        row_of(p, v, rs, re);
-        acc_m += (unsigned long long)(re - rs);
-        // on small levels the next level is latency-bound: start its column
-        // reads now (its offsets are now in L2 as well)
-        if (st.pf && re > rs) asm volatile("prefetch.global.L2 [%0];" ::"l"(p.cols + rs));
+        flush_degree(p, v, st.pf, acc_m);
     }
     __syncwarp();
     st.cnt = 0;
@@ -396,10 +482,7 @@ __device__ void block_flush(const SingleParams& p, WarpStage& st, int* qnext, un
     for (int i = lane; i < st.cnt; i += 32) {
         const int v = st.buf[i];
         qnext[base + i] = v;
-        long long rs, re;
-        row_of(p, v, rs, re);
-        acc_m += (unsigned long long)(re - rs);
-        if (st.pf && re > rs) asm volatile("prefetch.global.L2 [%0];" ::"l"(p.cols + rs));
+        flush_degree(p, v, st.pf, acc_m);
     }
     __syncwarp();
     st.cnt = 0;
@@ -559,17 +642,23 @@ __device__ void task_phase(const SingleParams& p, int d, long long ntask, int* q
     block_flush(p, st, qnext, tail, acc_m);
 }
 
-// parent_mode MIN_ID after a top-down level: each newly found v takes the
-// smallest neighbour on level d (rows are sorted, so the first one found).
-__device__ void td_min_parent(const SingleParams& p, int d, const int* qnext, long long nn) {
+// parent_mode MIN_ID, after the last level: every reached v other than a root
+// takes the smallest neighbour one level closer, min{u in adj(v) : level(u) =
+// level(v) - 1} (the (select2nd, min) semiring of the top-down local discovery;
+// rows are sorted, so the first such u in the row).  Bottom-up levels over the
+// id-ordered rows already found exactly that parent; top-down claims did not.
+// One pass after the loop instead of one per top-down level keeps the level
+// loop's register budget free of it.
+__device__ void min_parent_pass(const SingleParams& p) {
     const long long tid = gtid(), nth = gthreads();
-    for (long long i = tid; i < nn; i += nth) {
-        const int v = __ldcg(qnext + i);
+    for (long long v = tid; v < p.n; v += nth) {
+        const int lv = get_level(p, (int)v);
+        if (lv <= 0) continue;
         long long s, e;
-        row_of(p, v, s, e);
+        row_of(p, (int)v, s, e);
         for (long long k = s; k < e; k++) {
             const int u = __ldg(p.cols + k);
-            if (get_level(p, u) == d) {
+            if (get_level(p, u) == lv - 1) {
                 p.parent[v] = u;
                 break;
             }
@@ -682,8 +771,8 @@ __device__ __forceinline__ int bu_locate(int k, int T, int incl, int excl, unsig
 }
 
 __device__ void bu_phase_a(const SingleParams& p, int d, const unsigned* fcur, unsigned* fnext, int* longlist,
-                           unsigned long long* longcnt, unsigned long long* chunkctr, unsigned long long& acc_n,
-                           unsigned long long& acc_m, unsigned long long& acc_sc, unsigned long long& acc_ex) {
+                           unsigned long long* longcnt, unsigned long long& acc_n, unsigned long long& acc_m,
+                           unsigned long long& acc_sc, unsigned long long& acc_ex) {
     __shared__ unsigned s_next[kWarps][32];
     const int lane = lane_id(), wib = threadIdx.x >> 5;
     const long long nchunk = (p.W + 31) / 32;
@@ -691,18 +780,8 @@ __device__ void bu_phase_a(const SingleParams& p, int d, const unsigned* fcur, u
     s_next[wib][lane] = 0u;
     WarpStage lst = warp_stage();   // long-list entries, appended in batches
     __syncwarp();
-#if BFS_BU_DYN
-    // chunks handed out by a counter (the next one is claimed while this one runs)
-    unsigned long long grab = 0;
-    if (lane == 0) grab = atomicAdd(chunkctr, 1ull);
-    long long ch = (long long)__shfl_sync(kFull, grab, 0);
-    while (ch < nchunk) {
-        if (lane == 0) grab = atomicAdd(chunkctr, 1ull);
-#else
-    (void)chunkctr;
     const long long gw = gtid() >> 5, nw = gthreads() >> 5;
     for (long long ch = gw; ch < nchunk; ch += nw) {
-#endif
         const long long w = ch * 32 + lane;
         const unsigned cw = (w < p.W) ? __ldcg(p.visited + w) : kFull;
         const unsigned todo = ~cw;
@@ -798,106 +877,170 @@ __device__ void bu_phase_a(const SingleParams& p, int d, const unsigned* fcur, u
         acc_n += (unsigned long long)__popc(nx);
         s_next[wib][lane] = 0u;
         __syncwarp();
-#if BFS_BU_DYN
-        ch = (long long)__shfl_sync(kFull, grab, 0);
-#endif
     }
     long_flush(lst, longlist, longcnt);
 }
 
-// Bottom-up, phase A over the row heads.  The same warp-per-1024-vertices
-// compaction, but a searcher's first probes need no offsets: round r reads
-// the 32-byte heads of its 32 searchers (consecutive vertices, so the warp's
-// loads are contiguous), probes the first id alone and the other six
-// only on a miss.  Heads are prefetched two rounds ahead.  Searchers with
-// more than kHead neighbours and no hit among the first kHead go on the long
-// list, whose scan resumes at row position kHead.
-constexpr int kHead = 7;
+// Bottom-up over the hub-first rows, phase A: the first probe of every
+// searcher.  Algorithm 2 scans a searcher's row in order and stops at the first
+// neighbour in the frontier; over the hub-first rows that first neighbour is
+// the hit for most searchers on R-MAT graphs.  So phase A reads, per vertex,
+// only first[v] (the first id of its row, bit 31: more neighbours follow), a
+// plane streamed in vertex order.  A warp owns 32 completed-bitmap words (1024
+// vertices) at a time and walks them word by word, lane i on vertex 32w + i,
+// kSweepBatch words per step: all plane loads of a step are in flight
+// together, then all its frontier probes.  While a chunk runs, the plane lines
+// of the warp's next chunk (those with searchers) are prefetched into L2.  The
+// ballot of a word's hits is that word of the next frontier (the warp owns it:
+// no atomics).  A hit stores no parent: its parent is first[v], recorded by one
+// bit of pfirst (the final pass writes the parent array).  A miss with more
+// neighbours goes on the miss list (phase B); a degree-1 miss is done.
+//
+// No degree is read for a hit: the degree sum of the new frontier is m_u minus
+// the degree sum of the searchers left unvisited, which phases A-C count
+// (acc_left), and a searcher left unvisited has had its whole row examined.
+constexpr int kHead = 7;          // ids in a row head
+constexpr int kSweepBatch = 8;    // words per step of the sweep
+static_assert(32 % kSweepBatch == 0, "a step takes whole words of one 32-word chunk");
+constexpr unsigned kMore = 0x80000000u;
 
-__device__ void bu_phase_a_heads(const SingleParams& p, int d, const unsigned* fcur, unsigned* fnext,
-                                 int* longlist, unsigned long long* longcnt, unsigned long long& acc_n,
-                                 unsigned long long& acc_m, unsigned long long& acc_sc,
-                                 unsigned long long& acc_ex) {
-    __shared__ unsigned s_hnext[kWarps][32];
-    const int lane = lane_id(), wib = threadIdx.x >> 5;
+__device__ void bu_sweep(const SingleParams& p, int d, const unsigned* fcur, unsigned* fnext, int* misslist,
+                         unsigned long long* misscnt, unsigned long long& acc_n, unsigned long long& acc_left,
+                         unsigned long long& acc_sc, unsigned long long& acc_ex) {
+    const int lane = lane_id();
     const long long nchunk = (p.W + 31) / 32;
-    const int4 z4 = make_int4(0, 0, 0, 0);
-    s_hnext[wib][lane] = 0u;
-    WarpStage lst = warp_stage();
-    __syncwarp();
+    WarpStage mst = warp_stage();   // miss-list entries, appended in batches
     const long long gw = gtid() >> 5, nw = gthreads() >> 5;
+    // completed words of the warp's current chunk (lane i: word 32 ch + i); no
+    // other warp writes them during this phase
+    unsigned cw = kFull;
+    if (gw < nchunk && gw * 32 + lane < p.W) cw = __ldcg(p.visited + gw * 32 + lane);
+    if (gw < nchunk && cw != kFull) prefetch_l2_line(p.first + (gw * 32 + lane) * 32);
     for (long long ch = gw; ch < nchunk; ch += nw) {
-        const long long w = ch * 32 + lane;
-        const unsigned cw = (w < p.W) ? __ldcg(p.visited + w) : kFull;
+        const long long wl = ch * 32 + lane;      // this lane's word of the chunk
+        const long long wn = wl + nw * 32;        // its word of the warp's next chunk
+        const unsigned cwn = (ch + nw < nchunk && wn < p.W) ? __ldcg(p.visited + wn) : kFull;
+        if (cwn != kFull) prefetch_l2_line(p.first + wn * 32);
         const unsigned todo = ~cw;
-        const int cnt = __popc(todo);
-        const int incl = warp_inclusive_scan(cnt);
-        const int T = __shfl_sync(kFull, incl, 31);
-        const int excl = incl - cnt;
-        int u0 = bu_locate(lane, T, incl, excl, todo, ch);
-        int4 a0 = z4, b0 = z4;
-        if (u0 >= 0) {
-            ld_stream8(p.heads + 8 * (long long)u0, a0, b0);
-        }
-        int u1 = bu_locate(32 + lane, T, incl, excl, todo, ch);
-        int4 a1 = z4, b1 = z4;
-        if (u1 >= 0) {
-            ld_stream8(p.heads + 8 * (long long)u1, a1, b1);
-        }
-        for (int base = 0; base < T; base += 32) {
-            const int u2 = bu_locate(base + 64 + lane, T, incl, excl, todo, ch);
-            int4 a2 = z4, b2 = z4;
-            if (u2 >= 0) {
-                ld_stream8(p.heads + 8 * (long long)u2, a2, b2);
-            }
-            bool to_long = false;
-            if (u0 >= 0) {
-                const int deg = a0.x;
-                const int ids[kHead] = {a0.y, a0.z, a0.w, b0.x, b0.y, b0.z, b0.w};
-                unsigned hit = 0;
-                if (deg > 0 && in_frontier(fcur, ids[0])) {
-                    hit = 1u;
-                } else {
+        const unsigned busy = __ballot_sync(kFull, todo != 0u);   // words with searchers
+        unsigned nx = 0;                          // next-frontier bits of word wl
+        for (int jb = 0; jb < 32; jb += kSweepBatch) {
+            if (((busy >> jb) & ((1u << kSweepBatch) - 1u)) == 0u) continue;
+            int f[kSweepBatch];
+            unsigned actm = 0;                    // bit k: this lane searches in word jb + k
 #pragma unroll
-                    for (int t = 1; t < kHead; t++)
-                        if (t < deg && in_frontier(fcur, ids[t])) hit |= 1u << t;
+            for (int k = 0; k < kSweepBatch; k++) {
+                const bool a = (__shfl_sync(kFull, todo, jb + k) >> lane) & 1u;
+                f[k] = 0;
+                if (a) {
+                    f[k] = ld_stream32(p.first + (ch * 32 + jb + k) * 32 + lane);
+                    actm |= 1u << k;
                 }
-                acc_sc += 1;
+            }
+            unsigned hitm = 0;
+#pragma unroll
+            for (int k = 0; k < kSweepBatch; k++)
+                if (((actm >> k) & 1u) && in_frontier(fcur, f[k] & (int)~kMore)) hitm |= 1u << k;
+#pragma unroll
+            for (int k = 0; k < kSweepBatch; k++) {
+                const int v = (int)((ch * 32 + jb + k) * 32 + lane);
+                const bool act = (actm >> k) & 1u, hit = (hitm >> k) & 1u;
+                const unsigned hm = __ballot_sync(kFull, hit);
+                if (lane == jb + k) nx = hm;
+                const bool miss = act && !hit && ((unsigned)f[k] & kMore);
+                if (act) {
+                    acc_sc += 1;
+                    acc_ex += (unsigned long long)(hit || !miss);   // a hit, or a degree-1 row
+                    if (hit) {
+                        set_level(p, v, d + 1);
+                        if (!p.pfirst && p.parent) p.parent[v] = f[k] & (int)~kMore;
+                    } else if (!miss) {
+                        acc_left += 1;            // degree 1, left unvisited
+                    }
+                }
+                const unsigned mm = __ballot_sync(kFull, miss);
+                if (mm) {
+                    if (miss) mst.buf[mst.cnt + __popc(mm & lanemask_lt())] = v;
+                    mst.cnt += __popc(mm);
+                    if (mst.cnt > kStage - 32) long_flush(mst, misslist, misscnt);
+                }
+            }
+        }
+        if (wl < p.W) {
+            fnext[wl] = nx;
+            if (nx) {
+                p.visited[wl] = cw | nx;
+                if (p.pfirst) p.pfirst[wl] = __ldcg(p.pfirst + wl) | nx;
+            }
+        }
+        acc_n += (unsigned long long)__popc(nx);
+        cw = cwn;
+    }
+    long_flush(mst, misslist, misscnt);
+}
+
+// Bottom-up over the hub-first rows, phase B: the miss list.  Each lane takes
+// kMissPerLane searchers per step and reads their 32-byte row heads (degree and
+// the first seven ids, one 256-bit load each, all in flight together), then
+// probes ids 1..6 in row order.  A hit writes its parent directly; the next-
+// frontier and completed words are shared with other warps here, hence
+// atomicOr.  A searcher with more than seven neighbours and no hit among them
+// goes on the long list (phase C resumes its row at position 7).
+constexpr int kMissPerLane = 2;
+
+__device__ void bu_misses(const SingleParams& p, int d, const unsigned* fcur, unsigned* fnext, const int* misslist,
+                          long long nmiss, int* longlist, unsigned long long* longcnt, unsigned long long& acc_n,
+                          unsigned long long& acc_left, unsigned long long& acc_ex) {
+    const int lane = lane_id();
+    WarpStage lst = warp_stage();
+    const long long gw = gtid() >> 5, nw = gthreads() >> 5;
+    constexpr int kStep = 32 * kMissPerLane;
+    for (long long base = gw * kStep; base < nmiss; base += nw * kStep) {
+        int u[kMissPerLane];
+        int4 a[kMissPerLane], b[kMissPerLane];
+#pragma unroll
+        for (int r = 0; r < kMissPerLane; r++) {
+            const long long i = base + r * 32 + lane;
+            u[r] = -1;
+            a[r] = b[r] = make_int4(0, 0, 0, 0);
+            if (i < nmiss) {
+                u[r] = __ldcg(misslist + i);
+                ld_stream8(p.heads + 8 * (long long)u[r], a[r], b[r]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < kMissPerLane; r++) {
+            bool to_long = false;
+            if (u[r] >= 0) {
+                const int deg = a[r].x;
+                const int ids[kHead] = {a[r].y, a[r].z, a[r].w, b[r].x, b[r].y, b[r].z, b[r].w};
+                unsigned hit = 0;
+#pragma unroll
+                for (int t = 1; t < kHead; t++)
+                    if (t < deg && in_frontier(fcur, ids[t])) hit |= 1u << t;
                 if (hit) {
                     const int t = __ffs(hit) - 1;
+                    const int v = u[r];
                     acc_ex += (unsigned long long)(t + 1);
-                    acc_m += (unsigned long long)deg;
-                    if (p.parent) p.parent[u0] = pick(ids, t);
-                    set_level(p, u0, d + 1);
-                    atomicOr(&s_hnext[wib][(u0 >> 5) - ch * 32], 1u << (u0 & 31));
+                    acc_n += 1;
+                    if (p.parent) p.parent[v] = pick(ids, t);
+                    set_level(p, v, d + 1);
+                    atomicOr(fnext + (v >> 5), 1u << (v & 31));
+                    atomicOr(p.visited + (v >> 5), 1u << (v & 31));
                 } else if (deg > kHead) {
-                    to_long = true;       // examinations counted by phase B
+                    to_long = true;       // examinations counted by phase C
                 } else {
                     acc_ex += (unsigned long long)deg;
+                    acc_left += (unsigned long long)deg;
                 }
             }
             const unsigned lm = __ballot_sync(kFull, to_long);
             if (lm) {
-                if (to_long) lst.buf[lst.cnt + __popc(lm & lanemask_lt())] = u0;
+                if (to_long) lst.buf[lst.cnt + __popc(lm & lanemask_lt())] = u[r];
                 lst.cnt += __popc(lm);
                 if (lst.cnt > kStage - 32) long_flush(lst, longlist, longcnt);
             }
-            u0 = u1;
-            a0 = a1;
-            b0 = b1;
-            u1 = u2;
-            a1 = a2;
-            b1 = b2;
         }
-        __syncwarp();
-        const unsigned nx = s_hnext[wib][lane];
-        if (w < p.W) {
-            fnext[w] = nx;
-            if (nx) p.visited[w] = cw | nx;
-        }
-        acc_n += (unsigned long long)__popc(nx);
-        s_hnext[wib][lane] = 0u;
-        __syncwarp();
     }
     long_flush(lst, longlist, longcnt);
 }
@@ -908,53 +1051,11 @@ __device__ void bu_phase_a_heads(const SingleParams& p, int d, const unsigned* f
 // group with a hit, its lowest id -- so parents stay the minimum-id ones.
 // Next-frontier and completed words are shared across warps here, hence
 // atomicOr.
-#if BFS_BU_PHASEB == 2
+// With count_left, acc_m receives the degrees of the searchers left unvisited
+// (the hub-first sweep's accounting); otherwise those of the ones found.
 __device__ void bu_phase_b(const SingleParams& p, int d, const unsigned* fcur, unsigned* fnext, const int* longlist,
-                           long long nlong, int skip, unsigned long long& acc_n, unsigned long long& acc_m,
-                           unsigned long long& acc_ex) {
-    const long long tid = gtid(), nth = gthreads();
-    const int4 z4 = make_int4(0, 0, 0, 0);
-    for (long long i = tid; i < nlong; i += nth) {
-        const int u = __ldcg(longlist + i);
-        long long s0, e0;
-        row_of(p, u, s0, e0);
-        long long pos = (s0 + skip) & ~3LL;
-        long long hitpos = -1;
-        int pv = -1;
-        while (pos < e0) {
-            const int4* src = reinterpret_cast<const int4*>(p.cols_bu + pos);
-            const int4 xa = __ldg(src);
-            const int4 xb = (pos + 4 < e0) ? __ldg(src + 1) : z4;
-            const int ids[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
-            unsigned hb = 0;
-#pragma unroll
-            for (int t = 0; t < 8; t++)
-                if (pos + t < e0 && in_frontier(fcur, ids[t])) hb |= 1u << t;
-            if (hb) {
-                const int t = __ffs(hb) - 1;
-                hitpos = pos + t;
-                pv = pick(ids, t);
-                break;
-            }
-            pos += 8;
-        }
-        if (hitpos >= 0) {
-            acc_ex += (unsigned long long)(hitpos - s0 + 1);
-            acc_m += (unsigned long long)(e0 - s0);
-            acc_n += 1;
-            if (p.parent) p.parent[u] = pv;
-            set_level(p, u, d + 1);
-            atomicOr(fnext + (u >> 5), 1u << (u & 31));
-            atomicOr(p.visited + (u >> 5), 1u << (u & 31));
-        } else {
-            acc_ex += (unsigned long long)(e0 - s0);
-        }
-    }
-}
-#else
-__device__ void bu_phase_b(const SingleParams& p, int d, const unsigned* fcur, unsigned* fnext, const int* longlist,
-                           long long nlong, int skip, unsigned long long& acc_n, unsigned long long& acc_m,
-                           unsigned long long& acc_ex) {
+                           long long nlong, int skip, bool count_left, unsigned long long& acc_n,
+                           unsigned long long& acc_m, unsigned long long& acc_ex) {
     const int lane = lane_id(), grp = lane >> 2, gl = lane & 3;
     const long long gw = gtid() >> 5, nw = gthreads() >> 5;
     for (long long base = gw * 8; base < nlong; base += nw * 8) {
@@ -1003,7 +1104,7 @@ __device__ void bu_phase_b(const SingleParams& p, int d, const unsigned* fcur, u
         if (u >= 0 && gl == 0) {
             if (hitpos >= 0) {
                 acc_ex += (unsigned long long)(hitpos - s0 + 1);
-                acc_m += (unsigned long long)(e0 - s0);
+                if (!count_left) acc_m += (unsigned long long)(e0 - s0);
                 acc_n += 1;
                 if (p.parent) p.parent[u] = pv;
                 set_level(p, u, d + 1);
@@ -1011,11 +1112,11 @@ __device__ void bu_phase_b(const SingleParams& p, int d, const unsigned* fcur, u
                 atomicOr(p.visited + (u >> 5), 1u << (u & 31));
             } else {
                 acc_ex += (unsigned long long)(e0 - s0);
+                if (count_left) acc_m += (unsigned long long)(e0 - s0);
             }
         }
     }
 }
-#endif
 
 // ------------------------------------------------------------------ kernel
 
@@ -1048,9 +1149,9 @@ __global__ void __launch_bounds__(kBlock, BFS_MIN_BLOCKS) bfs_single_kernel(Sing
             c->scanned[sfree] = 0;
             c->examined[sfree] = 0;
             c->ntask[sfree] = 0;
-            c->chunk[sfree] = 0;
+            c->nmiss[sfree] = 0;
         }
-        long long nf_next, scanned = 0, examined = mf, aux = 0;
+        long long nf_next, scanned = 0, examined = mf, aux = 0, misses = 0;
         uint64_t t_mid = 0;
         int* qcur = qsel ? p.queue1 : p.queue0;
         int* qnext = qsel ? p.queue0 : p.queue1;
@@ -1075,28 +1176,44 @@ __global__ void __launch_bounds__(kBlock, BFS_MIN_BLOCKS) bfs_single_kernel(Sing
                 if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
             }
             nf_next = (long long)ld_relaxed64(&c->tail[snext]);
-            if (p.parent_mode == BFS_PARENT_MIN_ID && p.parent && p.level) td_min_parent(p, d, qnext, nf_next);
             qsel ^= 1;
         } else {
             if (prev == TD) {
                 queue_to_bitmap(p, qcur, nf, fcur);
                 if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
             }
+            // over the hub-first rows accm[snext] collects the degrees of the searchers
+            // left unvisited (the new frontier's degree sum is m_u minus that), over the
+            // id-ordered rows those of the vertices found
             unsigned long long an = 0, am = 0, asc = 0, aex = 0;
-            int* longlist = qnext;   // the queues are idle during bottom-up levels
-            if (p.heads)
-                bu_phase_a_heads(p, d, fcur, fnext, longlist, &c->ntask[snext], an, am, asc, aex);
+            // the queues are idle during bottom-up levels (a preceding queue -> bitmap
+            // conversion ended at the barrier above)
+            int* longlist = qnext;
+            int* misslist = qcur;
+            if (p.first)
+                bu_sweep(p, d, fcur, fnext, misslist, &c->nmiss[snext], an, am, asc, aex);
             else
-                bu_phase_a(p, d, fcur, fnext, longlist, &c->ntask[snext], &c->chunk[snext], an, am, asc, aex);
+                bu_phase_a(p, d, fcur, fnext, longlist, &c->ntask[snext], an, am, asc, aex);
             block_add4(an, am, asc, aex, &c->accn[snext], &c->accm[snext], &c->scanned[snext],
                        &c->examined[snext]);
             if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
+            if (lead) t_mid = globaltimer_ns();
+            if (p.first) {
+                const long long nmiss = (long long)ld_relaxed64(&c->nmiss[snext]);
+                misses = nmiss;
+                if (nmiss > 0) {
+                    unsigned long long bn = 0, bm = 0, bex = 0;
+                    bu_misses(p, d, fcur, fnext, misslist, nmiss, longlist, &c->ntask[snext], bn, bm, bex);
+                    block_add4(bn, bm, 0, bex, &c->accn[snext], &c->accm[snext], nullptr, &c->examined[snext]);
+                    if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
+                }
+            }
             const long long nlong = (long long)ld_relaxed64(&c->ntask[snext]);
             aux = nlong;
-            if (lead) t_mid = globaltimer_ns();
             if (nlong > 0) {
                 unsigned long long bn = 0, bm = 0, bex = 0;
-                bu_phase_b(p, d, fcur, fnext, longlist, nlong, p.heads ? kHead : kWin, bn, bm, bex);
+                bu_phase_b(p, d, fcur, fnext, longlist, nlong, p.first ? kHead : kWin, p.first != nullptr, bn, bm,
+                           bex);
                 block_add4(bn, bm, 0, bex, &c->accn[snext], &c->accm[snext], nullptr, &c->examined[snext]);
                 if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
             }
@@ -1105,11 +1222,12 @@ __global__ void __launch_bounds__(kBlock, BFS_MIN_BLOCKS) bfs_single_kernel(Sing
             examined = (long long)ld_relaxed64(&c->examined[snext]);
             bsel ^= 1;
         }
-        const long long mf_next = (long long)ld_relaxed64(&c->accm[snext]);
+        const long long macc = (long long)ld_relaxed64(&c->accm[snext]);
+        const long long mf_next = (dir == BU && p.first) ? mu - macc : macc;
         if (lead && d < p.rec_cap) {
             bfs_level_record r;
             r.dir = dir;
-            r.reserved = 0;
+            r.misses = (int)misses;
             r.nf = nf;
             r.mf = mf;
             r.nnext = nf_next;
@@ -1134,7 +1252,11 @@ __global__ void __launch_bounds__(kBlock, BFS_MIN_BLOCKS) bfs_single_kernel(Sing
         c->reached = reached;
     }
     // every level ended at a grid barrier, so all staged bytes are visible here
-    if (p.lv8 && p.level) expand_levels(p);
+    if (p.parent_mode == BFS_PARENT_MIN_ID && p.parent && p.level) {
+        min_parent_pass(p);
+        if (p.lv8 && !grid_sync(&c->b, p.expected, p.timeout_ns)) return;
+    }
+    if (p.lv8) materialise(p);
 }
 
 // ------------------------------------------------------------------ DCSC tiles
@@ -1329,7 +1451,6 @@ __global__ void __launch_bounds__(kDBlock, 1) bfs_dcsc_kernel(SingleParams p) {
             block_add4(0, am, 0, 0, nullptr, &c->accm[snext], nullptr, nullptr);
             if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
             nf_next = (long long)ld_relaxed64(&c->tail[snext]);
-            if (p.parent_mode == BFS_PARENT_MIN_ID && p.parent && p.level) td_min_parent(p, d, qnext, nf_next);
             qsel ^= 1;
         } else {
             if (prev == TD) {
@@ -1349,7 +1470,7 @@ __global__ void __launch_bounds__(kDBlock, 1) bfs_dcsc_kernel(SingleParams p) {
         if (lead && d < p.rec_cap) {
             bfs_level_record r;
             r.dir = dir;
-            r.reserved = 0;
+            r.misses = 0;
             r.nf = nf;
             r.mf = mf;
             r.nnext = nf_next;
@@ -1373,6 +1494,7 @@ __global__ void __launch_bounds__(kDBlock, 1) bfs_dcsc_kernel(SingleParams p) {
         c->num_levels = d + 1;
         c->reached = reached;
     }
+    if (p.parent_mode == BFS_PARENT_MIN_ID && p.parent && p.level) min_parent_pass(p);
 }
 
 // ------------------------------------------------------------------ allocation-free variant
@@ -1440,6 +1562,7 @@ bfs_status single_prepare_work(bfs_graph* g, SingleWork& w, cudaStream_t s, int 
         {(void**)&w.queue0, sizeof(int) * (size_t)(n + 32)},
         {(void**)&w.queue1, sizeof(int) * (size_t)(n + 32)},
         {(void**)&w.lv8, (size_t)W * 32},   // one byte per vertex, rounded up to whole bitmap words
+        {(void**)&w.pfirst, sizeof(unsigned) * (size_t)W},
         {(void**)&w.tasks, sizeof(Task) * (size_t)task_cap},
         {(void**)&w.ctrl, sizeof(Ctrl)},
         {(void**)&w.records, sizeof(bfs_level_record) * (size_t)rec_cap},
@@ -1482,6 +1605,7 @@ void single_release_work(bfs_graph* g, SingleWork& w) {
     g->mem.release(w.queue0, sizeof(int) * (size_t)(n + 32), nullptr);
     g->mem.release(w.queue1, sizeof(int) * (size_t)(n + 32), nullptr);
     g->mem.release(w.lv8, (size_t)W * 32, nullptr);
+    g->mem.release(w.pfirst, sizeof(unsigned) * (size_t)W, nullptr);
     if (w.level_scratch) g->mem.release(w.level_scratch, sizeof(int) * (size_t)n, nullptr);
     g->mem.release(w.tasks, sizeof(Task) * (size_t)w.task_cap, nullptr);
     g->mem.release(w.ctrl, sizeof(Ctrl), nullptr);
@@ -1507,16 +1631,20 @@ bfs_status single_launch_work(bfs_graph* g, SingleWork& w, const int32_t* roots_
     SingleParams p;
     p.off = reinterpret_cast<const long long*>(g->offsets);
     p.cols = g->cols;
-    p.cols_bu = (opt.bu_rows == BFS_BU_ROWS_HUB_FIRST && g->cols_hf) ? g->cols_hf : g->cols;
-    p.heads = (BFS_BU_HEADS && opt.bu_rows == BFS_BU_ROWS_HUB_FIRST && g->cols_hf && g->bu_heads)
-                  ? g->bu_heads : nullptr;
+    const bool hub = opt.bu_rows == BFS_BU_ROWS_HUB_FIRST && g->cols_hf;
+    p.cols_bu = hub ? g->cols_hf : g->cols;
+    p.heads = (hub && g->bu_heads && g->bu_first) ? g->bu_heads : nullptr;
+    p.first = p.heads ? g->bu_first : nullptr;
+    p.deg8 = g->deg8;
     p.isolated = g->isolated;
     p.n = g->n;
     p.nnz = g->nnz;
     p.W = g->W;
     p.parent = parent;
     p.level = level;
-    p.lv8 = (opt.layout == BFS_LAYOUT_DCSC_TILED) ? nullptr : w.lv8;
+    // staged outputs and the final whole-sector pass (CSR kernel, some output requested)
+    p.lv8 = (opt.layout == BFS_LAYOUT_DCSC_TILED || (!parent && !level)) ? nullptr : w.lv8;
+    p.pfirst = p.lv8 ? w.pfirst : nullptr;
     p.visited = w.visited;
     p.front0 = w.front0;
     p.front1 = w.front1;
@@ -1628,6 +1756,14 @@ extern "C" bfs_status bfs_run_csr_noalloc(const int64_t* row_offsets, const int3
         return fail(BFS_ERR_INVALID, "bfs_run_csr_noalloc: nnz must lie in [0, " +
                                          std::to_string(bfsk::kStaticMaxNnz) + "] (its scratch is a fixed device array)");
     if (root < 0 || (int64_t)root >= n) return fail(BFS_ERR_INVALID, "root outside [0, n)");
+    // the bottom-up scan reads col_ids 16 bytes at a time from 16-byte boundaries of the
+    // array, and the offsets are 8-byte loads: a misaligned pointer would fault on the GPU
+    if (((uintptr_t)col_ids & 15u) != 0)
+        return fail(BFS_ERR_INVALID, "bfs_run_csr_noalloc: col_ids must be 16-byte aligned");
+    if (((uintptr_t)row_offsets & 7u) != 0)
+        return fail(BFS_ERR_INVALID, "bfs_run_csr_noalloc: row_offsets must be 8-byte aligned");
+    if (((uintptr_t)parent_dev & 3u) != 0 || ((uintptr_t)level_dev & 3u) != 0)
+        return fail(BFS_ERR_INVALID, "bfs_run_csr_noalloc: parent_dev / level_dev must be 4-byte aligned");
     int dev = 0;
     BFS_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return fail(BFS_ERR_UNSUPPORTED, "device index above 63");

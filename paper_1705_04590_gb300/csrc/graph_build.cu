@@ -82,6 +82,16 @@ __global__ void k_isolated(const long long* __restrict__ off, long long n, long 
     }
 }
 
+// deg8[v] = min(deg(v), 255): the degree as bottom-up and top-down steps need it
+// (a coalesced byte stream instead of two int64 offsets per vertex)
+__global__ void k_deg8(const long long* __restrict__ off, long long n, uint8_t* __restrict__ deg8) {
+    const long long nth = (long long)gridDim.x * blockDim.x;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n + 32; v += nth) {
+        const long long dg = v < n ? off[v + 1] - off[v] : 0;
+        deg8[v] = (uint8_t)(dg < 255 ? dg : 255);
+    }
+}
+
 // CSR validation: warp per row.  bad codes: 1 offsets, 2 id range, 3 order/duplicate, 4 self-loop, 5 asymmetric
 __global__ void k_check_csr(const long long* __restrict__ off, const int32_t* __restrict__ cols, long long n,
                             long long nnz, int check_sym, int* __restrict__ bad) {
@@ -161,6 +171,11 @@ bfs_status build_isolated_bitmap(bfs_graph* g, cudaStream_t s) {
     g->graph_bytes += sizeof(uint32_t) * (size_t)g->W;
     k_isolated<<<grid_for(g->W, 256, g->sm_count), 256, 0, s>>>((const long long*)g->offsets, g->n, g->W,
                                                                 g->isolated);
+    BFS_CUDA_TRY(cudaGetLastError());
+    g->deg8 = (uint8_t*)g->mem.alloc((size_t)g->n + 32, s);
+    if (!g->deg8) return fail(BFS_ERR_OOM, "graph build: degree bytes");
+    g->graph_bytes += (size_t)g->n + 32;
+    k_deg8<<<grid_for(g->n + 32, 256, g->sm_count), 256, 0, s>>>((const long long*)g->offsets, g->n, g->deg8);
     BFS_CUDA_TRY(cudaGetLastError());
     return BFS_OK;
 }

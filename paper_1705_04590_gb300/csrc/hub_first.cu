@@ -41,17 +41,24 @@ __global__ void k_hub_keys(const long long* __restrict__ off, const int32_t* __r
 }
 
 // heads[2u] = {deg(u), r0, r1, r2}, heads[2u + 1] = {r3, r4, r5, r6}: the first
-// seven ids of u's reordered row, 0 past its end; one thread per vertex
+// seven ids of u's reordered row, 0 past its end; first[u] = r0 | (deg(u) >= 2)
+// << 31 (the plane a bottom-up sweep streams: its first probe, and whether the
+// row goes on); one thread per vertex, first[] zero-padded to n + 32
 __global__ void k_hub_heads(const long long* __restrict__ off, const int32_t* __restrict__ cols_hf, long long n,
-                            int4* __restrict__ heads) {
+                            int4* __restrict__ heads, int32_t* __restrict__ first) {
     const long long nth = (long long)gridDim.x * blockDim.x;
-    for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += nth) {
+    for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < n + 32; u += nth) {
+        if (u >= n) {
+            first[u] = 0;
+            continue;
+        }
         const long long s = off[u], dg = off[u + 1] - s;
         int r[7];
 #pragma unroll
         for (int t = 0; t < 7; t++) r[t] = t < dg ? cols_hf[s + t] : 0;
         heads[2 * u] = make_int4((int)dg, r[0], r[1], r[2]);
         heads[2 * u + 1] = make_int4(r[3], r[4], r[5], r[6]);
+        first[u] = (int32_t)((unsigned)r[0] | (dg >= 2 ? 0x80000000u : 0u));
     }
 }
 
@@ -64,19 +71,29 @@ using namespace bfsk_hub;
 static bfs_status build_bu_heads(bfs_graph* g, cudaStream_t s) {
     const long long n = g->n;
     const size_t bytes = sizeof(int32_t) * 8 * (size_t)n;
+    const size_t fbytes = sizeof(int32_t) * (size_t)(n + 32);
     g->bu_heads = (int32_t*)g->mem.alloc(bytes, s);
-    if (!g->bu_heads) return fail(BFS_ERR_OOM, "hub-first rows: row heads");
-    const int blocks = std::max(1, std::min<int>(g->sm_count * 8, (int)((n + 255) / 256)));
+    g->bu_first = (int32_t*)g->mem.alloc(fbytes, s);
+    if (!g->bu_heads || !g->bu_first) {
+        if (g->bu_heads) g->mem.release(g->bu_heads, bytes, s);
+        if (g->bu_first) g->mem.release(g->bu_first, fbytes, s);
+        g->bu_heads = nullptr;
+        g->bu_first = nullptr;
+        return fail(BFS_ERR_OOM, "hub-first rows: row heads");
+    }
+    const int blocks = std::max(1, std::min<int>(g->sm_count * 8, (int)((n + 32 + 255) / 256)));
     k_hub_heads<<<blocks, 256, 0, s>>>((const long long*)g->offsets, g->cols_hf, n,
-                                       reinterpret_cast<int4*>(g->bu_heads));
+                                       reinterpret_cast<int4*>(g->bu_heads), g->bu_first);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         g->mem.release(g->bu_heads, bytes, s);
+        g->mem.release(g->bu_first, fbytes, s);
         g->bu_heads = nullptr;
+        g->bu_first = nullptr;
         return cuda_fail(e, "hub-first rows: row heads");
     }
-    g->graph_bytes += bytes;
+    g->graph_bytes += bytes + fbytes;
     return BFS_OK;
 }
 

@@ -174,7 +174,7 @@ def test_hub_first_rows_and_searches(gpu_lib):
     hub-first rows; the option is refused where it cannot apply."""
     bfs = gpu_lib
     graphs = [workloads.RMAT[14].edges(), graphgen.random_small(257, 600, 11), graphgen.torus(64, seed=3000),
-              graphgen.erdos_renyi(100_003, 800_000, seed=5), graphgen.path(700)]
+              graphgen.erdos_renyi(100_003, 800_000, seed=5), graphgen.path(700), graphgen.star(600, center=17)]
     modes = {bfs.MODE_DO: oracle.MODE_DO, bfs.MODE_TD_ONLY: oracle.MODE_TD, bfs.MODE_BU_ONLY: oracle.MODE_BU}
     for e in graphs:
         case = Case(bfs, e)
@@ -189,6 +189,12 @@ def test_hub_first_rows_and_searches(gpu_lib):
             has = deg > t
             want[has, 1 + t] = h.cols[case.ref.offsets[:-1][has] + t]
         assert np.array_equal(g.row_heads_host(), want), e.name
+        # the plane a bottom-up sweep streams (first id of each hub-first row, bit 31
+        # set for two or more neighbours, 0 for degree 0) and the degree clamped to a byte
+        first, deg8 = g.bu_planes_host()
+        assert np.array_equal(first.view(np.uint32), want[:, 1].astype(np.uint32) | np.where(deg >= 2, 1 << 31, 0)
+                              .astype(np.uint32)), e.name
+        assert np.array_equal(deg8, np.minimum(deg, 255).astype(np.uint8)), e.name
         case.g.close()
         case.g = g
         deg = np.diff(case.ref.offsets)
@@ -247,6 +253,29 @@ def test_deep_levels_and_partial_outputs(gpu_lib):
                 pa_only.fill_(-7)
                 case.g.run(root, parent=pa_only, opts=opts)
                 assert np.array_equal(pa_only.cpu().numpy(), pwant), (root, mode, pm)
+    # the same over the hub-first rows (first-probe sweep, final whole-sector pass),
+    # and with outputs that are 4- but not 16-byte aligned (the pass's scalar path)
+    g = bfs.Graph.from_edges(case.e.src, case.e.dst, n, hub_first=True)
+    buf = torch.empty(2 * n + 8, dtype=torch.int32, device="cuda")
+    for root in (0, 350, n - 1):
+        want = np.abs(np.arange(n) - root)
+        pwant = np.where(np.arange(n) < root, np.arange(n) + 1, np.arange(n) - 1)
+        pwant[root] = root
+        for mode in (bfs.MODE_DO, bfs.MODE_TD_ONLY, bfs.MODE_BU_ONLY):
+            opts = bfs.options(mode=mode, bu_rows=bfs.BU_ROWS_HUB_FIRST)
+            for lv_t, pa_t in ((case.level, case.parent), (buf[1:n + 1], buf[n + 3:2 * n + 3])):
+                lv_t.fill_(-7)
+                pa_t.fill_(-7)
+                g.run(root, parent=pa_t, level=lv_t, opts=opts)
+                assert np.array_equal(lv_t.cpu().numpy(), want), (root, mode)
+                assert np.array_equal(pa_t.cpu().numpy(), pwant), (root, mode)
+            lv_only.fill_(-7)
+            g.run(root, level=lv_only, opts=opts)
+            assert np.array_equal(lv_only.cpu().numpy(), want), (root, mode)
+            pa_only.fill_(-7)
+            g.run(root, parent=pa_only, opts=opts)
+            assert np.array_equal(pa_only.cpu().numpy(), pwant), (root, mode)
+    g.close()
 
 
 def test_degree_zero_root_and_empty_graph(gpu_lib):

@@ -70,4 +70,50 @@ def test_noalloc_rejects_sizes_beyond_its_array(gpu_lib):
     assert st == L.BFS_ERR_INVALID and b"n must lie in" in lib.bfs_last_error()
     st = lib.bfs_run_csr_noalloc(po, pc, e.n, (1 << 24) + 1, 0, None, lv.data_ptr(), None)
     assert st == L.BFS_ERR_INVALID and b"nnz must lie in" in lib.bfs_last_error()
+    # a column array that is only 4-byte aligned (a slice of a larger buffer) is refused on
+    # the host: the bottom-up scan reads it 16 bytes at a time; nothing is launched
+    lv.fill_(7)
+    torch.cuda.synchronize()
+    st = lib.bfs_run_csr_noalloc(po, pc + 4, e.n, g.nnz, 0, None, lv.data_ptr(), None)
+    assert st == L.BFS_ERR_INVALID and b"col_ids must be 16-byte aligned" in lib.bfs_last_error()
+    st = lib.bfs_run_csr_noalloc(po + 4, pc, e.n, g.nnz, 0, None, lv.data_ptr(), None)
+    assert st == L.BFS_ERR_INVALID and b"row_offsets must be 8-byte aligned" in lib.bfs_last_error()
+    torch.cuda.synchronize()
+    assert int((lv != 7).sum()) == 0
     g.close()
+
+
+def test_noalloc_caller_owned_csr_at_its_size_limit(gpu_lib):
+    """A CSR the caller allocated itself (torch tensors, exactly the documented 32
+    entries of padding), n = 2^20 (the fixed array's vertex limit, so every work
+    buffer in it is fully used), one call with no parent output and one from a
+    degree-0 root, checked against the oracle."""
+    import torch
+    import paper_1705_04590_gb300._lib as L
+    lib = L.load()
+    n = 1 << 20
+    e = graphgen.erdos_renyi(n, 3 * n, seed=2020)      # nnz about 6n, below the 2^24 limit
+    ref = oracle.build_csr(e.n, e.src, e.dst)
+    assert ref.nnz <= (1 << 24)
+    deg = ref.degree()
+    off_d = torch.from_numpy(ref.offsets).cuda()
+    cols_d = torch.zeros(ref.nnz + 32, dtype=torch.int32, device="cuda")
+    cols_d[:ref.nnz] = torch.from_numpy(ref.cols).cuda()
+    stream = torch.cuda.current_stream().cuda_stream
+    root = int(np.flatnonzero(deg > 0)[17])
+    lv = torch.full((n,), 7, dtype=torch.int32, device="cuda")
+    st = lib.bfs_run_csr_noalloc(off_d.data_ptr(), cols_d.data_ptr(), n, ref.nnz, root, None, lv.data_ptr(), stream)
+    assert st == 0, lib.bfs_last_error()
+    torch.cuda.synchronize()
+    assert np.array_equal(lv.cpu().numpy(), oracle.levels(ref, root))
+    iso = int(np.flatnonzero(deg == 0)[0])
+    pa = torch.full((n,), 7, dtype=torch.int32, device="cuda")
+    st = lib.bfs_run_csr_noalloc(off_d.data_ptr(), cols_d.data_ptr(), n, ref.nnz, iso, pa.data_ptr(), lv.data_ptr(),
+                                 stream)
+    assert st == 0, lib.bfs_last_error()
+    torch.cuda.synchronize()
+    want = np.full(n, -1, np.int32)
+    want[iso] = 0
+    assert np.array_equal(lv.cpu().numpy(), want)
+    want[iso] = iso
+    assert np.array_equal(pa.cpu().numpy(), want)
