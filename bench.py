@@ -19,16 +19,26 @@ e2e     = the same through the public API with host buffers: each step also
 roofline: algorithmic bytes per search from the search's own per-level
           counters (paper_1705_04590_gb300.roofline) / measured duration,
           against the measured HBM copy bandwidth (MEASURED_PEAKS.json).
-cpu_baseline: the serial CPU oracle (Algorithm 1) on one host core, on a
-          bounded sample: R-MAT at a smaller scale with the same generator.
+cpu_baseline: the serial CPU oracle (Algorithm 1) on 4 roots of the headline graph
+          itself (the device CSR copied to host: the parity tests prove it equal
+          to the oracle's), one search per host core; cpu_multithreaded: the
+          multithreaded direction-optimizing CPU BFS (the paper's in-node
+          algorithm, OpenMP) on the same roots with every host thread.
+tuned:   the autotuner's options (alpha, beta, hub cut-off, top-down chunk,
+          CTAs per SM) on 4 sample roots, timed over the same steps.
 batched: 64-lane multi-source search (R-MAT 22, 64 roots, one launch) and an
           uneven batch of 256 graphs (one multi-root launch over their union),
           each against looping the plain single-source search.
-served:  continuous-batching server over 8 resident graphs, Poisson arrivals at
-          0.25/0.5/0.9 of the saturated throughput, p50/p99 latency and GTEPS,
-          against a one-at-a-time plain FIFO on the same arrival trace.
+served:  continuous-batching server over 8 resident graphs; the sustained
+          capacity is the highest Poisson rate it keeps up with (>= 97 % served,
+          p99 under 100 ms); Poisson arrivals at 0.25/0.5/0.9 of it, p50/p99
+          latency and GTEPS, against a one-at-a-time plain FIFO on the same trace.
+configs: R-MAT 24 over CSR (hub-first and id-ordered rows) and DCSC tiles, each
+          direction-optimizing / top-down only / bottom-up only; Erdos-Renyi
+          n = 2^26; the 4096^2 torus: a few roots each, GTEPS and roofline.
 
---impl reference times that oracle alone, the same way, one search per step.
+--impl reference times the oracle alone on the headline graph (built by the oracle),
+one whole search per step, one search per host core at a time.
 Multi-GPU (torchrun): replicas only -- each rank searches its own copy of the
 graph from its own roots; no collective on the data path.
 """
@@ -192,25 +202,76 @@ def e2e_pipelined(g, roots, opts, n: int, steps: int, stream, copy_streams: int 
 
 # ------------------------------------------------------------------ CPU oracle (baseline / reference arm)
 
-def oracle_sample(scale: int, nroots: int, repeats: int = 1):
-    """Serial Algorithm 1 on R-MAT `scale` (same generator): (GTEPS hmean, seconds, searches, m)."""
+def host_cpu() -> dict:
+    """nproc and the CPU model of this host (for the CPU lines)."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k = line.split(":")[0].strip().lower()
+                if k in ("model name", "cpu part", "hardware"):
+                    model = model or line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"nproc": os.cpu_count(), "model": model}
+
+
+def oracle_parallel(offsets, cols, roots, threads: int):
+    """Serial Algorithm 1 (the oracle, as it stands), one search per host thread, all
+    `roots` through a pool of `threads` (the C oracle releases the interpreter lock).
+    Returns (wall seconds, per-search seconds)."""
+    import concurrent.futures as cf
     import oracle
-    from graphgen import workloads
-    oracle.build()
-    w = workloads.RMAT[scale]
-    e = w.edges()
-    roots = w.roots(e, nroots).tolist()
-    ref = oracle.build_csr(e.n, e.src, e.dst)
-    del e
-    m = ref.nnz // 2
-    times = []
-    for _ in range(repeats):
-        for r in roots:
-            t0 = time.perf_counter()
-            oracle.bfs_topdown(ref, r)
-            times.append(time.perf_counter() - t0)
-    total = sum(times)
-    return len(times) * m / total / 1e9, total, len(times), m, times
+    ref = oracle.CSR(len(offsets) - 1, offsets, cols)
+
+    def one(r):
+        t0 = time.perf_counter()
+        oracle.bfs_topdown(ref, r)
+        return time.perf_counter() - t0
+
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(threads) as ex:
+        per = list(ex.map(one, roots))
+    return time.perf_counter() - t0, per
+
+
+def cpu_baselines(g, roots, m: int, alpha: int, beta: int) -> tuple[dict, dict]:
+    """CPU comparators on the headline graph itself.  Its CSR is copied from the device
+    (the parity tests prove it equal, bit for bit, to the oracle's own CSR of the same
+    edges), then (1) the serial oracle runs 4 roots, one per host core, and (2) the
+    multithreaded direction-optimizing CPU BFS runs 4 roots on every core."""
+    import cpubfs
+    off, cols = g.csr_host()
+    cpu = host_cpu()
+    k = min(4, len(roots))
+    wall, per = oracle_parallel(off, cols, roots[:k], k)
+    oracle_line = {"value": k * m / wall / 1e9, "unit": "GTEPS", "cores": k, "kind": "oracle",
+                   "per_core_gteps": float(k / sum(p for p in per) * m / 1e9),
+                   "sample": f"serial Algorithm 1 (the oracle) on {k} roots of this graph, one search per host core "
+                             f"at a time ({sum(per):.1f} s of CPU work); graph = the device CSR copied to host",
+                   "nproc": cpu["nproc"], "cpu_model": cpu["model"]}
+    cpubfs.build()
+    times, dups = [], 0
+    for r in roots[:k]:
+        t0 = time.perf_counter()
+        _, _, st = cpubfs.dobfs(off, cols, r, alpha=alpha, beta=beta)
+        times.append(time.perf_counter() - t0)
+        dups += st["duplicates"]
+    mt_line = {"value": k * m / sum(times) / 1e9, "unit": "GTEPS", "cores": cpu["nproc"],
+               "kind": "multithreaded direction-optimizing BFS (OpenMP, the paper's in-node algorithm)",
+               "sample": f"{k} roots of this graph, one search at a time on all {cpu['nproc']} host threads",
+               "ms_per_search": [round(t * 1e3, 1) for t in times], "duplicate_insertions": dups,
+               "cpu_model": cpu["model"]}
+    del off, cols
+    return oracle_line, mt_line
 
 
 def reference_arm(args):
@@ -224,35 +285,31 @@ def reference_arm(args):
     import oracle
     from graphgen import workloads
     oracle.build()
-    # sample scale chosen so that (W + K) serial searches take a few minutes on one core
-    scale = args.cpu_scale
-    while scale > 16 and (args.steps + args.warmup) * 1.6 * 2.0 ** (scale - 22) > 150.0:
-        scale -= 1
-    w = workloads.RMAT[scale]
+    w = workloads.RMAT[args.scale]
     e = w.edges()
+    roots = w.roots(e, args.roots).tolist()
+    t0 = time.perf_counter()
     ref = oracle.build_csr(e.n, e.src, e.dst)
-    roots = w.roots(e, 64).tolist()
+    build_s = time.perf_counter() - t0
     del e
     m = ref.nnz // 2
-    for i in range(args.warmup):
-        oracle.bfs_topdown(ref, roots[i % len(roots)])
-    times = []
-    for i in range(args.steps):
-        t0 = time.perf_counter()
-        oracle.bfs_topdown(ref, roots[i % len(roots)])
-        times.append(time.perf_counter() - t0)
-    total = sum(times)
-    value = args.steps * m / total / 1e9
-    sample = (f"serial Algorithm 1 (oracle) on R-MAT scale {scale} (same generator, edge factor 16; "
-              f"1/{2 ** (args.scale - scale)} of the scale-{args.scale} graph), one search per step, "
-              f"{len(roots)} roots cycled")
-    line = {"impl": "reference", "metric": metric_name(args, workloads.RMAT[args.scale]), "value": value,
+    cpu = host_cpu()
+    threads = max(1, min(args.steps, cpu["nproc"] or 1))
+    oracle_parallel(ref.offsets, ref.cols, [roots[i % len(roots)] for i in range(args.warmup)], threads)
+    wall, per = oracle_parallel(ref.offsets, ref.cols, [roots[i % len(roots)] for i in range(args.steps)], threads)
+    value = args.steps * m / wall / 1e9
+    sample = (f"serial Algorithm 1 (the oracle, as it stands) on the R-MAT scale-{args.scale} graph itself "
+              f"(oracle-built CSR, {build_s:.0f} s untimed), one whole search per step, {args.steps} steps through "
+              f"{threads} host threads (one search per core at a time), roots cycled over {len(roots)}")
+    line = {"impl": "reference", "metric": metric_name(args, w), "value": value,
             "unit": "GTEPS", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": total / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": wall / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": f"{workloads.RMAT[args.scale].name} single-source BFS, 64 roots cycled",
-                       "sample_scale": scale, "sample_roots": len(roots), "sample_undirected_edges": m},
-            "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": sample},
+            "config": {"workload": f"{w.name} single-source BFS, {len(roots)} roots cycled",
+                       "n": ref.n, "nnz": ref.nnz, "undirected_edges": m},
+            "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": threads, "kind": "oracle", "sample": sample,
+                             "per_search_s_mean": float(sum(per) / len(per)), "nproc": cpu["nproc"],
+                             "cpu_model": cpu["model"]},
             "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -332,6 +389,78 @@ def batched_section(seed: int = 4242, hub: bool = True) -> dict:
     for gg in gs:
         gg.close()
     gu.close()
+    return out
+
+
+def time_searches(g, roots, opts, n: int, reps: int = 1):
+    """Device time of one search per root (CUDA events around each), levels and parents
+    written; returns (per-search ms list, records of each root from an untimed pass)."""
+    import torch
+    from paper_1705_04590_gb300 import roofline
+    level = torch.empty(n, dtype=torch.int32, device="cuda")
+    parent = torch.empty(n, dtype=torch.int32, device="cuda")
+    bytes_of = []
+    for r in roots:
+        info = g.run(r, parent=parent, level=level, opts=opts, stats=True, record_levels=8192)
+        bytes_of.append(roofline.search_bytes(n, info["records"]))
+    g.run(roots[0], parent=parent, level=level, opts=opts)
+    ms = []
+    for _ in range(reps):
+        for r in roots:
+            a, b = _events(None)
+            torch.cuda.synchronize()
+            a.record()
+            g.run(r, parent=parent, level=level, opts=opts)
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+    return ms, bytes_of * reps
+
+
+def configs_section(peak_gbs: float) -> dict:
+    """Configurations 2 and 3 besides the headline, a few seeded roots each: R-MAT scale
+    24 over CSR and over DCSC column-block tiles, each direction-optimizing, top-down
+    only and bottom-up only; Erdos-Renyi n = 2^26 (E[deg] 16); the 4096 x 4096 torus.
+    GTEPS = edges x searches / summed device time (the harmonic mean over roots);
+    roofline = the byte model over each search's own level records."""
+    import numpy as np
+
+    import paper_1705_04590_gb300 as bfs
+    from graphgen import workloads
+
+    out = {}
+
+    def line(name, g, roots, opts, n, m, reps=1):
+        ms, by = time_searches(g, roots, opts, n, reps)
+        t = sum(ms)
+        out[name] = {"gteps": len(ms) * m / t / 1e6, "ms_per_search": t / len(ms), "roots": len(roots),
+                     "roofline_frac": sum(by) / (t / 1e3) / 1e9 / peak_gbs, "p99_ms": float(np.percentile(ms, 99))}
+
+    w = workloads.RMAT[24]
+    e = w.edges()
+    roots = w.roots(e, 4).tolist()
+    g = bfs.Graph.from_edges(e.src, e.dst, e.n, dcsc=True, hub_first=True)
+    n, m = e.n, g.nnz // 2
+    del e
+    for mode, mname in ((bfs.MODE_DO, "do"), (bfs.MODE_TD_ONLY, "td"), (bfs.MODE_BU_ONLY, "bu")):
+        line(f"rmat24_csr_{mname}", g, roots, bfs.options(mode=mode, bu_rows=bfs.BU_ROWS_HUB_FIRST), n, m)
+        line(f"rmat24_csr_idrows_{mname}", g, roots, bfs.options(mode=mode), n, m)
+        line(f"rmat24_dcsc_{mname}", g, roots[:2], bfs.options(mode=mode, layout=bfs.LAYOUT_DCSC_TILED), n, m)
+    g.close()
+    e = workloads.ER26.edges()
+    roots = workloads.ER26.roots(e, 8).tolist()
+    g = bfs.Graph.from_edges(e.src, e.dst, e.n, hub_first=True)
+    n, m = e.n, g.nnz // 2
+    del e
+    line("er26_do", g, roots, bfs.options(bu_rows=bfs.BU_ROWS_HUB_FIRST), n, m)
+    g.close()
+    e = workloads.TORUS4096.edges()
+    roots = workloads.TORUS4096.roots(e, 4).tolist()
+    g = bfs.Graph.from_edges(e.src, e.dst, e.n, hub_first=True)
+    n, m = e.n, g.nnz // 2
+    del e
+    line("torus4096_do", g, roots, bfs.options(bu_rows=bfs.BU_ROWS_HUB_FIRST), n, m)
+    g.close()
     return out
 
 
@@ -440,12 +569,39 @@ def served_section(g26, roots26, n_queries: int = 2000, seed: int = 5151) -> dic
         return {"wall_s": wall, "qps": len(tr) / wall, "gteps": done_m / wall / 1e9,
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))}
 
-    # warm-up and saturated throughput: a burst of queries all at time 0
+    # warm-up and saturated throughput: a burst of queries all at time 0 (its p99 is a queue
+    # of 1024 queries draining, reported on its own)
     run_server(trace(256), np.zeros(256))
     sat = run_server(trace(1024), np.zeros(1024))
-    out = {"graphs": [nme for nme, _ in specs], "saturated": sat, "loads": []}
+    # the sustained capacity: the highest Poisson rate (searched from below the burst's) at
+    # which the server keeps up, i.e. serves >= 97 % of the offered rate with a p99 under
+    # the target; the offered loads are fractions of it
+    p99_target_ms = 100.0
+    probes = []
+
+    def keeps_up(rate, k=600):
+        tr = trace(k)
+        arr = np.cumsum(rng.exponential(1.0 / rate, k))
+        arr -= arr[0]
+        r = run_server(tr, arr)
+        ok = r["qps"] >= 0.97 * rate and r["p99_ms"] <= p99_target_ms
+        probes.append({"offered_qps": rate, "served_qps": r["qps"], "p99_ms": r["p99_ms"], "keeps_up": ok})
+        return ok
+
+    lo, hi = 0.0, None
+    rate = 0.5 * sat["qps"]
+    for _ in range(6):
+        if keeps_up(rate):
+            lo = rate
+            rate = rate * 1.3 if hi is None else 0.5 * (rate + hi)
+        else:
+            hi = rate
+            rate = 0.5 * (lo + rate) if lo > 0 else 0.5 * rate
+    capacity = lo if lo > 0 else 0.25 * sat["qps"]
+    out = {"graphs": [nme for nme, _ in specs], "saturated": sat, "sustained_capacity_qps": capacity,
+           "p99_target_ms": p99_target_ms, "capacity_probes": probes, "loads": []}
     for frac in (0.25, 0.5, 0.9):
-        rate = frac * sat["qps"]
+        rate = frac * capacity
         tr = trace(n_queries)
         arrivals = np.cumsum(rng.exponential(1.0 / rate, n_queries))
         arrivals -= arrivals[0]
@@ -560,18 +716,29 @@ def our_arm(args):
                 and args.layout == "csr" and args.mode == "do" and tr.get("bu_rows", "id") == args.bu_rows:
             traffic = tr.get("dram_bytes_per_launch")
 
-    batched = served = None
+    # the autotuner's choice (direction thresholds, hub cut-off, top-down chunk, CTAs per
+    # SM) on 4 sample roots, timed over the same steps as the headline
+    tuned = None
+    if rank == 0 and not args.no_tuned and args.layout == "csr":
+        from paper_1705_04590_gb300 import autotune
+        best, _ = autotune.autotune(g, roots[:4], base=opts)
+        t_ms, t_bytes = time_searches(g, [roots[i % len(roots)] for i in range(args.steps)], best, n)
+        tuned = {"alpha": best.alpha, "beta": best.beta, "td_big_degree": best.td_big_degree,
+                 "td_chunk": best.td_chunk, "ctas_per_sm": best.ctas_per_sm,
+                 "value": args.steps * m / sum(t_ms) / 1e6, "unit": "GTEPS", "ms_per_step": sum(t_ms) / args.steps,
+                 "roofline_frac": sum(t_bytes) / (sum(t_ms) / 1e3) / 1e9 / peaks["hbm_gbs"],
+                 "note": "same roots and outputs as the headline, CUDA events per search; the headline keeps "
+                         "the configured alpha 14 / beta 24"}
+
+    batched = served = configs = None
     if rank == 0 and not args.no_batched:
         batched = batched_section(hub=(args.bu_rows == "hub"))
     if rank == 0 and not args.no_served:
         served = served_section(g, roots, n_queries=args.served_queries)
 
-    cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
-        gteps, secs, cnt, m_s, _ = oracle_sample(args.cpu_scale, 8)
-        cpu = {"value": gteps, "unit": "GTEPS", "cores": 1, "kind": "oracle",
-               "sample": f"serial Algorithm 1 (oracle, one host core) on R-MAT scale {args.cpu_scale} "
-                         f"(same generator; {m_s} undirected edges), {cnt} roots, {secs:.1f} s of CPU work"}
+    cpu = cpu_mt = None
+    if rank == 0 and not args.no_cpu_baseline and args.layout == "csr":
+        cpu, cpu_mt = cpu_baselines(g, roots, m, 14, 24)
 
     if rank == 0:
         line = {
@@ -598,12 +765,19 @@ def our_arm(args):
             "gpu_launches": args.steps,
             "clocks": clocks,
             "cpu_baseline": cpu,
+            "cpu_multithreaded": cpu_mt,
+            "tuned": tuned,
             "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
             "batched": batched,
             "served": served,
         }
+        if not args.no_configs and args.workload == "rmat" and args.scale == 26:
+            g.close()
+            g = None
+            line["configs"] = configs_section(peaks["hbm_gbs"])
         print(json.dumps(line), flush=True)
-    g.close()
+    if g is not None:
+        g.close()
     if ws > 1:
         dist.destroy_process_group()
     return 0
@@ -622,10 +796,12 @@ def main():
     ap.add_argument("--bu-rows", default="hub", choices=["hub", "id"],
                     help="row order of the bottom-up scans: hub-first copy (default) or the id-sorted rows")
     ap.add_argument("--roots", type=int, default=64)
-    ap.add_argument("--cpu-scale", type=int, default=22)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched multi-source section")
     ap.add_argument("--no-served", action="store_true", help="skip the served section")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the configurations besides the headline (R-MAT 24 CSR/DCSC x DO/TD/BU, ER 2^26, torus)")
+    ap.add_argument("--no-tuned", action="store_true", help="skip the autotuned line")
     ap.add_argument("--served-queries", type=int, default=2000, help="queries per offered load")
     args = ap.parse_args()
     if args.warmup < 3:

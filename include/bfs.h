@@ -104,12 +104,15 @@ typedef struct {
                               shared by all warps (0 = tuned default) */
     int64_t timeout_ms;    /* limit of every device-side wait; 0 = default 10000 */
     uint64_t seed;         /* BFS_MODE_RANDOM only */
-    int32_t debug_barrier_extra; /* testing only: every grid barrier waits for this many arrivals that
-                                    never come, so each wait runs out after timeout_ms (0 = off) */
     int32_t bu_rows;       /* order in which bottom-up steps scan a row: BFS_BU_ROWS_BY_ID (stored order,
                               the paper's) or BFS_BU_ROWS_HUB_FIRST (needs BFS_FLAG_BUILD_HUB_FIRST, the
                               CSR layout and BFS_PARENT_ANY).  Levels are the same; the bottom-up
                               examination counts and the parents chosen follow the order */
+    int32_t td_chunk;      /* top-down: edges per chunk task of a vertex above td_big_degree, 64..4096
+                              (0 = tuned default 256) */
+    int32_t ctas_per_sm;   /* CTAs per SM of the persistent single-source launch, 1 .. the resident
+                              maximum (0 = the maximum); fewer means fewer arrivals per grid barrier */
+    int32_t reserved;      /* must be 0 */
 } bfs_options;
 
 #define BFS_BU_ROWS_BY_ID     0
@@ -159,6 +162,17 @@ typedef struct {
 bfs_status bfs_graph_create_from_edges(const int32_t* src, const int32_t* dst, int64_t n_edges,
                                        int64_t n_vertices, uint32_t flags, const bfs_allocator* alloc,
                                        void* stream, bfs_graph** out);
+
+/*
+ * The same with 64-bit endpoint arrays (the paper stores 64-bit vertex ids):
+ * src[i], dst[i] must lie in [0, n_vertices), n_vertices <= 2^31 - 1 (ids are
+ * int32 on the device).  The arrays are narrowed to int32 in chunks (on the
+ * host, or with BFS_FLAG_DEVICE_PTRS on the device after a range check);
+ * an id out of range gives INVALID.  Otherwise as above.
+ */
+bfs_status bfs_graph_create_from_edges64(const int64_t* src, const int64_t* dst, int64_t n_edges,
+                                         int64_t n_vertices, uint32_t flags, const bfs_allocator* alloc,
+                                         void* stream, bfs_graph** out);
 
 /*
  * Build a graph from a CSR that is already undirected: row_offsets[n+1]
@@ -331,20 +345,33 @@ bfs_status bfs_run_csr_noalloc(const int64_t* row_offsets, const int32_t* col_id
                                int32_t root, int32_t* parent_dev, int32_t* level_dev, void* stream);
 
 /*
- * Autotuner: times bfs_run on `k` sample roots (roots_host) for a small grid
- * of direction thresholds (alpha, beta) and top-down hub cut-offs
- * (td_big_degree), each configuration once for warm-up and once timed with
- * CUDA events, and writes the fastest into *best (other fields from `base`,
- * or the defaults when base is NULL).  Levels do not depend on these choices
+ * Autotuner: times bfs_run (both outputs written) on `k` sample roots
+ * (roots_host) for a grid of direction thresholds alpha in {6,14,24,32,96},
+ * beta in {12,24,64,128} and top-down hub cut-offs td_big_degree in
+ * {64,96,256}; then, from the winner, the top-down chunk size td_chunk in
+ * {128,256,512,1024} and then ctas_per_sm in {1, the maximum}, one knob at a
+ * time.  Each configuration runs once for warm-up, then the k roots timed with
+ * CUDA events; the fastest mean goes to *best (other fields from `base`, or
+ * the defaults when base is NULL).  Levels do not depend on these choices
  * ("Parallel Direction-Optimizing BFS": the heuristic only picks the cheaper
- * direction).  Synchronises `stream`; *best_ms receives the winner's mean
- * time per search (may be NULL).  Errors: INVALID, CUDA, TIMEOUT.
+ * direction; the launch knobs only split the work).  Synchronises `stream`;
+ * *best_ms receives the winner's mean time per search (may be NULL).  Errors:
+ * INVALID, CUDA, TIMEOUT.
  */
 bfs_status bfs_autotune(bfs_graph* g, const int32_t* roots_host, int32_t k, const bfs_options* base,
                         bfs_options* best, double* best_ms, void* stream);
 
 /* Wait for the graph's enqueued searches; returns the first device-side error since the last sync. */
 bfs_status bfs_graph_sync(bfs_graph* g, void* stream);
+
+/*
+ * Testing only (failure detection without a fault): every grid barrier of the
+ * graph's later searches waits for `extra` arrivals that never come, so each
+ * wait runs out after the search's timeout_ms and the search returns
+ * BFS_ERR_TIMEOUT with the device context intact.  0 turns it off.  INVALID
+ * for extra < 0 or a NULL graph.
+ */
+bfs_status bfs_debug_set_barrier_extra(bfs_graph* g, int32_t extra);
 
 /* ----------------------------------------------------------------- server */
 
@@ -365,6 +392,15 @@ bfs_status bfs_graph_sync(bfs_graph* g, void* stream);
  * drives the device; outputs land in caller memory.
  */
 bfs_status bfs_server_create(int64_t hbm_budget_bytes, int32_t max_lanes, bfs_server** out);
+
+/*
+ * The same with an allocator: every device buffer the server owns (per-slot
+ * lane masks, queues and control blocks, the plain-search executors' work
+ * buffers) comes from `alloc` (NULL: cudaMalloc / cudaFree).  The hook must stay
+ * valid until bfs_server_destroy returns.
+ */
+bfs_status bfs_server_create_ex(int64_t hbm_budget_bytes, int32_t max_lanes, const bfs_allocator* alloc,
+                                bfs_server** out);
 
 /* Make `g` servable (the server does not own it; keep it alive until destroy). */
 bfs_status bfs_server_add_graph(bfs_server* s, bfs_graph* g, int32_t* slot);

@@ -10,6 +10,8 @@ Contents (each cites the passage of Bulu\\c{c} et al. 2015 it follows):
 * :func:`build_csr`       -- "Graph Representation" + "Data Sets" (numpy sort/unique)
 * :func:`hub_first`       -- the same rows, neighbours ordered by degree (the row order a
                              bottom-up step may scan in; Algorithm 2 fixes none beyond "in order")
+* :func:`hub_first_rows`  -- the same reordering row by row in C, for graphs too large
+                             for the numpy lexsort (pinned equal to :func:`hub_first`)
 * :func:`bfs_topdown`     -- Algorithm 1, serial FIFO (C)
 * :func:`bfs_bottomup`    -- Algorithm 2, serial (C)
 * :func:`min_parent`      -- (select2nd, min) semiring of the parallel top-down local discovery (C)
@@ -72,6 +74,8 @@ def _load():
         L.or_certify.restype = i64
         L.or_do_schedule.argtypes = [i64, vp, vp, vp, i32, i64, i64, i32] + [vp] * 7
         L.or_do_schedule.restype = i32
+        L.or_hub_first.argtypes = [i64, vp, vp, vp, i64, i64]
+        L.or_hub_first.restype = i32
         _lib = L
     return _lib
 
@@ -166,6 +170,29 @@ def hub_first(g: CSR) -> CSR:
     rows = np.repeat(np.arange(g.n, dtype=np.int64), deg)
     order = np.lexsort((g.cols, -deg[g.cols], rows))
     return CSR(g.n, g.offsets.copy(), np.ascontiguousarray(g.cols[order], np.int32))
+
+
+def hub_first_rows(g: CSR, threads: int = 0) -> CSR:
+    """:func:`hub_first` computed row by row in C (each row sorted on the key
+    (~degree << 32) | id): the same result, with memory for one row of scratch
+    instead of the lexsort's three full-length temporaries.  Rows are
+    independent; ranges of about equal edge count run on `threads` host
+    threads (0: one per core)."""
+    import concurrent.futures as cf
+    out = np.empty(max(g.nnz, 1), np.int32)
+    threads = threads or (os.cpu_count() or 1)
+    parts = max(1, min(4 * threads, g.n))
+    cuts = np.searchsorted(g.offsets, np.linspace(0, g.nnz, parts + 1), side="left")
+    cuts[0], cuts[-1] = 0, g.n
+    lib = _load()
+
+    def run(i):
+        return lib.or_hub_first(g.n, _ptr(g.offsets), _ptr(g.cols), _ptr(out), int(cuts[i]), int(cuts[i + 1]))
+
+    with cf.ThreadPoolExecutor(threads) as ex:
+        if any(r != 0 for r in ex.map(run, range(parts))):
+            raise MemoryError("or_hub_first: scratch allocation failed")
+    return CSR(g.n, g.offsets.copy(), out[: g.nnz])
 
 
 def bfs_topdown(g: CSR, root: int):

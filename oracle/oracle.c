@@ -30,6 +30,10 @@
  *                    Direction-Optimizing BFS"): per level the direction chosen
  *                    by the edges-out-of-frontier / frontier-size heuristics,
  *                    and the per-level work counts that the byte model uses.
+ *  or_hub_first      the rows in the order a bottom-up step may scan them:
+ *                    neighbours by degree, highest first, ties by id (Algorithm
+ *                    2 fixes no order beyond "in order"); each row sorted on
+ *                    its own, for graphs too large for the numpy lexsort.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -287,4 +291,72 @@ int32_t or_do_schedule(int64_t n, const int64_t* off, const int32_t* cols, const
     free(cnt);
     free(deg);
     return L;
+}
+
+/* ------------------------------------------------------------------ hub-first rows */
+
+/*
+ * Rows u0 <= u < u1 of out = the column ids with every row reordered by
+ * (degree descending, id ascending), the same rows in the same place (offsets
+ * unchanged, indices absolute).  Each row is sorted on its own with the key
+ * (~degree << 32) | id, which orders by degree descending and then id
+ * ascending (ids are unique within a row): insertion sort for short rows, a
+ * bottom-up merge sort for long ones.  Disjoint row ranges may run in
+ * parallel.  Returns 0, or -1 if scratch memory could not be allocated.
+ */
+static uint64_t or_hub_key(const int64_t* off, int32_t v) {
+    uint64_t d = (uint64_t)(off[v + 1] - off[v]);
+    if (d > 0xFFFFFFFFull) d = 0xFFFFFFFFull;
+    return ((0xFFFFFFFFull - d) << 32) | (uint32_t)v;
+}
+
+int32_t or_hub_first(int64_t n, const int64_t* off, const int32_t* cols, int32_t* out, int64_t u0, int64_t u1) {
+    (void)n;
+    int64_t maxdeg = 0;
+    for (int64_t u = u0; u < u1; u++)
+        if (off[u + 1] - off[u] > maxdeg) maxdeg = off[u + 1] - off[u];
+    uint64_t* a = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(maxdeg > 0 ? maxdeg : 1));
+    uint64_t* b = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(maxdeg > 0 ? maxdeg : 1));
+    if (!a || !b) {
+        free(a);
+        free(b);
+        return -1;
+    }
+    for (int64_t u = u0; u < u1; u++) {
+        const int64_t s = off[u], len = off[u + 1] - s;
+        for (int64_t k = 0; k < len; k++) a[k] = or_hub_key(off, cols[s + k]);
+        if (len <= 32) {
+            for (int64_t i = 1; i < len; i++) {
+                uint64_t x = a[i];
+                int64_t j = i - 1;
+                while (j >= 0 && a[j] > x) {
+                    a[j + 1] = a[j];
+                    j--;
+                }
+                a[j + 1] = x;
+            }
+        } else {
+            /* bottom-up merge sort, runs of width 1, 2, 4, ... alternating a and b */
+            uint64_t* src = a;
+            uint64_t* dst = b;
+            for (int64_t wdt = 1; wdt < len; wdt *= 2) {
+                for (int64_t lo = 0; lo < len; lo += 2 * wdt) {
+                    int64_t mid = lo + wdt < len ? lo + wdt : len;
+                    int64_t hi = lo + 2 * wdt < len ? lo + 2 * wdt : len;
+                    int64_t i = lo, j = mid, k = lo;
+                    while (i < mid && j < hi) dst[k++] = src[i] <= src[j] ? src[i++] : src[j++];
+                    while (i < mid) dst[k++] = src[i++];
+                    while (j < hi) dst[k++] = src[j++];
+                }
+                uint64_t* t = src;
+                src = dst;
+                dst = t;
+            }
+            if (src != a) memcpy(a, src, sizeof(uint64_t) * (size_t)len);
+        }
+        for (int64_t k = 0; k < len; k++) out[s + k] = (int32_t)(uint32_t)(a[k] & 0xFFFFFFFFull);
+    }
+    free(a);
+    free(b);
+    return 0;
 }

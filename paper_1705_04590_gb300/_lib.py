@@ -29,7 +29,7 @@ class Allocator(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("mode", c_i32), ("layout", c_i32), ("alpha", c_i32), ("beta", c_i32), ("parent_mode", c_i32),
                 ("td_big_degree", c_i32), ("timeout_ms", c_i64), ("seed", c_u64),
-                ("debug_barrier_extra", c_i32), ("bu_rows", c_i32)]
+                ("bu_rows", c_i32), ("td_chunk", c_i32), ("ctas_per_sm", c_i32), ("reserved", c_i32)]
 
 
 class LevelRecord(ctypes.Structure):
@@ -72,6 +72,10 @@ SIGNATURES = [
     ("bfs_autotune", c_i32, [c_vp, c_vp, c_i32, ctypes.POINTER(Options), ctypes.POINTER(Options),
                              ctypes.POINTER(ctypes.c_double), c_vp]),
     ("bfs_graph_sync", c_i32, [c_vp, c_vp]),
+    ("bfs_debug_set_barrier_extra", c_i32, [c_vp, c_i32]),
+    ("bfs_graph_create_from_edges64", c_i32, [c_vp, c_vp, c_i64, c_i64, c_u32, ctypes.POINTER(Allocator), c_vp,
+                                              ctypes.POINTER(c_vp)]),
+    ("bfs_server_create_ex", c_i32, [c_i64, c_i32, ctypes.POINTER(Allocator), ctypes.POINTER(c_vp)]),
     ("bfs_server_create", c_i32, [c_i64, c_i32, ctypes.POINTER(c_vp)]),
     ("bfs_server_add_graph", c_i32, [c_vp, c_vp, ctypes.POINTER(c_i32)]),
     ("bfs_submit", c_i32, [c_vp, c_i32, c_i32, c_vp, ctypes.POINTER(c_u64)]),

@@ -67,13 +67,12 @@ class _TorchAllocator:
 
 def options(mode: int = L.MODE_DO, layout: int = L.LAYOUT_CSR, alpha: int = 14, beta: int = 24,
             parent_mode: int = L.PARENT_ANY, td_big_degree: int = 0, timeout_ms: int = 10000, seed: int = 0,
-            debug_barrier_extra: int = 0, bu_rows: int = L.BU_ROWS_BY_ID) -> L.Options:
+            bu_rows: int = L.BU_ROWS_BY_ID, td_chunk: int = 0, ctas_per_sm: int = 0) -> L.Options:
     o = L.Options()
     L.load().bfs_options_default(ctypes.byref(o))
     o.mode, o.layout, o.alpha, o.beta, o.parent_mode = mode, layout, alpha, beta, parent_mode
-    o.td_big_degree, o.timeout_ms, o.seed, o.debug_barrier_extra = td_big_degree, timeout_ms, seed, \
-        debug_barrier_extra
-    o.bu_rows = bu_rows
+    o.td_big_degree, o.timeout_ms, o.seed = td_big_degree, timeout_ms, seed
+    o.bu_rows, o.td_chunk, o.ctas_per_sm = bu_rows, td_chunk, ctas_per_sm
     return o
 
 
@@ -92,7 +91,8 @@ class Graph:
     @classmethod
     def from_edges(cls, src, dst, n: int, dcsc: bool = False, stream=None, torch_allocator: bool = True,
                    hub_first: bool = False) -> "Graph":
-        """src/dst: numpy int32 arrays (host) or int32 CUDA tensors (device).  hub_first also
+        """src/dst: numpy int32 or int64 arrays (host) or CUDA tensors of either type (device;
+        64-bit ids go through bfs_graph_create_from_edges64).  hub_first also
         stores rows ordered by neighbour degree and a 32-byte head per vertex (its degree and
         first 7 reordered ids), 4*nnz + 32*n more device bytes, for bottom-up option
         bu_rows=BU_ROWS_HUB_FIRST."""
@@ -102,21 +102,25 @@ class Graph:
         if isinstance(src, torch.Tensor):
             if src.numel() != dst.numel():
                 raise ValueError("src and dst differ in length")
-            ps, pd = _dev_ptr(src, "int32", what="src"), _dev_ptr(dst, "int32", what="dst")
+            wide = src.dtype == torch.int64
+            ty = "int64" if wide else "int32"
+            ps, pd = _dev_ptr(src, ty, what="src"), _dev_ptr(dst, ty, what="dst")
             flags |= L.FLAG_DEVICE_PTRS
             m = src.numel()
             keep = (src, dst)
         else:
-            src = np.ascontiguousarray(src, np.int32)
-            dst = np.ascontiguousarray(dst, np.int32)
+            wide = np.asarray(src).dtype == np.int64
+            src = np.ascontiguousarray(src, np.int64 if wide else np.int32)
+            dst = np.ascontiguousarray(dst, np.int64 if wide else np.int32)
             if src.shape != dst.shape:
                 raise ValueError("src and dst differ in length")
             ps, pd, m, keep = src.ctypes.data, dst.ctypes.data, int(src.shape[0]), (src, dst)
         alloc = _TorchAllocator() if torch_allocator else None
         h = ctypes.c_void_p()
-        st = lib.bfs_graph_create_from_edges(ps, pd, m, n, flags, ctypes.byref(alloc.struct) if alloc else None,
-                                             _stream_ptr(stream), ctypes.byref(h))
-        L.check(st, "bfs_graph_create_from_edges")
+        create = lib.bfs_graph_create_from_edges64 if wide else lib.bfs_graph_create_from_edges
+        st = create(ps, pd, m, n, flags, ctypes.byref(alloc.struct) if alloc else None, _stream_ptr(stream),
+                    ctypes.byref(h))
+        L.check(st, "bfs_graph_create_from_edges64" if wide else "bfs_graph_create_from_edges")
         del keep
         return cls(h.value, alloc)
 
@@ -286,10 +290,17 @@ class Server:
     join the running multi-source search of their graph at the next level.
     """
 
-    def __init__(self, hbm_budget_bytes: int, max_lanes: int = 64):
+    def __init__(self, hbm_budget_bytes: int, max_lanes: int = 64, allocator=None):
+        """allocator: None (the library's cudaMalloc), True (PyTorch's caching allocator) or
+        an object with a `struct` attribute holding a bfs_allocator (kept alive here)."""
         lib = L.load()
         h = ctypes.c_void_p()
-        L.check(lib.bfs_server_create(int(hbm_budget_bytes), int(max_lanes), ctypes.byref(h)), "bfs_server_create")
+        if allocator is True:
+            allocator = _TorchAllocator()
+        self._alloc = allocator
+        L.check(lib.bfs_server_create_ex(int(hbm_budget_bytes), int(max_lanes),
+                                         ctypes.byref(allocator.struct) if allocator else None, ctypes.byref(h)),
+                "bfs_server_create_ex")
         self._h = h
         self._graphs = []
         self._outs = {}

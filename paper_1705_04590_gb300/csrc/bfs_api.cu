@@ -108,7 +108,10 @@ static bfs_status check_options(const bfs_options* in, bfs_options* out, const b
         return fail(BFS_ERR_INVALID, "options.parent_mode must be a BFS_PARENT_* value");
     if (out->timeout_ms < 0) return fail(BFS_ERR_INVALID, "options.timeout_ms must be >= 0");
     if (out->td_big_degree != 0 && out->td_big_degree < 64) out->td_big_degree = 64;
-    if (out->debug_barrier_extra < 0) return fail(BFS_ERR_INVALID, "options.debug_barrier_extra must be >= 0");
+    if (out->td_chunk != 0 && (out->td_chunk < 64 || out->td_chunk > 4096))
+        return fail(BFS_ERR_INVALID, "options.td_chunk must be 0 or lie in [64, 4096]");
+    if (out->ctas_per_sm < 0) return fail(BFS_ERR_INVALID, "options.ctas_per_sm must be >= 0");
+    if (out->reserved != 0) return fail(BFS_ERR_INVALID, "options.reserved must be 0");
     if (out->bu_rows != BFS_BU_ROWS_BY_ID && out->bu_rows != BFS_BU_ROWS_HUB_FIRST)
         return fail(BFS_ERR_INVALID, "options.bu_rows must be a BFS_BU_ROWS_* value");
     if (out->bu_rows == BFS_BU_ROWS_HUB_FIRST) {
@@ -165,6 +168,30 @@ bfs_status bfs_graph_create_from_edges(const int32_t* src, const int32_t* dst, i
     if (st != BFS_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     st = build_csr_from_edges(g, src, dst, n_edges, (flags & BFS_FLAG_DEVICE_PTRS) != 0, s);
+    if (st == BFS_OK && (flags & BFS_FLAG_BUILD_DCSC)) st = build_dcsc_tiles(g, s);
+    if (st == BFS_OK && (flags & BFS_FLAG_BUILD_HUB_FIRST)) st = build_hub_first_rows(g, s);
+    if (st != BFS_OK) {
+        std::string msg = bfs_last_error();
+        destroy_graph(g);
+        set_error(msg);
+        return st;
+    }
+    *out = g;
+    return BFS_OK;
+}
+
+bfs_status bfs_graph_create_from_edges64(const int64_t* src, const int64_t* dst, int64_t n_edges, int64_t n_vertices,
+                                         uint32_t flags, const bfs_allocator* alloc, void* stream, bfs_graph** out) {
+    if (out) *out = nullptr;
+    if (n_edges < 0) return fail(BFS_ERR_INVALID, "n_edges must be >= 0");
+    if (n_edges > 0 && (!src || !dst)) return fail(BFS_ERR_INVALID, "src/dst must not be NULL");
+    if (!(flags & BFS_FLAG_SYMMETRIZE))
+        return fail(BFS_ERR_UNSUPPORTED, "only undirected graphs are supported: pass BFS_FLAG_SYMMETRIZE");
+    bfs_graph* g = nullptr;
+    bfs_status st = new_graph(n_vertices, alloc, &g);
+    if (st != BFS_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    st = build_csr_from_edges64(g, src, dst, n_edges, (flags & BFS_FLAG_DEVICE_PTRS) != 0, s);
     if (st == BFS_OK && (flags & BFS_FLAG_BUILD_DCSC)) st = build_dcsc_tiles(g, s);
     if (st == BFS_OK && (flags & BFS_FLAG_BUILD_HUB_FIRST)) st = build_hub_first_rows(g, s);
     if (st != BFS_OK) {
@@ -375,40 +402,64 @@ bfs_status bfs_autotune(bfs_graph* g, const int32_t* roots_host, int32_t k, cons
         g->mem.release(tlev, ob, s);
         return fail(BFS_ERR_OOM, "autotune: output buffers");
     }
-    static const int alphas[] = {6, 14, 32, 96};
-    static const int betas[] = {12, 24, 64};
+    static const int alphas[] = {6, 14, 24, 32, 96};
+    static const int betas[] = {12, 24, 64, 128};
     static const int bigs[] = {64, 96, 256};
+    static const int chunks[] = {128, 256, 512, 1024};
+    static const int ctas[] = {1, 0};   // 1 CTA per SM, or as many as fit
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     BFS_CUDA_TRY(cudaEventCreate(&e0));
     BFS_CUDA_TRY(cudaEventCreate(&e1));
     double best_t = -1.0;
     bfs_options win = o0;
+    // mean ms per search of `o` over the sample roots (one warm-up search first)
+    auto trial = [&](const bfs_options& o) -> double {
+        st = run_common(g, roots_host, 1, tpar, tlev, &o, stream, nullptr);
+        if (st != BFS_OK) return -1.0;
+        if (cudaEventRecord(e0, s) != cudaSuccess) { st = BFS_ERR_CUDA; return -1.0; }
+        for (int32_t i = 0; i < k && st == BFS_OK; i++) st = run_common(g, roots_host + i, 1, tpar, tlev, &o, stream, nullptr);
+        if (st != BFS_OK) return -1.0;
+        if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+            st = BFS_ERR_CUDA;
+            return -1.0;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        return ms / k;
+    };
+    auto consider = [&](const bfs_options& o) {
+        const double per = trial(o);
+        if (per >= 0 && (best_t < 0 || per < best_t)) {
+            best_t = per;
+            win = o;
+        }
+    };
+    // the direction thresholds and the hub cut-off on a grid, then the launch knobs one at a time
     for (int a : alphas)
         for (int b : betas)
             for (int big : bigs) {
+                if (st != BFS_OK) break;
                 bfs_options o = o0;
                 o.mode = BFS_MODE_DO;
                 o.alpha = a;
                 o.beta = b;
                 o.td_big_degree = big;
-                st = run_common(g, roots_host, 1, tpar, tlev, &o, stream, nullptr);   // warm-up
-                if (st != BFS_OK) break;
-                if (cudaEventRecord(e0, s) != cudaSuccess) { st = BFS_ERR_CUDA; break; }
-                for (int32_t i = 0; i < k && st == BFS_OK; i++)
-                    st = run_common(g, roots_host + i, 1, tpar, tlev, &o, stream, nullptr);
-                if (st != BFS_OK) break;
-                if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
-                    st = BFS_ERR_CUDA;
-                    break;
-                }
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                const double per = ms / k;
-                if (best_t < 0 || per < best_t) {
-                    best_t = per;
-                    win = o;
-                }
+                consider(o);
             }
+    const bfs_options grid_win = win;
+    for (int c : chunks) {
+        if (st != BFS_OK) break;
+        bfs_options o = grid_win;
+        o.td_chunk = c;
+        consider(o);
+    }
+    const bfs_options chunk_win = win;
+    for (int c : ctas) {
+        if (st != BFS_OK) break;
+        bfs_options o = chunk_win;
+        o.ctas_per_sm = c;
+        consider(o);
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaStreamSynchronize(s);
@@ -419,6 +470,14 @@ bfs_status bfs_autotune(bfs_graph* g, const int32_t* roots_host, int32_t k, cons
     if (st != BFS_OK) return st;
     *best = win;
     if (best_ms) *best_ms = best_t;
+    return BFS_OK;
+}
+
+bfs_status bfs_debug_set_barrier_extra(bfs_graph* g, int32_t extra) {
+    if (!g) return fail(BFS_ERR_INVALID, "graph handle is NULL");
+    if (extra < 0) return fail(BFS_ERR_INVALID, "extra must be >= 0");
+    std::lock_guard<std::mutex> lk(g->run_mu);
+    g->debug_barrier_extra = extra;
     return BFS_OK;
 }
 

@@ -34,6 +34,7 @@ struct DeviceAlloc {
 
 // Per-graph buffers of the single-source search, reused by every run.
 struct SingleWork {
+    DeviceAlloc* mem = nullptr;    // allocator of these buffers (null: the graph's)
     bool ready = false;
     unsigned* visited = nullptr;   // [W]
     unsigned* front0 = nullptr;    // [W]
@@ -58,6 +59,7 @@ struct SingleWork {
 // Buffers of one multi-source (64-lane) search state: bfs_run_multi's own,
 // and one per graph slot of a server.
 struct MultiWork {
+    DeviceAlloc* mem = nullptr;    // allocator of these buffers (null: the graph's)
     bool ready = false;
     unsigned long long* seen = nullptr;   // [n] lane masks
     unsigned long long* front = nullptr;  // [n]
@@ -103,6 +105,8 @@ struct bfs_graph {
     int32_t* bu_first = nullptr;
     uint8_t* deg8 = nullptr;        // [n + 32] min(deg(v), 255)
     int64_t W = 0;                  // bitmap words
+    int64_t n_active = 0;           // vertices with degree > 0
+    int32_t debug_barrier_extra = 0;   // testing: arrivals every grid barrier waits for in vain
     size_t graph_bytes = 0;
     bfsrt::DeviceAlloc mem;
     bfsrt::SingleWork single;
@@ -118,6 +122,12 @@ struct bfs_graph {
 
 namespace bfsrt {
 
+// the allocator a work-buffer set draws from: its own (a server's) or the graph's
+template <typename Work>
+inline DeviceAlloc& mem_of(bfs_graph* g, Work& w) {
+    return w.mem ? *w.mem : g->mem;
+}
+
 constexpr int64_t kColPad = 32;  // readable slack after col_ids (vector loads past the last row)
 
 // graph_build.cu
@@ -125,6 +135,8 @@ bfs_status build_csr_from_edges(bfs_graph* g, const int32_t* src, const int32_t*
                                 bool device_ptrs, cudaStream_t s);
 bfs_status build_csr_from_csr(bfs_graph* g, const int64_t* off, const int32_t* cols, bool device_ptrs,
                               bool check_symmetry, cudaStream_t s);
+bfs_status build_csr_from_edges64(bfs_graph* g, const int64_t* src, const int64_t* dst, int64_t m, bool device_ptrs,
+                                  cudaStream_t s);
 bfs_status build_isolated_bitmap(bfs_graph* g, cudaStream_t s);
 bfs_status build_dcsc_tiles(bfs_graph* g, cudaStream_t s);
 bfs_status build_hub_first_rows(bfs_graph* g, cudaStream_t s);   // hub_first.cu

@@ -613,15 +613,15 @@ bfs_status multi_alloc(bfs_graph* g, MultiWork& w, cudaStream_t s) {
     if (w.ready) return BFS_OK;
     const size_t nb = mask_bytes(g);
     const long long task_cap = g->nnz / bfsk::kMChunk + g->nnz / 256 + 1024;
-    w.seen = (unsigned long long*)g->mem.alloc(nb, s);
-    w.front = (unsigned long long*)g->mem.alloc(nb, s);
-    w.next = (unsigned long long*)g->mem.alloc(nb, s);
-    w.ctrl = g->mem.alloc(sizeof(MCtrl), s);
-    w.tasks = g->mem.alloc(sizeof(MTask) * (size_t)task_cap, s);
-    w.hubmask = g->mem.alloc(sizeof(unsigned long long) * (size_t)task_cap, s);
-    w.lanes = g->mem.alloc(sizeof(bfsk::LaneTable), s);
-    w.q0 = (int*)g->mem.alloc(sizeof(int) * (size_t)(g->n + 64), s);
-    w.q1 = (int*)g->mem.alloc(sizeof(int) * (size_t)(g->n + 64), s);
+    w.seen = (unsigned long long*)mem_of(g, w).alloc(nb, s);
+    w.front = (unsigned long long*)mem_of(g, w).alloc(nb, s);
+    w.next = (unsigned long long*)mem_of(g, w).alloc(nb, s);
+    w.ctrl = mem_of(g, w).alloc(sizeof(MCtrl), s);
+    w.tasks = mem_of(g, w).alloc(sizeof(MTask) * (size_t)task_cap, s);
+    w.hubmask = mem_of(g, w).alloc(sizeof(unsigned long long) * (size_t)task_cap, s);
+    w.lanes = mem_of(g, w).alloc(sizeof(bfsk::LaneTable), s);
+    w.q0 = (int*)mem_of(g, w).alloc(sizeof(int) * (size_t)(g->n + 64), s);
+    w.q1 = (int*)mem_of(g, w).alloc(sizeof(int) * (size_t)(g->n + 64), s);
     w.task_cap = task_cap;
     if (!w.seen || !w.front || !w.next || !w.ctrl || !w.tasks || !w.hubmask || !w.lanes || !w.q0 || !w.q1) {
         w.ready = true;
@@ -644,16 +644,18 @@ bfs_status multi_alloc(bfs_graph* g, MultiWork& w, cudaStream_t s) {
 void multi_free(bfs_graph* g, MultiWork& w) {
     if (!w.ready) return;
     const size_t nb = mask_bytes(g);
-    g->mem.release(w.seen, nb, nullptr);
-    g->mem.release(w.front, nb, nullptr);
-    g->mem.release(w.next, nb, nullptr);
-    g->mem.release(w.ctrl, sizeof(MCtrl), nullptr);
-    g->mem.release(w.tasks, sizeof(MTask) * (size_t)w.task_cap, nullptr);
-    g->mem.release(w.hubmask, sizeof(unsigned long long) * (size_t)w.task_cap, nullptr);
-    g->mem.release(w.lanes, sizeof(bfsk::LaneTable), nullptr);
-    g->mem.release(w.q0, sizeof(int) * (size_t)(g->n + 64), nullptr);
-    g->mem.release(w.q1, sizeof(int) * (size_t)(g->n + 64), nullptr);
+    mem_of(g, w).release(w.seen, nb, nullptr);
+    mem_of(g, w).release(w.front, nb, nullptr);
+    mem_of(g, w).release(w.next, nb, nullptr);
+    mem_of(g, w).release(w.ctrl, sizeof(MCtrl), nullptr);
+    mem_of(g, w).release(w.tasks, sizeof(MTask) * (size_t)w.task_cap, nullptr);
+    mem_of(g, w).release(w.hubmask, sizeof(unsigned long long) * (size_t)w.task_cap, nullptr);
+    mem_of(g, w).release(w.lanes, sizeof(bfsk::LaneTable), nullptr);
+    mem_of(g, w).release(w.q0, sizeof(int) * (size_t)(g->n + 64), nullptr);
+    mem_of(g, w).release(w.q1, sizeof(int) * (size_t)(g->n + 64), nullptr);
+    DeviceAlloc* keep = w.mem;   // the allocator choice outlives the buffers
     w = MultiWork();
+    w.mem = keep;
 }
 
 bfs_status multi_prepare(bfs_graph* g, cudaStream_t s) { return multi_alloc(g, g->multi, s); }
@@ -685,7 +687,7 @@ static MultiParams multi_params(bfs_graph* g, MultiWork& w, const bfs_options& o
     p.beta = opt.beta;
     p.big_deg = opt.td_big_degree > 0 ? opt.td_big_degree : 256;
     p.timeout_ns = (unsigned long long)(opt.timeout_ms > 0 ? opt.timeout_ms : 10000) * 1000000ull;
-    p.expected = (unsigned)w.grid + (unsigned)(opt.debug_barrier_extra > 0 ? opt.debug_barrier_extra : 0);
+    p.expected = (unsigned)w.grid + (unsigned)(g->debug_barrier_extra > 0 ? g->debug_barrier_extra : 0);
     return p;
 }
 

@@ -47,7 +47,8 @@ namespace bfsk {
 constexpr int kBlock = BFS_BLOCK;  // CSR kernel
 constexpr int kDBlock = 1024;   // DCSC kernel (one CTA per vertex block)
 constexpr int kWarps = 32;      // shared-memory per-warp arrays sized for up to 1024 threads
-constexpr int kChunk = 256;    // edges per top-down chunk task
+constexpr int kChunk = 256;    // default edges per top-down chunk task (options.td_chunk)
+constexpr int kMinChunk = 64;  // smallest chunk task: the task lists are sized for it
 constexpr int kStage = 256;    // per-warp shared-memory staging of next-queue entries
 constexpr long long kPrefetchNf = 1 << 16;   // top-down levels below this prefetch the next rows
 #ifndef BFS_TD_CHECK
@@ -102,6 +103,7 @@ struct SingleParams {
     int root0;     // the root when nroots == 1
     int nroots;    // > 1: roots already copied into queue0[0..nroots)
     int mode, alpha, beta, parent_mode, big_deg;
+    int td_chunk;      // edges per top-down chunk task (>= kMinChunk)
     unsigned long long seed;
     unsigned long long timeout_ns;
     unsigned expected;
@@ -191,18 +193,6 @@ __device__ __forceinline__ unsigned ld_stream_u8(const unsigned char* a) {
     return v;
 #else
     return __ldg(a);
-#endif
-}
-
-// Bring a 128-byte line into L2 ahead of its use, marked evict-first like the
-// streamed loads that will read it.
-__device__ __forceinline__ void prefetch_l2_line(const void* a) {
-#if BFS_EVICT
-    asm volatile("cp.async.bulk.prefetch.L2.global.L2::cache_hint [%0], 128, %1;" ::"l"(a),
-                 "l"(evict_first_policy())
-                 : "memory");
-#else
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], 128;" ::"l"(a) : "memory");
 #endif
 }
 
@@ -309,6 +299,13 @@ __device__ void materialise(const SingleParams& p) {
         const bool full = v0 + 8 <= p.n;
         const unsigned valid = full ? 0xFFu : ((1u << (unsigned)(p.n - v0)) - 1u);
         const uint2 lb = __ldcg(reinterpret_cast<const uint2*>(p.lv8 + v0));
+        // most sectors hold a first-probe hit: load its plane values together with
+        // the staged bytes instead of after them
+        int4 fa = make_int4(-1, -1, -1, -1), fb = fa;
+        if (p.parent && p.pfirst && p.first) {
+            fa = ld_stream4(reinterpret_cast<const int4*>(p.first + v0));
+            fb = ld_stream4(reinterpret_cast<const int4*>(p.first + v0) + 1);
+        }
         unsigned reached = 0, deep = 0;
         int lv[8];
 #pragma unroll
@@ -337,11 +334,9 @@ __device__ void materialise(const SingleParams& p) {
 #pragma unroll
             for (int k = 0; k < 8; k++) f[k] = q[k] = -1;
             if (pf) {
-                const int4 a = ld_stream4(reinterpret_cast<const int4*>(p.first + v0));
-                const int4 b = ld_stream4(reinterpret_cast<const int4*>(p.first + v0) + 1);
                 const int m = 0x7FFFFFFF;   // bit 31 flags a row that goes on
-                f[0] = a.x & m; f[1] = a.y & m; f[2] = a.z & m; f[3] = a.w & m;
-                f[4] = b.x & m; f[5] = b.y & m; f[6] = b.z & m; f[7] = b.w & m;
+                f[0] = fa.x & m; f[1] = fa.y & m; f[2] = fa.z & m; f[3] = fa.w & m;
+                f[4] = fb.x & m; f[5] = fb.y & m; f[6] = fb.z & m; f[7] = fb.w & m;
             }
             if (direct) {
                 if (pvec && full) {
@@ -562,7 +557,7 @@ __device__ void td_phase(const SingleParams& p, int d, const int* qcur, long lon
             bm &= bm - 1;
             const long long bs = __shfl_sync(kFull, s, L), be = __shfl_sync(kFull, e, L);
             const int bu = __shfl_sync(kFull, u, L);
-            const long long nch = (be - bs + kChunk - 1) / kChunk;
+            const long long nch = (be - bs + p.td_chunk - 1) / p.td_chunk;
             unsigned long long t0 = 0;
             if (lane == 0) t0 = atomicAdd(&p.ctrl->ntask[snext], (unsigned long long)nch);
             t0 = __shfl_sync(kFull, t0, 0);
@@ -570,8 +565,8 @@ __device__ void td_phase(const SingleParams& p, int d, const int* qcur, long lon
                 const long long ti = (long long)t0 + c;
                 if (ti < p.task_cap) {
                     Task t;
-                    t.start = bs + c * kChunk;
-                    t.len = (int)min((long long)kChunk, be - t.start);
+                    t.start = bs + c * p.td_chunk;
+                    t.len = (int)min((long long)p.td_chunk, be - t.start);
                     t.u = bu;
                     p.tasks[ti] = t;
                 } else {
@@ -884,97 +879,91 @@ __device__ void bu_phase_a(const SingleParams& p, int d, const unsigned* fcur, u
 // Bottom-up over the hub-first rows, phase A: the first probe of every
 // searcher.  Algorithm 2 scans a searcher's row in order and stops at the first
 // neighbour in the frontier; over the hub-first rows that first neighbour is
-// the hit for most searchers on R-MAT graphs.  So phase A reads, per vertex,
+// the hit for most searchers on R-MAT graphs.  So phase A reads, per searcher,
 // only first[v] (the first id of its row, bit 31: more neighbours follow), a
-// plane streamed in vertex order.  A warp owns 32 completed-bitmap words (1024
-// vertices) at a time and walks them word by word, lane i on vertex 32w + i,
-// kSweepBatch words per step: all plane loads of a step are in flight
-// together, then all its frontier probes.  While a chunk runs, the plane lines
-// of the warp's next chunk (those with searchers) are prefetched into L2.  The
-// ballot of a word's hits is that word of the next frontier (the warp owns it:
-// no atomics).  A hit stores no parent: its parent is first[v], recorded by one
-// bit of pfirst (the final pass writes the parent array).  A miss with more
-// neighbours goes on the miss list (phase B); a degree-1 miss is done.
+// per-vertex plane.  A warp takes 32 completed-bitmap words (1024 vertices) at a
+// time and compacts their searchers onto lanes (a warp prefix sum), one
+// searcher per lane per round, software-pipelined three deep: round r+2's plane
+// value and round r+1's frontier probe are in flight while round r consumes its
+// probe.  Hits are collected per word in shared memory and written as whole
+// next-frontier words (the warp owns its chunk's words).  A hit stores no
+// parent: its parent is first[v], recorded by one bit of pfirst (the final pass
+// writes the parent array).  A miss with more neighbours goes on the miss list
+// (phase B); a degree-1 miss is done.
 //
 // No degree is read for a hit: the degree sum of the new frontier is m_u minus
 // the degree sum of the searchers left unvisited, which phases A-C count
 // (acc_left), and a searcher left unvisited has had its whole row examined.
 constexpr int kHead = 7;          // ids in a row head
-constexpr int kSweepBatch = 8;    // words per step of the sweep
-static_assert(32 % kSweepBatch == 0, "a step takes whole words of one 32-word chunk");
 constexpr unsigned kMore = 0x80000000u;
 
-__device__ void bu_sweep(const SingleParams& p, int d, const unsigned* fcur, unsigned* fnext, int* misslist,
-                         unsigned long long* misscnt, unsigned long long& acc_n, unsigned long long& acc_left,
-                         unsigned long long& acc_sc, unsigned long long& acc_ex) {
-    const int lane = lane_id();
+__device__ __forceinline__ unsigned frontier_word(const unsigned* f, int v) { return __ldcg(f + (v >> 5)); }
+
+__device__ void bu_compact(const SingleParams& p, int d, const unsigned* fcur, unsigned* fnext, int* misslist,
+                           unsigned long long* misscnt, unsigned long long& acc_n, unsigned long long& acc_left,
+                           unsigned long long& acc_sc, unsigned long long& acc_ex) {
+    __shared__ unsigned s_cnext[kWarps][32];
+    const int lane = lane_id(), wib = threadIdx.x >> 5;
     const long long nchunk = (p.W + 31) / 32;
-    WarpStage mst = warp_stage();   // miss-list entries, appended in batches
+    s_cnext[wib][lane] = 0u;
+    WarpStage mst = warp_stage();
+    __syncwarp();
     const long long gw = gtid() >> 5, nw = gthreads() >> 5;
-    // completed words of the warp's current chunk (lane i: word 32 ch + i); no
-    // other warp writes them during this phase
-    unsigned cw = kFull;
-    if (gw < nchunk && gw * 32 + lane < p.W) cw = __ldcg(p.visited + gw * 32 + lane);
-    if (gw < nchunk && cw != kFull) prefetch_l2_line(p.first + (gw * 32 + lane) * 32);
     for (long long ch = gw; ch < nchunk; ch += nw) {
-        const long long wl = ch * 32 + lane;      // this lane's word of the chunk
-        const long long wn = wl + nw * 32;        // its word of the warp's next chunk
-        const unsigned cwn = (ch + nw < nchunk && wn < p.W) ? __ldcg(p.visited + wn) : kFull;
-        if (cwn != kFull) prefetch_l2_line(p.first + wn * 32);
+        const long long w = ch * 32 + lane;
+        const unsigned cw = (w < p.W) ? __ldcg(p.visited + w) : kFull;
         const unsigned todo = ~cw;
-        const unsigned busy = __ballot_sync(kFull, todo != 0u);   // words with searchers
-        unsigned nx = 0;                          // next-frontier bits of word wl
-        for (int jb = 0; jb < 32; jb += kSweepBatch) {
-            if (((busy >> jb) & ((1u << kSweepBatch) - 1u)) == 0u) continue;
-            int f[kSweepBatch];
-            unsigned actm = 0;                    // bit k: this lane searches in word jb + k
-#pragma unroll
-            for (int k = 0; k < kSweepBatch; k++) {
-                const bool a = (__shfl_sync(kFull, todo, jb + k) >> lane) & 1u;
-                f[k] = 0;
-                if (a) {
-                    f[k] = ld_stream32(p.first + (ch * 32 + jb + k) * 32 + lane);
-                    actm |= 1u << k;
+        const int cnt = __popc(todo);
+        const int incl = warp_inclusive_scan(cnt);
+        const int T = __shfl_sync(kFull, incl, 31);
+        const int excl = incl - cnt;
+        int u0 = bu_locate(lane, T, incl, excl, todo, ch);
+        int f0 = u0 >= 0 ? ld_stream32(p.first + u0) : 0;
+        int u1 = bu_locate(32 + lane, T, incl, excl, todo, ch);
+        int f1 = u1 >= 0 ? ld_stream32(p.first + u1) : 0;
+        unsigned pw0 = u0 >= 0 ? frontier_word(fcur, f0 & (int)~kMore) : 0u;
+        for (int base = 0; base < T; base += 32) {
+            const int u2 = bu_locate(base + 64 + lane, T, incl, excl, todo, ch);
+            const int f2 = u2 >= 0 ? ld_stream32(p.first + u2) : 0;
+            const unsigned pw1 = u1 >= 0 ? frontier_word(fcur, f1 & (int)~kMore) : 0u;
+            const bool act = u0 >= 0;
+            const bool hit = act && ((pw0 >> (f0 & 31)) & 1u);
+            const bool miss = act && !hit && ((unsigned)f0 & kMore);
+            if (act) {
+                acc_sc += 1;
+                acc_ex += (unsigned long long)(hit || !miss);
+                if (hit) {
+                    set_level(p, u0, d + 1);
+                    if (!p.pfirst && p.parent) p.parent[u0] = f0 & (int)~kMore;
+                    atomicOr(&s_cnext[wib][(u0 >> 5) - ch * 32], 1u << (u0 & 31));
+                } else if (!miss) {
+                    acc_left += 1;
                 }
             }
-            unsigned hitm = 0;
-#pragma unroll
-            for (int k = 0; k < kSweepBatch; k++)
-                if (((actm >> k) & 1u) && in_frontier(fcur, f[k] & (int)~kMore)) hitm |= 1u << k;
-#pragma unroll
-            for (int k = 0; k < kSweepBatch; k++) {
-                const int v = (int)((ch * 32 + jb + k) * 32 + lane);
-                const bool act = (actm >> k) & 1u, hit = (hitm >> k) & 1u;
-                const unsigned hm = __ballot_sync(kFull, hit);
-                if (lane == jb + k) nx = hm;
-                const bool miss = act && !hit && ((unsigned)f[k] & kMore);
-                if (act) {
-                    acc_sc += 1;
-                    acc_ex += (unsigned long long)(hit || !miss);   // a hit, or a degree-1 row
-                    if (hit) {
-                        set_level(p, v, d + 1);
-                        if (!p.pfirst && p.parent) p.parent[v] = f[k] & (int)~kMore;
-                    } else if (!miss) {
-                        acc_left += 1;            // degree 1, left unvisited
-                    }
-                }
-                const unsigned mm = __ballot_sync(kFull, miss);
-                if (mm) {
-                    if (miss) mst.buf[mst.cnt + __popc(mm & lanemask_lt())] = v;
-                    mst.cnt += __popc(mm);
-                    if (mst.cnt > kStage - 32) long_flush(mst, misslist, misscnt);
-                }
+            const unsigned mm = __ballot_sync(kFull, miss);
+            if (mm) {
+                if (miss) mst.buf[mst.cnt + __popc(mm & lanemask_lt())] = u0;
+                mst.cnt += __popc(mm);
+                if (mst.cnt > kStage - 32) long_flush(mst, misslist, misscnt);
             }
+            u0 = u1;
+            f0 = f1;
+            pw0 = pw1;
+            u1 = u2;
+            f1 = f2;
         }
-        if (wl < p.W) {
-            fnext[wl] = nx;
+        __syncwarp();
+        const unsigned nx = s_cnext[wib][lane];
+        if (w < p.W) {
+            fnext[w] = nx;
             if (nx) {
-                p.visited[wl] = cw | nx;
-                if (p.pfirst) p.pfirst[wl] = __ldcg(p.pfirst + wl) | nx;
+                p.visited[w] = cw | nx;
+                if (p.pfirst) atomicOr(p.pfirst + w, nx);
             }
         }
         acc_n += (unsigned long long)__popc(nx);
-        cw = cwn;
+        s_cnext[wib][lane] = 0u;
+        __syncwarp();
     }
     long_flush(mst, misslist, misscnt);
 }
@@ -1191,7 +1180,7 @@ __global__ void __launch_bounds__(kBlock, BFS_MIN_BLOCKS) bfs_single_kernel(Sing
             int* longlist = qnext;
             int* misslist = qcur;
             if (p.first)
-                bu_sweep(p, d, fcur, fnext, misslist, &c->nmiss[snext], an, am, asc, aex);
+                bu_compact(p, d, fcur, fnext, misslist, &c->nmiss[snext], an, am, asc, aex);
             else
                 bu_phase_a(p, d, fcur, fnext, longlist, &c->ntask[snext], an, am, asc, aex);
             block_add4(an, am, asc, aex, &c->accn[snext], &c->accm[snext], &c->scanned[snext],
@@ -1506,7 +1495,7 @@ __global__ void __launch_bounds__(kDBlock, 1) bfs_dcsc_kernel(SingleParams p) {
 constexpr long long kStaticMaxN = 1LL << 20;
 constexpr long long kStaticMaxNnz = 1LL << 24;
 constexpr long long kStaticW = kStaticMaxN / 32;
-constexpr long long kStaticTasks = kStaticMaxNnz / kChunk + kStaticMaxNnz / 64 + 1024;
+constexpr long long kStaticTasks = kStaticMaxNnz / kChunk + kStaticMaxNnz / 64 + 1024;   // default chunk
 constexpr int kStaticRec = 64;
 constexpr size_t kStaticCtrlOff = 0;
 constexpr size_t kStaticIsoOff = (sizeof(Ctrl) + 255) / 256 * 256;   // control block slot
@@ -1552,7 +1541,8 @@ bfs_status single_prepare(bfs_graph* g, cudaStream_t s) { return single_prepare_
 bfs_status single_prepare_work(bfs_graph* g, SingleWork& w, cudaStream_t s, int grid) {
     if (w.ready) return BFS_OK;
     const long long n = g->n, W = g->W;
-    const long long task_cap = g->nnz / bfsk::kChunk + g->nnz / 64 + 1024;  // big degree is >= 64
+    // chunks of >= kMinChunk edges of vertices of degree > 64: at most nnz/64 + nnz/64 tasks
+    const long long task_cap = g->nnz / bfsk::kMinChunk + g->nnz / 64 + 1024;
     const int rec_cap = 1 << 16;
     struct Item { void** p; size_t bytes; };
     Item items[] = {
@@ -1569,10 +1559,10 @@ bfs_status single_prepare_work(bfs_graph* g, SingleWork& w, cudaStream_t s, int 
     };
     size_t total = 0;
     for (auto& it : items) {
-        *it.p = g->mem.alloc(it.bytes, s);
+        *it.p = mem_of(g, w).alloc(it.bytes, s);
         if (!*it.p) {
             for (auto& jt : items)
-                if (*jt.p) { g->mem.release(*jt.p, jt.bytes, s); *jt.p = nullptr; }
+                if (*jt.p) { mem_of(g, w).release(*jt.p, jt.bytes, s); *jt.p = nullptr; }
             return fail(BFS_ERR_OOM, "single-source work buffers: device allocation failed");
         }
         total += it.bytes;
@@ -1599,18 +1589,20 @@ void single_release(bfs_graph* g) { single_release_work(g, g->single); }
 void single_release_work(bfs_graph* g, SingleWork& w) {
     if (!w.ready) return;
     const long long n = g->n, W = g->W;
-    g->mem.release(w.visited, sizeof(unsigned) * (size_t)W, nullptr);
-    g->mem.release(w.front0, sizeof(unsigned) * (size_t)W, nullptr);
-    g->mem.release(w.front1, sizeof(unsigned) * (size_t)W, nullptr);
-    g->mem.release(w.queue0, sizeof(int) * (size_t)(n + 32), nullptr);
-    g->mem.release(w.queue1, sizeof(int) * (size_t)(n + 32), nullptr);
-    g->mem.release(w.lv8, (size_t)W * 32, nullptr);
-    g->mem.release(w.pfirst, sizeof(unsigned) * (size_t)W, nullptr);
-    if (w.level_scratch) g->mem.release(w.level_scratch, sizeof(int) * (size_t)n, nullptr);
-    g->mem.release(w.tasks, sizeof(Task) * (size_t)w.task_cap, nullptr);
-    g->mem.release(w.ctrl, sizeof(Ctrl), nullptr);
-    g->mem.release(w.records, sizeof(bfs_level_record) * (size_t)w.rec_cap, nullptr);
+    mem_of(g, w).release(w.visited, sizeof(unsigned) * (size_t)W, nullptr);
+    mem_of(g, w).release(w.front0, sizeof(unsigned) * (size_t)W, nullptr);
+    mem_of(g, w).release(w.front1, sizeof(unsigned) * (size_t)W, nullptr);
+    mem_of(g, w).release(w.queue0, sizeof(int) * (size_t)(n + 32), nullptr);
+    mem_of(g, w).release(w.queue1, sizeof(int) * (size_t)(n + 32), nullptr);
+    mem_of(g, w).release(w.lv8, (size_t)W * 32, nullptr);
+    mem_of(g, w).release(w.pfirst, sizeof(unsigned) * (size_t)W, nullptr);
+    if (w.level_scratch) mem_of(g, w).release(w.level_scratch, sizeof(int) * (size_t)n, nullptr);
+    mem_of(g, w).release(w.tasks, sizeof(Task) * (size_t)w.task_cap, nullptr);
+    mem_of(g, w).release(w.ctrl, sizeof(Ctrl), nullptr);
+    mem_of(g, w).release(w.records, sizeof(bfs_level_record) * (size_t)w.rec_cap, nullptr);
+    DeviceAlloc* keep = w.mem;   // the allocator choice outlives the buffers
     w = SingleWork();
+    w.mem = keep;
 }
 
 bfs_status single_launch(bfs_graph* g, const int32_t* roots_host, int32_t k, int32_t* parent,
@@ -1623,7 +1615,7 @@ bfs_status single_launch_work(bfs_graph* g, SingleWork& w, const int32_t* roots_
     if (opt.parent_mode == BFS_PARENT_MIN_ID && parent && !level) {
         // minimum-id parents are picked by level; keep them in a private array
         if (!w.level_scratch) {
-            w.level_scratch = (int*)g->mem.alloc(sizeof(int) * (size_t)g->n, s);
+            w.level_scratch = (int*)mem_of(g, w).alloc(sizeof(int) * (size_t)g->n, s);
             if (!w.level_scratch) return fail(BFS_ERR_OOM, "MIN_ID parents: level scratch allocation failed");
         }
         level = w.level_scratch;
@@ -1644,7 +1636,7 @@ bfs_status single_launch_work(bfs_graph* g, SingleWork& w, const int32_t* roots_
     p.level = level;
     // staged outputs and the final whole-sector pass (CSR kernel, some output requested)
     p.lv8 = (opt.layout == BFS_LAYOUT_DCSC_TILED || (!parent && !level)) ? nullptr : w.lv8;
-    p.pfirst = p.lv8 ? w.pfirst : nullptr;
+    p.pfirst = (p.lv8 && p.first) ? w.pfirst : nullptr;   // only a plane sweep sets its bits
     p.visited = w.visited;
     p.front0 = w.front0;
     p.front1 = w.front1;
@@ -1662,9 +1654,10 @@ bfs_status single_launch_work(bfs_graph* g, SingleWork& w, const int32_t* roots_
     p.beta = opt.beta;
     p.parent_mode = opt.parent_mode;
     p.big_deg = opt.td_big_degree > 0 ? opt.td_big_degree : 96;
+    p.td_chunk = opt.td_chunk > 0 ? opt.td_chunk : bfsk::kChunk;
     p.seed = opt.seed;
     p.timeout_ns = (unsigned long long)(opt.timeout_ms > 0 ? opt.timeout_ms : 10000) * 1000000ull;
-    const unsigned extra = (unsigned)(opt.debug_barrier_extra > 0 ? opt.debug_barrier_extra : 0);
+    const unsigned extra = (unsigned)(g->debug_barrier_extra > 0 ? g->debug_barrier_extra : 0);
     p.expected = (unsigned)w.grid + extra;
     p.tile_ptr = nullptr;
     p.jc = nullptr;
@@ -1675,6 +1668,10 @@ bfs_status single_launch_work(bfs_graph* g, SingleWork& w, const int32_t* roots_
     p.Bw = 0;
     const bool dcsc = opt.layout == BFS_LAYOUT_DCSC_TILED;
     int grid = w.grid, block = w.block;
+    if (opt.ctas_per_sm > 0 && (long long)opt.ctas_per_sm * g->sm_count < grid) {
+        grid = opt.ctas_per_sm * g->sm_count;
+        p.expected = (unsigned)grid + extra;
+    }
     size_t dyn = bfsk::kSingleDynSmem;
     if (dcsc) {
         const DcscTiles& D = g->dcsc;
@@ -1822,6 +1819,7 @@ extern "C" bfs_status bfs_run_csr_noalloc(const int64_t* row_offsets, const int3
     p.beta = 24;
     p.parent_mode = BFS_PARENT_ANY;
     p.big_deg = 96;
+    p.td_chunk = bfsk::kChunk;
     p.timeout_ns = 10000ull * 1000000ull;
     p.expected = (unsigned)grid;
     const int ig = (int)std::min<long long>((W + 255) / 256, (long long)g_noalloc_sms[dev] * 4);

@@ -82,6 +82,31 @@ __global__ void k_isolated(const long long* __restrict__ off, long long n, long 
     }
 }
 
+// 64-bit endpoints narrowed to int32; *bad = 1 when one lies outside [0, n)
+__global__ void k_narrow_edges(const int64_t* __restrict__ s64, const int64_t* __restrict__ d64, long long m,
+                               long long n, int32_t* __restrict__ s32, int32_t* __restrict__ d32, int* bad) {
+    const long long nth = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += nth) {
+        const int64_t a = s64[i], b = d64[i];
+        if (a < 0 || a >= n || b < 0 || b >= n) {
+            *bad = 1;
+            s32[i] = 0;
+            d32[i] = 0;
+        } else {
+            s32[i] = (int32_t)a;
+            d32[i] = (int32_t)b;
+        }
+    }
+}
+
+// number of vertices with degree > 0 (clear bits of the isolated bitmap)
+__global__ void k_count_active(const uint32_t* __restrict__ iso, long long W, unsigned long long* cnt) {
+    const long long nth = (long long)gridDim.x * blockDim.x;
+    unsigned long long c = 0;
+    for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < W; w += nth) c += __popc(~iso[w]);
+    if (c) atomicAdd(cnt, c);
+}
+
 // deg8[v] = min(deg(v), 255): the degree as bottom-up and top-down steps need it
 // (a coalesced byte stream instead of two int64 offsets per vertex)
 __global__ void k_deg8(const long long* __restrict__ off, long long n, uint8_t* __restrict__ deg8) {
@@ -172,6 +197,18 @@ bfs_status build_isolated_bitmap(bfs_graph* g, cudaStream_t s) {
     k_isolated<<<grid_for(g->W, 256, g->sm_count), 256, 0, s>>>((const long long*)g->offsets, g->n, g->W,
                                                                 g->isolated);
     BFS_CUDA_TRY(cudaGetLastError());
+    {
+        Scratch cnt(&g->mem, s);
+        if (!cnt.get(16)) return fail(BFS_ERR_OOM, "graph build: counter");
+        BFS_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, 16, s));
+        k_count_active<<<grid_for(g->W, 256, g->sm_count), 256, 0, s>>>(g->isolated, g->W,
+                                                                        (unsigned long long*)cnt.p);
+        BFS_CUDA_TRY(cudaGetLastError());
+        unsigned long long h = 0;
+        BFS_CUDA_TRY(cudaMemcpyAsync(&h, cnt.p, sizeof h, cudaMemcpyDeviceToHost, s));
+        BFS_CUDA_TRY(cudaStreamSynchronize(s));
+        g->n_active = (int64_t)h;
+    }
     g->deg8 = (uint8_t*)g->mem.alloc((size_t)g->n + 32, s);
     if (!g->deg8) return fail(BFS_ERR_OOM, "graph build: degree bytes");
     g->graph_bytes += (size_t)g->n + 32;
@@ -256,6 +293,42 @@ bfs_status build_csr_from_edges(bfs_graph* g, const int32_t* src, const int32_t*
     if (st != BFS_OK) return st;
     BFS_CUDA_TRY(cudaStreamSynchronize(s));
     return BFS_OK;
+}
+
+bfs_status build_csr_from_edges64(bfs_graph* g, const int64_t* src, const int64_t* dst, int64_t m, bool device_ptrs,
+                                  cudaStream_t s) {
+    Scratch s32(&g->mem, s), d32(&g->mem, s), flag(&g->mem, s), stage(&g->mem, s);
+    if (m > 0 && (!s32.get(sizeof(int32_t) * (size_t)m) || !d32.get(sizeof(int32_t) * (size_t)m)))
+        return fail(BFS_ERR_OOM, "graph build: int32 edge arrays");
+    if (!flag.get(16)) return fail(BFS_ERR_OOM, "graph build: counter");
+    BFS_CUDA_TRY(cudaMemsetAsync(flag.p, 0, 16, s));
+    int* d_bad = (int*)flag.p;
+    if (device_ptrs) {
+        if (m > 0) {
+            k_narrow_edges<<<grid_for(m, 256, g->sm_count), 256, 0, s>>>(src, dst, m, g->n, (int32_t*)s32.p,
+                                                                       (int32_t*)d32.p, d_bad);
+            BFS_CUDA_TRY(cudaGetLastError());
+        }
+    } else if (m > 0) {
+        // host arrays: copied in chunks through a device staging buffer, narrowed there
+        const long long chunk = std::min<long long>(m, 1LL << 24);
+        if (!stage.get(2 * sizeof(int64_t) * (size_t)chunk)) return fail(BFS_ERR_OOM, "graph build: edge staging");
+        int64_t* st_s = (int64_t*)stage.p;
+        int64_t* st_d = st_s + chunk;
+        for (long long a = 0; a < m; a += chunk) {
+            const long long c = std::min(chunk, m - a);
+            BFS_CUDA_TRY(cudaMemcpyAsync(st_s, src + a, sizeof(int64_t) * (size_t)c, cudaMemcpyHostToDevice, s));
+            BFS_CUDA_TRY(cudaMemcpyAsync(st_d, dst + a, sizeof(int64_t) * (size_t)c, cudaMemcpyHostToDevice, s));
+            k_narrow_edges<<<grid_for(c, 256, g->sm_count), 256, 0, s>>>(st_s, st_d, c, g->n, (int32_t*)s32.p + a,
+                                                                       (int32_t*)d32.p + a, d_bad);
+            BFS_CUDA_TRY(cudaGetLastError());
+        }
+    }
+    int hbad = 0;
+    BFS_CUDA_TRY(cudaMemcpyAsync(&hbad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BFS_CUDA_TRY(cudaStreamSynchronize(s));
+    if (hbad) return fail(BFS_ERR_INVALID, "an edge endpoint lies outside [0, n_vertices)");
+    return build_csr_from_edges(g, (const int32_t*)s32.p, (const int32_t*)d32.p, m, true, s);
 }
 
 bfs_status build_csr_from_csr(bfs_graph* g, const int64_t* off, const int32_t* cols, bool device_ptrs,

@@ -109,6 +109,7 @@ struct Slot {
 }  // namespace
 
 struct bfs_server {
+    bfsrt::DeviceAlloc mem;   // every device buffer the server owns (hook or cudaMalloc)
     int64_t budget = 0;
     int64_t used = 0;
     int32_t max_lanes = 64;
@@ -333,9 +334,9 @@ void worker_main(bfs_server* sv) {
                     if (L.busy) continue;
                     if (!L.row) {
                         if (sv->used + (int64_t)row_bytes > sv->budget) break;   // admission bounded by HBM budget
-                        if (cudaMalloc(&L.row, row_bytes) != cudaSuccess) {
+                        L.row = (int32_t*)sv->mem.alloc(row_bytes, s.stream);
+                        if (!L.row) {
                             (void)cudaGetLastError();
-                            L.row = nullptr;
                             break;
                         }
                         sv->used += (int64_t)row_bytes;
@@ -378,7 +379,7 @@ void worker_main(bfs_server* sv) {
 }
 
 // Levels of one search from the first vertex with neighbours (0 if the graph has none).
-bfs_status probe_levels(bfs_graph* g, int* levels) {
+bfs_status probe_levels(bfs_graph* g, bfsrt::DeviceAlloc* mem, int* levels) {
     *levels = 0;
     const long long words = std::min<long long>(g->W, 1 << 16);
     std::vector<uint32_t> iso((size_t)words);
@@ -388,15 +389,17 @@ bfs_status probe_levels(bfs_graph* g, int* levels) {
     for (long long w = 0; w < words && root < 0; w++)
         if (iso[(size_t)w] != 0xFFFFFFFFu) root = (int)(w * 32 + __builtin_ctz(~iso[(size_t)w]));
     if (root < 0) return BFS_OK;
-    int32_t* lv = nullptr;
-    if (cudaMalloc(&lv, sizeof(int32_t) * (size_t)g->n) != cudaSuccess) return fail(BFS_ERR_OOM, "probe: level buffer");
+    const size_t lv_bytes = sizeof(int32_t) * (size_t)g->n;
+    int32_t* lv = (int32_t*)mem->alloc(lv_bytes, nullptr);
+    if (!lv) return fail(BFS_ERR_OOM, "probe: level buffer");
     bfs_level_record recs[1];
     bfs_stats st;
     memset(&st, 0, sizeof st);
     st.levels = recs;
     st.levels_capacity = 1;
     const bfs_status r = bfs_run(g, root, nullptr, lv, nullptr, nullptr, &st);
-    cudaFree(lv);
+    if (cudaDeviceSynchronize() != cudaSuccess) (void)cudaGetLastError();
+    mem->release(lv, lv_bytes, nullptr);
     if (r != BFS_OK) return r;
     *levels = st.num_levels;
     return BFS_OK;
@@ -421,10 +424,9 @@ bfs_status add_execs(bfs_server* sv, Slot* s, int count, int grid, int min_count
             return fail(BFS_ERR_CUDA, "search executor stream / event");
         if (cudaMallocHost(&ex->ctrl_pinned, single_ctrl_bytes()) != cudaSuccess)
             return fail(BFS_ERR_OOM, "search executor control copy");
-        if (cudaMalloc(&ex->dlevel, (size_t)row) != cudaSuccess) {
-            ex->dlevel = nullptr;
-            return fail(BFS_ERR_OOM, "search executor level buffer");
-        }
+        ex->dlevel = (int32_t*)sv->mem.alloc((size_t)row, ex->stream);
+        if (!ex->dlevel) return fail(BFS_ERR_OOM, "search executor level buffer");
+        ex->w.mem = &sv->mem;
         bfs_status r = single_prepare_work(s->g, ex->w, ex->stream, grid);
         if (r != BFS_OK) return r;
         if (cudaStreamSynchronize(ex->stream) != cudaSuccess) return fail(BFS_ERR_CUDA, "search executor setup");
@@ -433,11 +435,11 @@ bfs_status add_execs(bfs_server* sv, Slot* s, int count, int grid, int min_count
     return BFS_OK;
 }
 
-void free_execs(Slot* s) {
+void free_execs(bfs_server* sv, Slot* s) {
     for (Exec* ex : s->execs) {
         if (ex->stream) cudaStreamSynchronize(ex->stream);
         single_release_work(s->g, ex->w);
-        if (ex->dlevel) cudaFree(ex->dlevel);
+        if (ex->dlevel) sv->mem.release(ex->dlevel, sizeof(int32_t) * (size_t)s->g->n, ex->stream);
         if (ex->ctrl_pinned) cudaFreeHost(ex->ctrl_pinned);
         if (ex->ev) cudaEventDestroy(ex->ev);
         if (ex->stream) cudaStreamDestroy(ex->stream);
@@ -451,14 +453,25 @@ void free_execs(Slot* s) {
 extern "C" {
 
 bfs_status bfs_server_create(int64_t hbm_budget_bytes, int32_t max_lanes, bfs_server** out) {
+    return bfs_server_create_ex(hbm_budget_bytes, max_lanes, nullptr, out);
+}
+
+bfs_status bfs_server_create_ex(int64_t hbm_budget_bytes, int32_t max_lanes, const bfs_allocator* alloc,
+                                bfs_server** out) {
     if (!out) return fail(BFS_ERR_INVALID, "out handle pointer is NULL");
     *out = nullptr;
+    if (alloc && (!alloc->alloc || !alloc->free))
+        return fail(BFS_ERR_INVALID, "allocator hook needs both alloc and free");
     if (hbm_budget_bytes <= 0) return fail(BFS_ERR_INVALID, "hbm_budget_bytes must be > 0");
     if (max_lanes < 1 || max_lanes > 64) return fail(BFS_ERR_INVALID, "max_lanes must lie in [1, 64]");
     bfs_server* sv = new (std::nothrow) bfs_server();
     if (!sv) return fail(BFS_ERR_OOM, "host allocation of the server");
     sv->budget = hbm_budget_bytes;
     sv->max_lanes = max_lanes;
+    if (alloc) {
+        sv->mem.hook = *alloc;
+        sv->mem.has_hook = true;
+    }
     cudaError_t e = cudaGetDevice(&sv->device);
     if (e != cudaSuccess) {
         delete sv;
@@ -476,7 +489,7 @@ bfs_status bfs_server_add_graph(bfs_server* sv, bfs_graph* g, int32_t* slot) {
     if (!s) return fail(BFS_ERR_OOM, "host allocation of a slot");
     s->g = g;
     int deep_levels = 0;
-    bfs_status pr = probe_levels(g, &deep_levels);
+    bfs_status pr = probe_levels(g, &sv->mem, &deep_levels);
     if (pr != BFS_OK) {
         delete s;
         return fail(pr, std::string("server: add_graph: probe search: ") + bfs_last_error());
@@ -486,7 +499,7 @@ bfs_status bfs_server_add_graph(bfs_server* sv, bfs_graph* g, int32_t* slot) {
         bfs_status r = add_execs(sv, s, kDeepExecs, std::max(kMinCtas, 2 * g->sm_count / kDeepExecs), 1);
         if (r != BFS_OK) {
             std::string msg = bfs_last_error();
-            free_execs(s);
+            free_execs(sv, s);
             delete s;
             return fail(r, "server: add_graph: " + msg);
         }
@@ -508,6 +521,7 @@ bfs_status bfs_server_add_graph(bfs_server* sv, bfs_graph* g, int32_t* slot) {
     }
     s->stream = st;
     s->copy_stream = cst;
+    s->w.mem = &sv->mem;
     bfs_status r = multi_alloc(g, s->w, st);
     if (r == BFS_OK) r = ms_serve_reset(g, s->w, st);
     if (r == BFS_OK && cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming) != cudaSuccess) r = BFS_ERR_CUDA;
@@ -530,7 +544,7 @@ bfs_status bfs_server_add_graph(bfs_server* sv, bfs_graph* g, int32_t* slot) {
         bfs_status r = add_execs(sv, s, kExecs, grid, 0);
         if (r != BFS_OK) {
             std::string msg = bfs_last_error();
-            free_execs(s);
+            free_execs(sv, s);
             multi_free(g, s->w);
             cudaEventDestroy(s->ev);
             cudaFreeHost(s->ctrl_pinned);
@@ -623,15 +637,15 @@ void bfs_server_destroy(bfs_server* sv) {
     if (sv->worker.joinable()) sv->worker.join();
     for (Slot* s : sv->slots) {
         if (s->deep) {
-            free_execs(s);
+            free_execs(sv, s);
             delete s;
             continue;
         }
-        free_execs(s);
+        free_execs(sv, s);
         cudaStreamSynchronize(s->stream);
         cudaStreamSynchronize(s->copy_stream);
         for (auto& L : s->lanes)
-            if (L.row) cudaFree(L.row);
+            if (L.row) sv->mem.release(L.row, sizeof(int32_t) * (size_t)s->g->n, s->stream);
         multi_free(s->g, s->w);
         cudaEventDestroy(s->ev);
         for (auto& cb : s->copies)

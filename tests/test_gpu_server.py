@@ -113,3 +113,51 @@ def test_server_deep_graph_runs_concurrent_searches(gpu_lib):
     srv.close()
     gt.close()
     gr.close()
+
+
+def test_server_allocator_hook(gpu_lib):
+    """bfs_server_create_ex: every device buffer the server owns comes from the
+    caller's allocator (here PyTorch's caching allocator, with the calls counted),
+    is returned by destroy, and queries still equal the oracle."""
+    import ctypes
+    import torch
+    bfs = gpu_lib
+    L = bfs._lib
+    calls = {"alloc": 0, "free": 0, "live": {}}
+
+    def _alloc(nbytes, stream, ctx):
+        p = int(torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(), stream or 0))
+        calls["alloc"] += 1
+        calls["live"][p] = nbytes
+        return p
+
+    def _free(ptr, nbytes, stream, ctx):
+        calls["free"] += 1
+        calls["live"].pop(ptr, None)
+        torch.cuda.caching_allocator_delete(ptr)
+
+    class Hook:
+        pass
+
+    hook = Hook()
+    hook.cb = (L.ALLOC_FN(_alloc), L.FREE_FN(_free))
+    hook.struct = L.Allocator(hook.cb[0], hook.cb[1], None)
+    e = workloads.RMAT[13].edges()
+    ref = oracle.build_csr(e.n, e.src, e.dst)
+    g = bfs.Graph.from_edges(e.src, e.dst, e.n)
+    srv = bfs.Server(hbm_budget_bytes=2 << 30, max_lanes=64, allocator=hook)
+    slot = srv.add_graph(g)
+    assert calls["alloc"] > 0
+    roots = graphgen.pick_roots(e, 40, 5).tolist()
+    outs = [(r, np.empty(e.n, np.int32)) for r in roots]
+    tickets = [srv.submit(slot, r, o) for r, o in outs]
+    for (r, o), t in zip(outs, tickets):
+        assert srv.wait(t, 60000)
+        assert np.array_equal(o, oracle.levels(ref, r)), r
+    srv.close()
+    assert calls["free"] == calls["alloc"] and not calls["live"]
+    with pytest.raises(bfs.BfsError):
+        bad = Hook()
+        bad.struct = L.Allocator(hook.cb[0], L.FREE_FN(0), None)
+        bfs.Server(hbm_budget_bytes=1 << 30, allocator=bad)
+    g.close()

@@ -394,9 +394,12 @@ def test_barrier_timeout_returns_error_and_recovers(gpu_lib):
     e = w.edges()
     case = Case(bfs, e)
     root = int(w.roots(e, 1)[0])
+    L = bfs._lib
+    L.check(L.load().bfs_debug_set_barrier_extra(case.g.handle, 1), "debug_set_barrier_extra")
     with pytest.raises(bfs.BfsError) as ex:
-        case.run(root, bfs.options(timeout_ms=200, debug_barrier_extra=1), stats=True)
+        case.run(root, bfs.options(timeout_ms=200), stats=True)
     assert ex.value.status == 4
+    L.check(L.load().bfs_debug_set_barrier_extra(case.g.handle, 0), "debug_set_barrier_extra")
     lv, pa, _ = case.run(root, stats=True)
     assert np.array_equal(lv, oracle.levels(case.ref, root))
 
@@ -427,13 +430,72 @@ def test_autotune_picks_a_grid_point_and_levels_do_not_change(gpu_lib, tmp_path,
     case = Case(bfs, e)
     roots = w.roots(e, 4).tolist()
     best, ms = autotune.autotune(case.g, roots)
-    assert best.alpha in (6, 14, 32, 96) and best.beta in (12, 24, 64) and best.td_big_degree in (64, 96, 256)
+    assert best.alpha in (6, 14, 24, 32, 96) and best.beta in (12, 24, 64, 128)
+    assert best.td_big_degree in (64, 96, 256) and best.td_chunk in (0, 128, 256, 512, 1024)
+    assert best.ctas_per_sm in (0, 1)
     assert ms > 0
     monkeypatch.setenv("BFS_AUTOTUNE_CACHE", str(tmp_path / "cache.json"))
     o1 = autotune.tuned_options(case.g, roots)
     o2 = autotune.tuned_options(case.g, roots)        # served from the cache file
-    assert (o1.alpha, o1.beta, o1.td_big_degree) == (o2.alpha, o2.beta, o2.td_big_degree)
+    knobs = ("alpha", "beta", "td_big_degree", "td_chunk", "ctas_per_sm")
+    assert [getattr(o1, k) for k in knobs] == [getattr(o2, k) for k in knobs]
     for root in roots:
         lv, pa, _ = case.run(root, o1)
         assert np.array_equal(lv, oracle.levels(case.ref, root))
         assert oracle.certify(case.ref, root, lv, pa, case.labels) == (0, -1)
+
+
+def test_edges64_entry_point(gpu_lib):
+    """bfs_graph_create_from_edges64 (64-bit endpoint arrays, host and device): the CSR
+    equals the oracle's bit for bit and searches are exact; an endpoint outside
+    [0, n) is refused."""
+    import torch
+    bfs = gpu_lib
+    e = graphgen.random_small(5000, 40000, 3)
+    ref = oracle.build_csr(e.n, e.src, e.dst)
+    s64, d64 = e.src.astype(np.int64), e.dst.astype(np.int64)
+    for src, dst in ((s64, d64), (torch.from_numpy(s64).cuda(), torch.from_numpy(d64).cuda())):
+        g = bfs.Graph.from_edges(src, dst, e.n, hub_first=True)
+        off, cols = g.csr_host()
+        assert np.array_equal(off, ref.offsets) and np.array_equal(cols, ref.cols)
+        lv = torch.empty(e.n, dtype=torch.int32, device="cuda")
+        root = int(np.argmax(ref.degree()))
+        g.run(root, level=lv, opts=bfs.options(bu_rows=bfs.BU_ROWS_HUB_FIRST))
+        assert np.array_equal(lv.cpu().numpy(), oracle.levels(ref, root))
+        g.close()
+    bad = s64.copy()
+    bad[77] = e.n
+    with pytest.raises(bfs.BfsError) as ex:
+        bfs.Graph.from_edges(bad, d64, e.n)
+    assert ex.value.status == 1
+
+
+def test_launch_knobs_keep_levels_exact(gpu_lib):
+    """The tuning knobs (top-down chunk size, CTAs per SM, hub cut-off) change the
+    work split only: levels bit-exact, parents certified, per-level counters equal
+    to the oracle's schedule; out-of-range values are refused."""
+    bfs = gpu_lib
+    w = workloads.RMAT[16]
+    e = w.edges()
+    case = Case(bfs, e)
+    g = bfs.Graph.from_edges(e.src, e.dst, e.n, hub_first=True)
+    h = oracle.hub_first(case.ref)
+    for root in w.roots(e, 2).tolist():
+        want = oracle.levels(case.ref, root)
+        for kw in (dict(td_chunk=64), dict(td_chunk=4096, td_big_degree=64), dict(ctas_per_sm=1),
+                   dict(ctas_per_sm=1, td_chunk=128, bu_rows=bfs.BU_ROWS_HUB_FIRST)):
+            hub = kw.get("bu_rows") == bfs.BU_ROWS_HUB_FIRST
+            case.g, keep = (g, case.g) if hub else (case.g, None)
+            lv, pa, info = case.run(root, bfs.options(**kw), stats=True)
+            if keep is not None:
+                case.g = keep
+            assert np.array_equal(lv, want), (root, kw)
+            assert oracle.certify(case.ref, root, lv, pa, case.labels) == (0, -1), (root, kw)
+            s = oracle.do_schedule(h if hub else case.ref, want, oracle.MODE_DO, 14, 24)
+            for col, name in enumerate(["dir", "nf", "mf", "nnext", "mnext", "scanned", "examined"]):
+                assert np.array_equal(info["records"][:, col], getattr(s, name)), (root, kw, name)
+    for kw in (dict(td_chunk=32), dict(td_chunk=5000), dict(ctas_per_sm=-1)):
+        with pytest.raises(bfs.BfsError) as ex:
+            case.run(0, bfs.options(**kw))
+        assert ex.value.status == 1
+    g.close()

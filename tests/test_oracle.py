@@ -368,6 +368,27 @@ def test_hub_first_rows_match_definition(seed):
 
 
 @pytest.mark.parametrize("seed", range(3))
+def test_hub_first_rows_in_c_match_definition(seed):
+    """hub_first_rows (row by row in C: insertion sort for rows of <= 32, merge
+    sort above) gives every row in the order of a plain Python sort on (-degree,
+    id) of the set-built adjacency, and equals the lexsort hub_first() on larger
+    graphs whose hub rows take the merge-sort branch."""
+    g = graphgen.rmat(9, seed=700 + seed)
+    c = csr(g)
+    h = oracle.hub_first_rows(c)
+    adj = _set_csr(g.n, g.src, g.dst)
+    deg = [len(a) for a in adj]
+    assert np.array_equal(h.offsets, c.offsets)
+    assert max(deg) > 32
+    for u in range(g.n):
+        want = sorted(adj[u], key=lambda v: (-deg[v], v))
+        assert h.cols[h.offsets[u]:h.offsets[u + 1]].tolist() == want
+    for e in (graphgen.rmat(13, seed=90 + seed), graphgen.star(300, center=7 + seed), graphgen.from_pairs(5, [])):
+        c = csr(e)
+        assert np.array_equal(oracle.hub_first_rows(c).cols, oracle.hub_first(c).cols)
+
+
+@pytest.mark.parametrize("seed", range(3))
 def test_hub_first_schedule_counts_follow_row_order(seed):
     """Levels do not depend on the row order; the bottom-up examination counts of
     the schedule equal a literal walk of Algorithm 2 over the hub-first rows; and
