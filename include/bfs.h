@@ -144,6 +144,9 @@ typedef struct {
     bfs_level_record* levels;  /* in: host array or NULL; out: min(num_levels, capacity) records */
     int64_t vertices_reached;
     int64_t edges_examined;    /* sum of `examined` over all levels */
+    int64_t t_init_ns;         /* device time of the initialisation (output staging, bitmaps, root) */
+    int64_t t_final_ns;        /* device time from the end of the last level to the last CTA's end of the
+                                  final pass that writes level[] and parent[] (0 when none ran) */
 } bfs_stats;
 
 /* ----------------------------------------------------------------- graphs */

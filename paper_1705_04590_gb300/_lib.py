@@ -40,7 +40,7 @@ class LevelRecord(ctypes.Structure):
 
 class Stats(ctypes.Structure):
     _fields_ = [("num_levels", c_i32), ("levels_capacity", c_i32), ("levels", ctypes.POINTER(LevelRecord)),
-                ("vertices_reached", c_i64), ("edges_examined", c_i64)]
+                ("vertices_reached", c_i64), ("edges_examined", c_i64), ("t_init_ns", c_i64), ("t_final_ns", c_i64)]
 
 
 class DcscLayout(ctypes.Structure):

@@ -268,7 +268,7 @@ class Graph:
                 for r in recs[:nrec]]
         arr = np.array(rows, dtype=np.int64).reshape(-1, 11)
         return {"num_levels": s.num_levels, "reached": s.vertices_reached, "edges_examined": s.edges_examined,
-                "records": arr}
+                "t_init_ns": s.t_init_ns, "t_final_ns": s.t_final_ns, "records": arr}
 
     def close(self):
         if self._h:

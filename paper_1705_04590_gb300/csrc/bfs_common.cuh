@@ -48,6 +48,11 @@ struct Ctrl {
     unsigned long long nmiss[3];     // bottom-up searchers whose first probe missed (miss-list length)
     long long num_levels;
     long long reached;
+    unsigned long long t_enter;    // lead CTA's clock at kernel entry
+    unsigned long long t_init;     // ... after the initialisation barrier
+    unsigned long long t_levels;   // ... after the last level
+    unsigned long long t_done;     // clock of the last CTA to finish the final pass
+    unsigned long long done_ctas;  // CTAs through the final pass
 };
 
 __device__ __forceinline__ uint64_t globaltimer_ns() {

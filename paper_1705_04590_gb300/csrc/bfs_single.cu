@@ -902,8 +902,11 @@ __device__ __forceinline__ unsigned frontier_word(const unsigned* f, int v) { re
 __device__ void bu_compact(const SingleParams& p, int d, const unsigned* fcur, unsigned* fnext, int* misslist,
                            unsigned long long* misscnt, unsigned long long& acc_n, unsigned long long& acc_left,
                            unsigned long long& acc_sc, unsigned long long& acc_ex) {
-    __shared__ unsigned s_cnext[kWarps][32];
+    __shared__ unsigned s_cnext[kBlock / 32][32];
+    // the chunk's searchers as offsets within the chunk (0..1023), in vertex order
+    __shared__ unsigned short s_list[kBlock / 32][1024];
     const int lane = lane_id(), wib = threadIdx.x >> 5;
+    unsigned short* list = s_list[wib];
     const long long nchunk = (p.W + 31) / 32;
     s_cnext[wib][lane] = 0u;
     WarpStage mst = warp_stage();
@@ -912,20 +915,29 @@ __device__ void bu_compact(const SingleParams& p, int d, const unsigned* fcur, u
     for (long long ch = gw; ch < nchunk; ch += nw) {
         const long long w = ch * 32 + lane;
         const unsigned cw = (w < p.W) ? __ldcg(p.visited + w) : kFull;
-        const unsigned todo = ~cw;
+        unsigned todo = ~cw;
         const int cnt = __popc(todo);
         const int incl = warp_inclusive_scan(cnt);
         const int T = __shfl_sync(kFull, incl, 31);
-        const int excl = incl - cnt;
-        int u0 = bu_locate(lane, T, incl, excl, todo, ch);
-        int f0 = u0 >= 0 ? ld_stream32(p.first + u0) : 0;
-        int u1 = bu_locate(32 + lane, T, incl, excl, todo, ch);
-        int f1 = u1 >= 0 ? ld_stream32(p.first + u1) : 0;
-        unsigned pw0 = u0 >= 0 ? frontier_word(fcur, f0 & (int)~kMore) : 0u;
-        for (int base = 0; base < T; base += 32) {
-            const int u2 = bu_locate(base + 64 + lane, T, incl, excl, todo, ch);
-            const int f2 = u2 >= 0 ? ld_stream32(p.first + u2) : 0;
-            const unsigned pw1 = u1 >= 0 ? frontier_word(fcur, f1 & (int)~kMore) : 0u;
+        int pos = incl - cnt;
+        while (todo) {
+            const int b = __ffs(todo) - 1;
+            todo &= todo - 1;
+            list[pos++] = (unsigned short)(lane * 32 + b);
+        }
+        __syncwarp();
+        const long long vbase = ch * 1024;
+        // round r's searcher: vertex vbase + list[32 r + lane], or none past T
+        auto who = [&](int r) -> int { const int k = 32 * r + lane; return k < T ? (int)(vbase + list[k]) : -1; };
+        auto plane = [&](int u) -> int { return u >= 0 ? ld_stream32(p.first + u) : 0; };
+        // software pipeline: plane values three rounds ahead, frontier probes one round ahead
+        int f0 = plane(who(0)), f1 = plane(who(1)), f2 = plane(who(2));
+        unsigned pw0 = who(0) >= 0 ? frontier_word(fcur, f0 & (int)~kMore) : 0u;
+        const int R = (T + 31) / 32;
+        for (int r = 0; r < R; r++) {
+            const int f3 = plane(who(r + 3));
+            const unsigned pw1 = who(r + 1) >= 0 ? frontier_word(fcur, f1 & (int)~kMore) : 0u;
+            const int u0 = who(r);
             const bool act = u0 >= 0;
             const bool hit = act && ((pw0 >> (f0 & 31)) & 1u);
             const bool miss = act && !hit && ((unsigned)f0 & kMore);
@@ -946,11 +958,10 @@ __device__ void bu_compact(const SingleParams& p, int d, const unsigned* fcur, u
                 mst.cnt += __popc(mm);
                 if (mst.cnt > kStage - 32) long_flush(mst, misslist, misscnt);
             }
-            u0 = u1;
             f0 = f1;
-            pw0 = pw1;
-            u1 = u2;
             f1 = f2;
+            f2 = f3;
+            pw0 = pw1;
         }
         __syncwarp();
         const unsigned nx = s_cnext[wib][lane];
@@ -1111,8 +1122,10 @@ __device__ void bu_phase_b(const SingleParams& p, int d, const unsigned* fcur, u
 
 __global__ void __launch_bounds__(kBlock, BFS_MIN_BLOCKS) bfs_single_kernel(SingleParams p) {
     Ctrl* c = p.ctrl;
+    if (blockIdx.x == 0 && threadIdx.x == 0) c->t_enter = globaltimer_ns();
     init_phase(p);
     if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) c->t_init = globaltimer_ns();
     if (p.nroots == 1 && gtid() == 0) {
         if (p.parent) p.parent[p.root0] = p.root0;
         set_level(p, p.root0, 0);
@@ -1239,13 +1252,20 @@ __global__ void __launch_bounds__(kBlock, BFS_MIN_BLOCKS) bfs_single_kernel(Sing
     if (lead) {
         c->num_levels = d + 1;
         c->reached = reached;
+        c->t_levels = globaltimer_ns();
     }
     // every level ended at a grid barrier, so all staged bytes are visible here
     if (p.parent_mode == BFS_PARENT_MIN_ID && p.parent && p.level) {
         min_parent_pass(p);
         if (p.lv8 && !grid_sync(&c->b, p.expected, p.timeout_ns)) return;
     }
-    if (p.lv8) materialise(p);
+    if (p.lv8) {
+        materialise(p);
+        // the last CTA through the final pass stamps its end
+        __syncthreads();
+        if (threadIdx.x == 0 && atomicAdd(&c->done_ctas, 1ull) == (unsigned long long)gridDim.x - 1ull)
+            c->t_done = globaltimer_ns();
+    }
 }
 
 // ------------------------------------------------------------------ DCSC tiles
@@ -1714,6 +1734,8 @@ bfs_status single_collect(bfs_graph* g, cudaStream_t s, bfs_stats* stats) {
         return fail(BFS_ERR_CUDA, "top-down chunk task list overflowed (internal sizing error)");
     if (stats) {
         stats->num_levels = (int32_t)c.num_levels;
+        stats->t_init_ns = c.t_init > c.t_enter ? (int64_t)(c.t_init - c.t_enter) : 0;
+        stats->t_final_ns = c.t_done > c.t_levels ? (int64_t)(c.t_done - c.t_levels) : 0;
         stats->vertices_reached = c.reached;
         const int nrec = (int)std::min<long long>(c.num_levels, (long long)w.rec_cap);
         const int ncopy = std::min(nrec, stats->levels_capacity);
