@@ -35,7 +35,8 @@ served:  continuous-batching server over 8 resident graphs; the sustained
           latency and GTEPS, against a one-at-a-time plain FIFO on the same trace.
 configs: R-MAT 24 over CSR (hub-first and id-ordered rows) and DCSC tiles, each
           direction-optimizing / top-down only / bottom-up only; Erdos-Renyi
-          n = 2^26; the 4096^2 torus: a few roots each, GTEPS and roofline.
+          n = 2^26; the 4096^2 torus; a Twitter-sized power-law graph (61.5 M
+          vertices, 1.47 B edges): a few roots each, GTEPS and roofline.
 
 --impl reference times the oracle alone on the headline graph (built by the oracle),
 one whole search per step, one search per host core at a time.
@@ -461,6 +462,16 @@ def configs_section(peak_gbs: float) -> dict:
     del e
     line("torus4096_do", g, roots, bfs.options(bu_rows=bfs.BU_ROWS_HUB_FIRST), n, m)
     g.close()
+    # the paper's real-world graph has Twitter's size: a seeded power-law stand-in of that size
+    w = workloads.TWITTERLIKE
+    e = w.edges()
+    roots = w.roots(e, 8).tolist()
+    g = bfs.Graph.from_edges(e.src, e.dst, e.n, hub_first=True)
+    n, m = e.n, g.nnz // 2
+    del e
+    line("twitterlike_do", g, roots, bfs.options(bu_rows=bfs.BU_ROWS_HUB_FIRST), n, m)
+    out["twitterlike_do"]["graph"] = {"n": n, "undirected_edges": m, "generated_edges": 1_470_000_000}
+    g.close()
     return out
 
 
@@ -623,7 +634,8 @@ def served_section(g26, roots26, n_queries: int = 2000, seed: int = 5151) -> dic
 def metric_name(args, w) -> str:
     what = {"do": "direction-optimizing", "td": "top-down only", "bu": "bottom-up only"}[args.mode]
     graph = {"rmat": f"R-MAT scale {args.scale}", "er": f"Erdos-Renyi n=2^{args.scale} deg 16",
-             "torus": "4096x4096 torus"}[args.workload]
+             "torus": "4096x4096 torus",
+             "twitterlike": "Twitter-sized power-law graph (61.5M vertices, 1.47B edges)"}[args.workload]
     lay = ", DCSC tiles" if args.layout == "dcsc" else ""
     return f"GTEPS harmonic mean, {graph}, 1 GB300 (single-source, {what}{lay})"
 
@@ -648,6 +660,8 @@ def our_arm(args):
         w = workloads.Workload("er", args.scale)
     elif args.workload == "torus":
         w = workloads.TORUS4096
+    elif args.workload == "twitterlike":
+        w = workloads.TWITTERLIKE
     else:
         w = workloads.RMAT[args.scale]
     t0 = time.time()
@@ -790,7 +804,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--scale", type=int, default=26, help="R-MAT scale, or log2 n for --workload er")
-    ap.add_argument("--workload", default="rmat", choices=["rmat", "er", "torus"])
+    ap.add_argument("--workload", default="rmat", choices=["rmat", "er", "torus", "twitterlike"])
     ap.add_argument("--layout", default="csr", choices=["csr", "dcsc"])
     ap.add_argument("--mode", default="do", choices=["do", "td", "bu"])
     ap.add_argument("--bu-rows", default="hub", choices=["hub", "id"],

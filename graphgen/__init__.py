@@ -48,6 +48,9 @@ def _load():
         lib.gg_rmat.restype = ctypes.c_int
         lib.gg_er.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int, i32p, i32p, ctypes.c_int]
         lib.gg_er.restype = ctypes.c_int
+        lib.gg_powerlaw.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
+                                    ctypes.c_int, i32p, i32p, ctypes.c_int]
+        lib.gg_powerlaw.restype = ctypes.c_int
         lib.gg_torus.argtypes = [ctypes.c_int64, ctypes.c_uint64, ctypes.c_int, i32p, i32p, ctypes.c_int]
         lib.gg_torus.restype = ctypes.c_int
         lib.gg_permutation.argtypes = [ctypes.c_int64, ctypes.c_uint64, i32p]
@@ -104,6 +107,18 @@ def erdos_renyi(n: int, m: int, seed: int = 1, permute: bool = True, threads: in
     if _load().gg_er(n, m, seed, int(permute), _p32(src), _p32(dst), threads) != 0:
         raise ValueError("bad Erdos-Renyi arguments")
     return EdgeList(n, src, dst, f"er{n}")
+
+
+def powerlaw(n: int, m: int, gamma: float = 2.1, i0: float = 50.0, seed: int = 1, permute: bool = True,
+             threads: int = 0) -> EdgeList:
+    """m edges whose ends are drawn with density (x + i0)^(-1/(gamma-1)) over vertex
+    ranks x in [0, n) (Chung-Lu expected degrees, power-law exponent gamma > 2),
+    ranks relabelled by the seeded bijection."""
+    src = np.empty(m, np.int32)
+    dst = np.empty(m, np.int32)
+    if _load().gg_powerlaw(n, m, gamma, i0, seed, int(permute), _p32(src), _p32(dst), threads) != 0:
+        raise ValueError("bad power-law arguments")
+    return EdgeList(n, src, dst, f"powerlaw{n}")
 
 
 def torus(side: int, seed: int = 3000, permute: bool = True, threads: int = 0) -> EdgeList:

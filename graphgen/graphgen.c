@@ -25,6 +25,14 @@
  *  - Erdos-Renyi G(n, m): m independent uniform endpoint pairs.
  *  - 2D torus side x side with wrap-around (each vertex linked to its right
  *    and lower neighbour).
+ *  - Power-law expected degrees (Chung and Lu, "Connected components in
+ *    random graphs with given expected degree sequences", 2002): each edge
+ *    end is vertex floor(x) with x drawn from the density proportional to
+ *    (x + i0)^(-1/(gamma-1)) on [0, n) by inverting its CDF in closed form,
+ *    so vertex rank r has expected degree proportional to (r + i0)^(-1/(gamma-1))
+ *    and the degrees follow a power law of exponent gamma.  A scale-free
+ *    stand-in for a social graph of a given size (the CDF goes through the
+ *    host's libm pow, so one machine always gives one graph per seed).
  * Vertex ids are optionally relabelled by a seeded pseudo-random bijection of
  * [0, n): a few rounds of (odd multiply + add) mod 2^k and xor-shift, each
  * invertible on k-bit integers, with cycle walking when n is not a power of
@@ -111,7 +119,7 @@ void gg_permutation(int64_t n, uint64_t seed, int32_t* perm_out) {
 /* ---------------------------------------------------------------- threading */
 
 typedef struct {
-    int kind;           /* 0 rmat, 1 er, 2 torus, 3 relabel */
+    int kind;           /* 0 rmat, 1 er, 2 torus, 3 relabel, 4 power law */
     int64_t lo, hi;     /* edge range */
     int scale;
     uint64_t n;
@@ -120,9 +128,19 @@ typedef struct {
     int permute;
     const gg_perm* perm;
     int64_t side;
+    double pa, ps, pinv, pi0;   /* power law: i0^b, (n+i0)^b - i0^b, 1/b, i0 */
     int32_t* src;
     int32_t* dst;
 } gg_job;
+
+/* one end of a power-law edge: the inverse CDF at the uniform u in [0, 1) */
+static inline uint64_t gg_powerlaw_end(const gg_job* j, uint64_t r) {
+    const double u = (double)(r >> 11) * (1.0 / 9007199254740992.0);
+    double x = pow(u * j->ps + j->pa, j->pinv) - j->pi0;
+    if (!(x >= 0.0)) x = 0.0;
+    uint64_t id = (uint64_t)x;
+    return id < j->n ? id : j->n - 1;
+}
 
 static void gg_run_job(gg_job* j) {
     if (j->kind == 0) {
@@ -148,6 +166,14 @@ static void gg_run_job(gg_job* j) {
         for (int64_t i = j->lo; i < j->hi; i++) {
             uint64_t u = gg_below(gg_rand(j->key, 2 * (uint64_t)i), j->n);
             uint64_t v = gg_below(gg_rand(j->key, 2 * (uint64_t)i + 1), j->n);
+            if (j->permute) { u = gg_perm_apply(j->perm, u); v = gg_perm_apply(j->perm, v); }
+            j->src[i] = (int32_t)u;
+            j->dst[i] = (int32_t)v;
+        }
+    } else if (j->kind == 4) {
+        for (int64_t i = j->lo; i < j->hi; i++) {
+            uint64_t u = gg_powerlaw_end(j, gg_rand(j->key, 2 * (uint64_t)i));
+            uint64_t v = gg_powerlaw_end(j, gg_rand(j->key, 2 * (uint64_t)i + 1));
             if (j->permute) { u = gg_perm_apply(j->perm, u); v = gg_perm_apply(j->perm, v); }
             j->src[i] = (int32_t)u;
             j->dst[i] = (int32_t)v;
@@ -238,6 +264,34 @@ int gg_er(int64_t n, int64_t m, uint64_t seed, int permute, int32_t* src, int32_
     j.kind = 1;
     j.n = (uint64_t)n;
     j.key = gg_stream_key(seed, 0x6572ULL);
+    j.permute = permute;
+    j.perm = &perm;
+    j.src = src;
+    j.dst = dst;
+    gg_parallel(&j, m, nthreads);
+    return 0;
+}
+
+/*
+ * Power-law expected-degree graph: m edges, both ends drawn with density
+ * proportional to (x + i0)^(-1/(gamma-1)) on [0, n), gamma > 2 (so the
+ * exponent 1/(gamma-1) < 1), i0 > 0.  n <= 2^31-1.
+ */
+int gg_powerlaw(int64_t n, int64_t m, double gamma, double i0, uint64_t seed, int permute, int32_t* src,
+                int32_t* dst, int nthreads) {
+    if (n < 1 || n > 2147483647LL || m < 0 || !(gamma > 2.0) || !(i0 > 0.0)) return -1;
+    const double b = 1.0 - 1.0 / (gamma - 1.0);
+    gg_perm perm;
+    gg_perm_init(&perm, (uint64_t)n, seed);
+    gg_job j;
+    memset(&j, 0, sizeof j);
+    j.kind = 4;
+    j.n = (uint64_t)n;
+    j.pi0 = i0;
+    j.pa = pow(i0, b);
+    j.ps = pow((double)n + i0, b) - j.pa;
+    j.pinv = 1.0 / b;
+    j.key = gg_stream_key(seed, 0x706c6177ULL);
     j.permute = permute;
     j.perm = &perm;
     j.src = src;

@@ -499,3 +499,30 @@ def test_launch_knobs_keep_levels_exact(gpu_lib):
             case.run(0, bfs.options(**kw))
         assert ex.value.status == 1
     g.close()
+
+
+def test_powerlaw_graph_bench_configuration(gpu_lib):
+    """The Twitter-sized workload's generator (power-law expected degrees, exponent 2.1,
+    rank offset 50) at 1/32 of its size (1.92 M vertices, 45.9 M edges), searched as
+    bench.py searches it: levels bit-exact for 3 roots, parents certified, per-level
+    counters equal to the oracle's schedule over the hub-first rows."""
+    import torch
+    bfs = gpu_lib
+    e = graphgen.powerlaw(61_500_000 // 32, 1_470_000_000 // 32, 2.1, 50.0, seed=4000)
+    ref = oracle.build_csr(e.n, e.src, e.dst)
+    labels = oracle.components(ref)
+    h = oracle.hub_first_rows(ref)
+    g = bfs.Graph.from_edges(e.src, e.dst, e.n, hub_first=True)
+    level = torch.empty(e.n, dtype=torch.int32, device="cuda")
+    parent = torch.empty(e.n, dtype=torch.int32, device="cuda")
+    opts = bfs.options(bu_rows=bfs.BU_ROWS_HUB_FIRST)
+    for root in graphgen.pick_roots(e, 3, 4001).tolist():
+        info = g.run(root, parent=parent, level=level, opts=opts, stats=True, record_levels=256)
+        lv, pa = level.cpu().numpy(), parent.cpu().numpy()
+        want = oracle.levels(ref, root)
+        assert np.array_equal(lv, want), root
+        assert oracle.certify(ref, root, lv, pa, labels) == (0, -1), root
+        s = oracle.do_schedule(h, want, oracle.MODE_DO, 14, 24)
+        for col, name in enumerate(["dir", "nf", "mf", "nnext", "mnext", "scanned", "examined"]):
+            assert np.array_equal(info["records"][:, col], getattr(s, name)), (root, name)
+    g.close()

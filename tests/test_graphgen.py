@@ -92,3 +92,30 @@ def test_workload_seeds():
     w = workloads.RMAT[12]
     assert w.graph_seed == 1012 and w.root_seed == 1001012
     assert workloads.ER26.graph_seed == 2026 and workloads.TORUS4096.graph_seed == 3000
+
+
+def test_powerlaw_generator_deterministic_and_follows_its_cdf():
+    """The power-law generator gives one edge list per seed whatever the thread count,
+    keeps ids in range, and (unpermuted) its endpoint ranks follow the closed-form CDF
+    G(x) = ((x + i0)^b - i0^b) / ((n + i0)^b - i0^b), b = 1 - 1/(gamma - 1), within
+    sampling error."""
+    import math
+    n, m, gamma, i0 = 200_000, 400_000, 2.1, 50.0
+    a = graphgen.powerlaw(n, m, gamma, i0, seed=11, threads=1)
+    b = graphgen.powerlaw(n, m, gamma, i0, seed=11, threads=4)
+    assert np.array_equal(a.src, b.src) and np.array_equal(a.dst, b.dst)
+    assert a.src.min() >= 0 and max(a.src.max(), a.dst.max()) < n
+    c = graphgen.powerlaw(n, m, gamma, i0, seed=12, threads=2)
+    assert not np.array_equal(a.src, c.src)
+    raw = graphgen.powerlaw(n, m, gamma, i0, seed=11, permute=False, threads=2)
+    ends = np.concatenate([raw.src, raw.dst]).astype(np.int64)
+    bb = 1.0 - 1.0 / (gamma - 1.0)
+    for x in (1, 10, 100, 1000, 10_000, 100_000):
+        want = ((x + i0) ** bb - i0 ** bb) / ((n + i0) ** bb - i0 ** bb)
+        got = float(np.mean(ends < x))
+        sd = math.sqrt(want * (1 - want) / ends.size)
+        assert abs(got - want) < 6 * sd + 1e-6, (x, got, want)
+    # a permutation of the unpermuted graph: same degree multiset
+    da = np.sort(np.bincount(np.concatenate([a.src, a.dst]), minlength=n))
+    dr = np.sort(np.bincount(ends, minlength=n))
+    assert np.array_equal(da, dr)
