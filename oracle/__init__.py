@@ -21,6 +21,10 @@ Contents (each cites the passage of Bulu\\c{c} et al. 2015 it follows):
                              direction-optimizing search ("Parallel Direction-Optimizing BFS") (C)
 * :func:`dcsc_tiles`      -- DCSC of the row-block x column-block tiles ("Graph Representation":
                              IR row ids, JC non-empty column ids, CP column pointers), numpy
+* :func:`build_digraph`, :func:`do_schedule_dir`, :func:`reach`, :func:`certify_dir`
+                          -- directed graphs: out-edge CSR and its transpose, the
+                             schedule with out-/in-degree sums, depth-first
+                             reachability, the invariants along directed edges (C)
 * :func:`brute_force_levels` -- all-pairs unit-weight relaxation to a fixpoint
                              (Bellman-Ford style), numpy, tiny graphs only
 
@@ -76,6 +80,12 @@ def _load():
         L.or_do_schedule.restype = i32
         L.or_hub_first.argtypes = [i64, vp, vp, vp, i64, i64]
         L.or_hub_first.restype = i32
+        L.or_do_schedule_dir.argtypes = [i64, vp, vp, vp, vp, i32, i64, i64, i32] + [vp] * 7
+        L.or_do_schedule_dir.restype = i32
+        L.or_reach.argtypes = [i64, vp, vp, i32, vp]
+        L.or_reach.restype = i64
+        L.or_certify_dir.argtypes = [i64, vp, vp, i32, vp, vp, vp]
+        L.or_certify_dir.restype = i64
         _lib = L
     return _lib
 
@@ -99,7 +109,7 @@ class CSR:
         return np.diff(self.offsets)
 
 
-def build_csr(n: int, src: np.ndarray, dst: np.ndarray, chunk: int = 1 << 26) -> CSR:
+def build_csr(n: int, src: np.ndarray, dst: np.ndarray, chunk: int = 1 << 26, directed: bool = False) -> CSR:
     """CSR of the undirected graph ("Graph Representation": sorted adjacencies,
     each undirected edge stored in both rows, an n+1 row-pointer array; "Data
     Sets": duplicate edges pruned).  Self-loops are dropped.
@@ -108,7 +118,10 @@ def build_csr(n: int, src: np.ndarray, dst: np.ndarray, chunk: int = 1 << 26) ->
     u != v} as 64-bit keys u*2^32 + v, sorted (numpy's sort, a library
     primitive), repeats removed; the low halves are the column ids and the
     row lengths are counts of the high halves.  Chunked only to bound host
-    memory (about 8 bytes per directed entry plus the 4-byte result)."""
+    memory (about 8 bytes per directed entry plus the 4-byte result).
+
+    directed=True keeps only (u, v) for an input edge u -> v: the out-edge CSR
+    of a directed graph (the method "applies to directed graphs", "Data Sets")."""
     src = np.asarray(src)
     dst = np.asarray(dst)
     m = int(src.shape[0])
@@ -117,7 +130,7 @@ def build_csr(n: int, src: np.ndarray, dst: np.ndarray, chunk: int = 1 << 26) ->
     keep_total = 0
     for a in range(0, m, chunk):
         keep_total += int(np.count_nonzero(src[a:a + chunk] != dst[a:a + chunk]))
-    keys = np.empty(2 * keep_total, np.uint64)
+    keys = np.empty((1 if directed else 2) * keep_total, np.uint64)
     w = 0
     for a in range(0, m, chunk):
         u = src[a:a + chunk].astype(np.uint64)
@@ -126,7 +139,8 @@ def build_csr(n: int, src: np.ndarray, dst: np.ndarray, chunk: int = 1 << 26) ->
         u, v = u[k], v[k]
         c = u.shape[0]
         keys[w:w + c] = (u << np.uint64(32)) | v
-        keys[keep_total + w:keep_total + w + c] = (v << np.uint64(32)) | u
+        if not directed:
+            keys[keep_total + w:keep_total + w + c] = (v << np.uint64(32)) | u
         w += c
     keys.sort()
     # drop repeats in place (the write cursor never passes the read cursor)
@@ -276,15 +290,65 @@ def do_schedule(g: CSR, level: np.ndarray, mode: int = MODE_DO, alpha: int = 14,
     return Schedule(*[a[:L].copy() for a in arrs])
 
 
-def brute_force_levels(n: int, src: np.ndarray, dst: np.ndarray, root: int) -> np.ndarray:
+def build_digraph(n: int, src: np.ndarray, dst: np.ndarray) -> tuple[CSR, CSR]:
+    """(out, inn): the out-edge CSR of the directed graph {u -> v : (u, v) an input
+    edge, u != v} and its transpose (the in-edge CSR, each row the sorted sources of
+    the edges into that vertex), the second adjacency a bottom-up step needs ("Data
+    Decomposition": the transpose).  Each is the set definition of build_csr."""
+    return build_csr(n, src, dst, directed=True), build_csr(n, dst, src, directed=True)
+
+
+def do_schedule_dir(out: CSR, inn: CSR, level: np.ndarray, mode: int = 0, alpha: int = 14,
+                    beta: int = 24) -> "Schedule":
+    """The direction-optimizing schedule of a directed search: m_f sums out-degrees of
+    the frontier, m_u in-degrees of the unreached vertices, bottom-up steps scan in-rows."""
+    level = np.ascontiguousarray(level, np.int32)
+    cap = int(level.max()) + 2 if level.size else 2
+    arrs = [np.zeros(cap, np.int32)] + [np.zeros(cap, np.int64) for _ in range(6)]
+    L = _load().or_do_schedule_dir(out.n, _ptr(out.offsets), _ptr(inn.offsets), _ptr(inn.cols), _ptr(level), mode,
+                                   alpha, beta, cap, *[_ptr(a) for a in arrs])
+    if L < 0:
+        raise RuntimeError("schedule capacity")
+    return Schedule(*[a[:L].copy() for a in arrs])
+
+
+def reach(out: CSR, root: int) -> np.ndarray:
+    """bool[n]: vertices reachable from root along out-edges (depth-first search)."""
+    mark = np.zeros(out.n, np.uint8)
+    if _load().or_reach(out.n, _ptr(out.offsets), _ptr(out.cols), int(root), _ptr(mark)) < 0:
+        raise MemoryError("or_reach: scratch allocation failed")
+    return mark.astype(bool)
+
+
+def certify_dir(out: CSR, root: int, level: np.ndarray, parent: np.ndarray | None = None,
+                reached: np.ndarray | None = None) -> tuple[int, int]:
+    """(0, -1) if (level, parent) is a BFS from root along out-edges, else (failed
+    invariant code, vertex).  See or_certify_dir in oracle.c."""
+    if reached is None:
+        reached = reach(out, root)
+    level = np.ascontiguousarray(level, np.int32)
+    if parent is not None:
+        parent = np.ascontiguousarray(parent, np.int32)
+    r = _load().or_certify_dir(out.n, _ptr(out.offsets), _ptr(out.cols), int(root), _ptr(parent), _ptr(level),
+                               _ptr(np.ascontiguousarray(reached, np.uint8)))
+    if r == 0:
+        return 0, -1
+    return int(r >> 40), int(r & ((1 << 40) - 1))
+
+
+def brute_force_levels(n: int, src: np.ndarray, dst: np.ndarray, root: int, directed: bool = False) -> np.ndarray:
     """Unit-weight relaxation d[v] = min(d[v], d[u] + 1) over every edge, both
-    directions, until nothing changes (Bellman-Ford style).  Self-loops and
-    duplicates are harmless here.  O(n * m): tiny graphs only."""
+    directions (only u -> v with directed=True), until nothing changes
+    (Bellman-Ford style).  Self-loops and duplicates are harmless here.
+    O(n * m): tiny graphs only."""
     INF = np.iinfo(np.int64).max // 4
     d = np.full(n, INF, np.int64)
     d[root] = 0
-    s = np.concatenate([np.asarray(src, np.int64), np.asarray(dst, np.int64)])
-    t = np.concatenate([np.asarray(dst, np.int64), np.asarray(src, np.int64)])
+    if directed:
+        s, t = np.asarray(src, np.int64), np.asarray(dst, np.int64)
+    else:
+        s = np.concatenate([np.asarray(src, np.int64), np.asarray(dst, np.int64)])
+        t = np.concatenate([np.asarray(dst, np.int64), np.asarray(src, np.int64)])
     for _ in range(n + 1):
         cand = d[s] + 1
         new = d.copy()

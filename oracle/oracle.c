@@ -30,6 +30,12 @@
  *                    Direction-Optimizing BFS"): per level the direction chosen
  *                    by the edges-out-of-frontier / frontier-size heuristics,
  *                    and the per-level work counts that the byte model uses.
+ *  or_do_schedule_dir the same schedule on a directed graph (top-down over
+ *                    out-edges, bottom-up over in-edges: "Data Sets" says the
+ *                    method applies to directed graphs, and the bottom-up step
+ *                    needs the transpose, "Data Decomposition").
+ *  or_reach          depth-first reachability (the reached set, independently).
+ *  or_certify_dir    the BFS invariants along directed edges.
  *  or_hub_first      the rows in the order a bottom-up step may scan them:
  *                    neighbours by degree, highest first, ties by id (Algorithm
  *                    2 fixes no order beyond "in order"); each row sorted on
@@ -239,24 +245,49 @@ int64_t or_certify(int64_t n, const int64_t* off, const int32_t* cols, int32_t r
  *               order, or the degree if none (the serial early-exit count)
  * Returns num_levels, or -1 if cap is too small.
  */
+int32_t or_do_schedule_dir(int64_t n, const int64_t* off_out, const int64_t* off_bu, const int32_t* cols_bu,
+                           const int32_t* level, int32_t mode, int64_t alpha, int64_t beta, int32_t cap,
+                           int32_t* dir, int64_t* nf, int64_t* mf, int64_t* nnext, int64_t* mnext,
+                           int64_t* scanned, int64_t* examined);
+
 int32_t or_do_schedule(int64_t n, const int64_t* off, const int32_t* cols, const int32_t* level,
                        int32_t mode, int64_t alpha, int64_t beta, int32_t cap,
                        int32_t* dir, int64_t* nf, int64_t* mf, int64_t* nnext, int64_t* mnext,
                        int64_t* scanned, int64_t* examined) {
+    return or_do_schedule_dir(n, off, off, cols, level, mode, alpha, beta, cap, dir, nf, mf, nnext, mnext,
+                              scanned, examined);
+}
+
+/*
+ * The same schedule on a directed graph: a top-down step expands the
+ * frontier's out-edges (off_out), a bottom-up step lets an unvisited vertex
+ * scan its in-edges (the transpose: off_bu, cols_bu), so m_f = sum of
+ * out-degrees over the frontier and m_u = sum of in-degrees over the vertices
+ * not yet reached (the edges a bottom-up step could still examine); scanned
+ * counts unvisited vertices with in-degree > 0; mnext is the out-degree sum
+ * of the next frontier.  With off_out == off_bu (an undirected graph) this is
+ * or_do_schedule.
+ */
+int32_t or_do_schedule_dir(int64_t n, const int64_t* off_out, const int64_t* off_bu, const int32_t* cols_bu,
+                           const int32_t* level, int32_t mode, int64_t alpha, int64_t beta, int32_t cap,
+                           int32_t* dir, int64_t* nf, int64_t* mf, int64_t* nnext, int64_t* mnext,
+                           int64_t* scanned, int64_t* examined) {
     int32_t L = 0;
     for (int64_t v = 0; v < n; v++) if (level[v] + 1 > L) L = level[v] + 1;
     if (L > cap) return -1;
     int64_t* cnt = (int64_t*)calloc((size_t)L + 1, sizeof(int64_t));
-    int64_t* deg = (int64_t*)calloc((size_t)L + 1, sizeof(int64_t));
-    int64_t total_deg_unreached = 0, nnz = off[n];
+    int64_t* deg = (int64_t*)calloc((size_t)L + 1, sizeof(int64_t));     /* out-degree sum per level */
+    int64_t* ideg = (int64_t*)calloc((size_t)L + 1, sizeof(int64_t));    /* in-degree sum per level */
+    int64_t nnz_in = off_bu[n];
     for (int64_t v = 0; v < n; v++) {
-        int64_t dv = off[v + 1] - off[v];
-        if (level[v] >= 0) { cnt[level[v]]++; deg[level[v]] += dv; }
-        else total_deg_unreached += dv;
+        if (level[v] >= 0) {
+            cnt[level[v]]++;
+            deg[level[v]] += off_out[v + 1] - off_out[v];
+            ideg[level[v]] += off_bu[v + 1] - off_bu[v];
+        }
     }
-    (void)total_deg_unreached;
-    int64_t m_u = nnz - deg[0];     /* degree sum of vertices not in levels 0..d */
-    int32_t cur = 0;                /* start top-down */
+    int64_t m_u = nnz_in - ideg[0];   /* in-degree sum of vertices not in levels 0..d */
+    int32_t cur = 0;                  /* start top-down */
     for (int32_t d = 0; d < L; d++) {
         int64_t n_f = cnt[d], m_f = deg[d];
         if (mode == 1) cur = 0;
@@ -275,22 +306,114 @@ int32_t or_do_schedule(int64_t n, const int64_t* off, const int32_t* cols, const
             int64_t sc = 0, ex = 0;
             for (int64_t u = 0; u < n; u++) {
                 if (level[u] >= 0 && level[u] <= d) continue;   /* already visited */
-                int64_t b = off[u], e = off[u + 1];
-                if (e == b) continue;                          /* degree 0 never searches */
+                int64_t b = off_bu[u], e = off_bu[u + 1];
+                if (e == b) continue;                          /* no in-edge: never searches */
                 sc++;
                 int64_t pos = e - b;
                 for (int64_t k = b; k < e; k++)
-                    if (level[cols[k]] == d) { pos = k - b + 1; break; }
+                    if (level[cols_bu[k]] == d) { pos = k - b + 1; break; }
                 ex += pos;
             }
             scanned[d] = sc;
             examined[d] = ex;
         }
-        m_u -= deg[d + 1];
+        m_u -= ideg[d + 1];
     }
     free(cnt);
     free(deg);
+    free(ideg);
     return L;
+}
+
+/* ------------------------------------------------------------------ directed graphs */
+
+/*
+ * Vertices reachable from root along out-edges, by an explicit-stack depth-
+ * first search (a different traversal order from breadth-first search, used
+ * to check the reached set independently).  mark[v] = 1 if reachable.
+ * Returns the number reached, or -1 if scratch memory could not be allocated.
+ */
+int64_t or_reach(int64_t n, const int64_t* off, const int32_t* cols, int32_t root, uint8_t* mark) {
+    int32_t* stack = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    if (!stack) return -1;
+    for (int64_t v = 0; v < n; v++) mark[v] = 0;
+    int64_t top = 0, cnt = 1;
+    stack[top++] = root;
+    mark[root] = 1;
+    while (top > 0) {
+        int32_t u = stack[--top];
+        for (int64_t k = off[u]; k < off[u + 1]; k++) {
+            int32_t v = cols[k];
+            if (!mark[v]) {
+                mark[v] = 1;
+                cnt++;
+                stack[top++] = v;
+            }
+        }
+    }
+    free(stack);
+    return cnt;
+}
+
+/*
+ * Check that (level, parent) is a breadth-first search from root along the
+ * out-edges of a directed graph (off/cols = the out-edge CSR):
+ *   1 level[root] = 0 and parent[root] = root (when parent is given)
+ *   2 for every reached v != root: level[v] >= 1, (parent[v] -> v) is an edge,
+ *     level[parent[v]] = level[v] - 1 (without parents: some in-neighbour of v
+ *     sits at level[v] - 1, found by scanning the out-rows of all vertices)
+ *   3 every edge u -> v out of a reached u ends at a reached v with
+ *     level[v] <= level[u] + 1
+ *   4 (unused code, kept apart from the undirected checker's numbering)
+ *   5 the reached set is exactly reach[] (or_reach) and unreached vertices
+ *     carry parent = level = -1.
+ * 2 gives dist <= level along the parent chain, 3 gives level <= dist along a
+ * shortest directed path; together level = dist.  Returns 0 if valid, else
+ * (code << 40) | vertex.
+ */
+int64_t or_certify_dir(int64_t n, const int64_t* off, const int32_t* cols, int32_t root, const int32_t* parent,
+                       const int32_t* level, const uint8_t* reach) {
+    if (root < 0 || root >= n) return (int64_t)1 << 40;
+    if (level[root] != 0) return ((int64_t)1 << 40) | root;
+    if (parent && parent[root] != root) return ((int64_t)1 << 40) | root;
+    uint8_t* has_pred = NULL;
+    if (!parent) {
+        has_pred = (uint8_t*)calloc((size_t)(n > 0 ? n : 1), 1);
+        if (!has_pred) return ((int64_t)6 << 40);
+        for (int64_t u = 0; u < n; u++) {
+            if (level[u] < 0) continue;
+            for (int64_t k = off[u]; k < off[u + 1]; k++)
+                if (level[cols[k]] == level[u] + 1) has_pred[cols[k]] = 1;
+        }
+    }
+    int64_t bad = 0;
+    for (int64_t v = 0; v < n && !bad; v++) {
+        int reached = level[v] >= 0;
+        if (reached != (reach[v] != 0)) { bad = ((int64_t)5 << 40) | v; break; }
+        if (!reached) {
+            if (level[v] != -1 || (parent && parent[v] != -1)) bad = ((int64_t)5 << 40) | v;
+            continue;
+        }
+        if (v != root) {
+            if (level[v] < 1) { bad = ((int64_t)2 << 40) | v; break; }
+            if (parent) {
+                int32_t p = parent[v];
+                if (p < 0 || p >= n || !or_has_edge(off, cols, p, (int32_t)v) || level[p] != level[v] - 1) {
+                    bad = ((int64_t)2 << 40) | v;
+                    break;
+                }
+            } else if (!has_pred[v]) {
+                bad = ((int64_t)2 << 40) | v;
+                break;
+            }
+        }
+        for (int64_t k = off[v]; k < off[v + 1]; k++) {
+            int32_t u = cols[k];
+            if (level[u] < 0 || level[u] > level[v] + 1) { bad = ((int64_t)3 << 40) | v; break; }
+        }
+    }
+    free(has_pred);
+    return bad;
 }
 
 /* ------------------------------------------------------------------ hub-first rows */

@@ -414,3 +414,116 @@ def test_hub_first_schedule_counts_follow_row_order(seed):
             if hits.size:
                 assert deg[row[hits[0]]] == deg[row[lv[row] == d]].max()
         assert total == s.examined[d]
+
+
+# ------------------------------------------------------------------ directed graphs
+
+def _digraphs():
+    gs = [graphgen.random_small(n, m, s) for n, m, s in [(2, 1, 1), (9, 20, 2), (40, 90, 3), (64, 300, 4),
+                                                         (130, 260, 5)]]
+    gs.append(graphgen.from_pairs(6, [(0, 1), (1, 2), (2, 0), (3, 4), (4, 4), (5, 3), (1, 1), (0, 1)]))
+    gs.append(graphgen.rmat(8, seed=91))
+    return gs
+
+
+@pytest.mark.parametrize("gi", range(7))
+def test_directed_bfs_matches_brute_force_networkx_and_bottom_up(gi):
+    """Directed graphs: Algorithm 1 over the out-edge CSR gives the brute-force
+    directed distances and networkx's directed shortest-path lengths from every root;
+    Algorithm 2 over the transpose gives the same levels; both outputs pass the
+    directed certificate; the reached set equals networkx's descendants."""
+    nx = pytest.importorskip("networkx")
+    e = _digraphs()[gi]
+    out, inn = oracle.build_digraph(e.n, e.src, e.dst)
+    G = nx.DiGraph()
+    G.add_nodes_from(range(e.n))
+    G.add_edges_from((int(u), int(v)) for u, v in zip(e.src, e.dst) if u != v)
+    for root in range(e.n):
+        want = oracle.brute_force_levels(e.n, e.src, e.dst, root, directed=True)
+        nxd = nx.single_source_shortest_path_length(G, root)
+        assert np.array_equal(want, np.array([nxd.get(v, -1) for v in range(e.n)], np.int32))
+        pa, lv, _ = oracle.bfs_topdown(out, root)
+        assert np.array_equal(lv, want), root
+        pb, lb, _ = oracle.bfs_bottomup(inn, root)
+        assert np.array_equal(lb, want), root
+        rch = oracle.reach(out, root)
+        assert set(np.flatnonzero(rch).tolist()) == {root} | set(nx.descendants(G, root))
+        assert oracle.certify_dir(out, root, lv, pa, rch) == (0, -1)
+        assert oracle.certify_dir(out, root, lb, pb, rch) == (0, -1)
+        assert oracle.certify_dir(out, root, lv, None, rch) == (0, -1)
+
+
+def test_build_digraph_is_the_set_definition():
+    e = graphgen.random_small(70, 400, 9)
+    out, inn = oracle.build_digraph(e.n, e.src, e.dst)
+    succ = [set() for _ in range(e.n)]
+    pred = [set() for _ in range(e.n)]
+    for u, v in zip(e.src.tolist(), e.dst.tolist()):
+        if u != v:
+            succ[u].add(v)
+            pred[v].add(u)
+    for u in range(e.n):
+        assert out.cols[out.offsets[u]:out.offsets[u + 1]].tolist() == sorted(succ[u])
+        assert inn.cols[inn.offsets[u]:inn.offsets[u + 1]].tolist() == sorted(pred[u])
+
+
+def test_certify_dir_rejects_planted_mistakes():
+    """Each planted mistake fails the directed certificate with its code; the
+    reversed-parent case is one an undirected checker would accept."""
+    e = graphgen.from_pairs(6, [(0, 1), (1, 2), (2, 3), (4, 0), (3, 5)])
+    out, _ = oracle.build_digraph(e.n, e.src, e.dst)
+    root = 0
+    pa, lv, _ = oracle.bfs_topdown(out, root)
+    assert lv.tolist() == [0, 1, 2, 3, -1, 4]
+    assert oracle.certify_dir(out, root, lv, pa) == (0, -1)
+    bad = lv.copy(); bad[2] = 3; bad[3] = 4; bad[5] = 5           # 1 -> 2 spans two levels
+    assert oracle.certify_dir(out, root, bad, None)[0] in (2, 3)
+    bad = lv.copy(); bad[4] = 1                                     # 4 is not reachable from 0
+    assert oracle.certify_dir(out, root, bad, None) == (5, 4)
+    bad = lv.copy(); bad[5] = -1                                    # 5 is reachable
+    assert oracle.certify_dir(out, root, bad, None)[0] in (3, 5)
+    # 0 -> 1, 0 -> 2, 1 -> 3, 3 -> 2: vertex 3 (level 2) has parent 1; vertex 2 is also one
+    # level closer and joined to 3, but by 3 -> 2 only, so it is not a parent of 3
+    e = graphgen.from_pairs(4, [(0, 1), (0, 2), (1, 3), (3, 2)])
+    out, _ = oracle.build_digraph(e.n, e.src, e.dst)
+    pa, lv, _ = oracle.bfs_topdown(out, 0)
+    assert lv.tolist() == [0, 1, 1, 2] and pa[3] == 1
+    wrong = pa.copy(); wrong[3] = 2
+    assert oracle.certify_dir(out, 0, lv, wrong) == (2, 3)
+    und = oracle.build_csr(e.n, e.src, e.dst)
+    assert oracle.certify(und, 0, lv, wrong) == (0, -1)            # the undirected reading accepts it
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_directed_schedule_counts(seed):
+    """do_schedule_dir: on an undirected graph it is do_schedule; on a directed one its
+    bottom-up examination counts equal a literal Algorithm 2 walk over the in-rows,
+    m_f sums out-degrees of the frontier, and the direction sequence follows the rule
+    with m_u = in-degree sum of the vertices not yet reached, recomputed from scratch."""
+    g = graphgen.rmat(9, seed=500 + seed)
+    c = csr(g)
+    root = int(graphgen.pick_roots(g, 1, seed)[0])
+    lv = oracle.levels(c, root)
+    for mode in (oracle.MODE_DO, oracle.MODE_BU):
+        a = oracle.do_schedule(c, lv, mode)
+        b = oracle.do_schedule_dir(c, c, lv, mode)
+        for name in ("dir", "nf", "mf", "nnext", "mnext", "scanned", "examined"):
+            assert np.array_equal(getattr(a, name), getattr(b, name)), name
+    out, inn = oracle.build_digraph(g.n, g.src, g.dst)
+    pa, lv, _ = oracle.bfs_topdown(out, root)
+    odeg, ideg = out.degree(), inn.degree()
+    s = oracle.do_schedule_dir(out, inn, lv, oracle.MODE_BU)
+    for d in range(s.num_levels):
+        assert (s.scanned[d], s.examined[d]) == _alg2_walk(inn, lv, d)
+        assert s.mf[d] == odeg[lv == d].sum() and s.nf[d] == (lv == d).sum()
+    s = oracle.do_schedule_dir(out, inn, lv, oracle.MODE_DO, 14, 24)
+    cur = 0
+    for d in range(s.num_levels):
+        unreached = (lv < 0) | (lv > d)
+        m_u = int(ideg[unreached].sum())
+        n_f, m_f = int((lv == d).sum()), int(odeg[lv == d].sum())
+        if cur == 0 and m_f * 14 > m_u:
+            cur = 1
+        elif cur == 1 and n_f * 24 < g.n:
+            cur = 0
+        assert s.dir[d] == cur, d
