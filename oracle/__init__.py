@@ -254,8 +254,9 @@ def certify(g: CSR, root: int, level: np.ndarray, parent: np.ndarray | None = No
     level = np.ascontiguousarray(level, np.int32)
     if parent is not None:
         parent = np.ascontiguousarray(parent, np.int32)
+    labels = np.ascontiguousarray(labels, np.int32)   # kept alive across the call
     r = _load().or_certify(g.n, _ptr(g.offsets), _ptr(g.cols), int(root), _ptr(parent), _ptr(level),
-                           _ptr(np.ascontiguousarray(labels, np.int32)))
+                           _ptr(labels))
     if r == 0:
         return 0, -1
     return int(r >> 40), int(r & ((1 << 40) - 1))
@@ -329,8 +330,9 @@ def certify_dir(out: CSR, root: int, level: np.ndarray, parent: np.ndarray | Non
     level = np.ascontiguousarray(level, np.int32)
     if parent is not None:
         parent = np.ascontiguousarray(parent, np.int32)
+    reached = np.ascontiguousarray(reached, np.uint8)   # kept alive across the call
     r = _load().or_certify_dir(out.n, _ptr(out.offsets), _ptr(out.cols), int(root), _ptr(parent), _ptr(level),
-                               _ptr(np.ascontiguousarray(reached, np.uint8)))
+                               _ptr(reached))
     if r == 0:
         return 0, -1
     return int(r >> 40), int(r & ((1 << 40) - 1))
