@@ -34,7 +34,8 @@ served:  continuous-batching server over 8 resident graphs; the sustained
           p99 under 100 ms); Poisson arrivals at 0.25/0.5/0.9 of it, p50/p99
           latency and GTEPS, against a one-at-a-time plain FIFO on the same trace.
 configs: R-MAT 24 over CSR (hub-first and id-ordered rows) and DCSC tiles, each
-          direction-optimizing / top-down only / bottom-up only; Erdos-Renyi
+          direction-optimizing / top-down only / bottom-up only, and as a directed
+          graph (out-rows top-down, their transpose bottom-up); Erdos-Renyi
           n = 2^26; the 4096^2 torus; a Twitter-sized power-law graph (61.5 M
           vertices, 1.47 B edges): a few roots each, GTEPS and roofline.
 
@@ -447,6 +448,15 @@ def configs_section(peak_gbs: float) -> dict:
         line(f"rmat24_csr_{mname}", g, roots, bfs.options(mode=mode, bu_rows=bfs.BU_ROWS_HUB_FIRST), n, m)
         line(f"rmat24_csr_idrows_{mname}", g, roots, bfs.options(mode=mode), n, m)
         line(f"rmat24_dcsc_{mname}", g, roots[:2], bfs.options(mode=mode, layout=bfs.LAYOUT_DCSC_TILED), n, m)
+    g.close()
+    # the same R-MAT edges as a directed graph (edge i: src -> dst; top-down over out-rows,
+    # bottom-up over their transpose); GTEPS over its directed edge count
+    e = w.edges()
+    g = bfs.Graph.from_edges(e.src, e.dst, e.n, directed=True)
+    n, md = e.n, g.nnz
+    del e
+    line("rmat24_directed_do", g, roots, bfs.options(), n, md)
+    out["rmat24_directed_do"]["directed_edges"] = md
     g.close()
     e = workloads.ER26.edges()
     roots = workloads.ER26.roots(e, 8).tolist()

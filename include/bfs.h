@@ -152,10 +152,17 @@ typedef struct {
 /* ----------------------------------------------------------------- graphs */
 
 /*
- * Build a graph from an undirected edge list (src[i], dst[i]), i < n_edges,
- * ids in [0, n_vertices).  Self-loops and duplicate edges are dropped and each
- * row is sorted ascending ("Graph Representation", "Data Sets").  flags must
- * include BFS_FLAG_SYMMETRIZE (directed graphs are not supported).  With
+ * Build a graph from an edge list (src[i], dst[i]), i < n_edges, ids in
+ * [0, n_vertices).  Self-loops and duplicate edges are dropped and each row is
+ * sorted ascending ("Graph Representation", "Data Sets").  With
+ * BFS_FLAG_SYMMETRIZE the graph is undirected (each edge in both rows).
+ * Without it the graph is directed ("Data Sets": the algorithms apply to
+ * directed graphs): edge i runs src[i] -> dst[i]; the library stores the
+ * out-edge rows (top-down steps expand them) and their transpose (the in-edge
+ * rows bottom-up steps scan: "Data Decomposition"), 8*nnz + 8*n more device
+ * bytes; a search follows edge directions; BFS_FLAG_BUILD_DCSC and
+ * BFS_FLAG_BUILD_HUB_FIRST are refused (UNSUPPORTED), and so are
+ * bfs_run_multi and the server on such a graph.  With
  * BFS_FLAG_DEVICE_PTRS, src/dst are device pointers, else host pointers
  * (copied in chunks).  The build runs on `stream` and returns when the graph
  * is ready.  Isolated vertices keep their ids.  *out receives the handle.
@@ -238,6 +245,14 @@ bfs_status bfs_graph_copy_row_heads(const bfs_graph* g, int32_t* heads_out, void
  * built without the flag), CUDA.
  */
 bfs_status bfs_graph_copy_bu_planes(const bfs_graph* g, int32_t* first_out, uint8_t* deg8_out, void* stream);
+
+/*
+ * A directed graph's transpose (the in-edge rows) into caller memory (host or
+ * device): offsets_out int64[n+1], cols_out int32[nnz]; row v holds the sorted
+ * sources of the edges into v.  Synchronises `stream`.  Errors: INVALID (NULL
+ * argument, undirected graph), CUDA.
+ */
+bfs_status bfs_graph_copy_transpose(const bfs_graph* g, int64_t* offsets_out, int32_t* cols_out, void* stream);
 
 /*
  * Device pointers of the DCSC tiles built with BFS_FLAG_BUILD_DCSC ("Graph

@@ -61,6 +61,7 @@ SIGNATURES = [
     ("bfs_graph_copy_hub_first", c_i32, [c_vp, c_vp, c_vp]),
     ("bfs_graph_copy_row_heads", c_i32, [c_vp, c_vp, c_vp]),
     ("bfs_graph_copy_bu_planes", c_i32, [c_vp, c_vp, c_vp, c_vp]),
+    ("bfs_graph_copy_transpose", c_i32, [c_vp, c_vp, c_vp, c_vp]),
     ("bfs_graph_dcsc", c_i32, [c_vp, ctypes.POINTER(DcscLayout)]),
     ("bfs_graph_copy_dcsc", c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     ("bfs_graph_destroy", None, [c_vp]),

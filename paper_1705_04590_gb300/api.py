@@ -90,15 +90,17 @@ class Graph:
     # ---------------------------------------------------------------- creation
     @classmethod
     def from_edges(cls, src, dst, n: int, dcsc: bool = False, stream=None, torch_allocator: bool = True,
-                   hub_first: bool = False) -> "Graph":
+                   hub_first: bool = False, directed: bool = False) -> "Graph":
         """src/dst: numpy int32 or int64 arrays (host) or CUDA tensors of either type (device;
         64-bit ids go through bfs_graph_create_from_edges64).  hub_first also
         stores rows ordered by neighbour degree and a 32-byte head per vertex (its degree and
         first 7 reordered ids), 4*nnz + 32*n more device bytes, for bottom-up option
-        bu_rows=BU_ROWS_HUB_FIRST."""
+        bu_rows=BU_ROWS_HUB_FIRST.  directed=True keeps edge i as src[i] -> dst[i] (out-edge
+        rows for top-down steps, their transpose for bottom-up steps)."""
         lib = L.load()
         torch = _torch()
-        flags = L.FLAG_SYMMETRIZE | (L.FLAG_BUILD_DCSC if dcsc else 0) | (L.FLAG_BUILD_HUB_FIRST if hub_first else 0)
+        flags = (0 if directed else L.FLAG_SYMMETRIZE) | (L.FLAG_BUILD_DCSC if dcsc else 0) | \
+            (L.FLAG_BUILD_HUB_FIRST if hub_first else 0)
         if isinstance(src, torch.Tensor):
             if src.numel() != dst.numel():
                 raise ValueError("src and dst differ in length")
@@ -180,6 +182,14 @@ class Graph:
         heads = np.empty((self.n, 8), np.int32)
         L.check(L.load().bfs_graph_copy_row_heads(self._h, heads.ctypes.data, None), "graph_copy_row_heads")
         return heads
+
+    def transpose_host(self):
+        """A directed graph's in-edge rows: (offsets int64[n+1], cols int32[nnz]) on the host."""
+        off = np.empty(self.n + 1, np.int64)
+        cols = np.empty(max(self.nnz, 1), np.int32)
+        L.check(L.load().bfs_graph_copy_transpose(self._h, off.ctypes.data, cols.ctypes.data, None),
+                "graph_copy_transpose")
+        return off, cols[: self.nnz]
 
     def bu_planes_host(self, first: bool = True):
         """(first, deg8): per vertex the first id of its hub-first row with bit 31 set when

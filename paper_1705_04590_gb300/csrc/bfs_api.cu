@@ -60,6 +60,9 @@ static void destroy_graph(bfs_graph* g) {
     if (g->cols_hf) g->mem.release(g->cols_hf, sizeof(int32_t) * (size_t)(g->nnz + kColPad), nullptr);
     if (g->bu_heads) g->mem.release(g->bu_heads, sizeof(int32_t) * 8 * (size_t)g->n, nullptr);
     if (g->bu_first) g->mem.release(g->bu_first, sizeof(int32_t) * (size_t)(g->n + 32), nullptr);
+    if (g->offsets_in) g->mem.release(g->offsets_in, sizeof(int64_t) * (size_t)(g->n + 1), nullptr);
+    if (g->cols_in) g->mem.release(g->cols_in, sizeof(int32_t) * (size_t)(g->nnz + kColPad), nullptr);
+    if (g->deg8_in) g->mem.release(g->deg8_in, (size_t)g->n + 32, nullptr);
     if (g->deg8) g->mem.release(g->deg8, (size_t)g->n + 32, nullptr);
     g->mem.release(g->isolated, sizeof(uint32_t) * (size_t)g->W, nullptr);
     if (g->last_done) cudaEventDestroy(g->last_done);
@@ -161,11 +164,13 @@ bfs_status bfs_graph_create_from_edges(const int32_t* src, const int32_t* dst, i
     if (out) *out = nullptr;
     if (n_edges < 0) return fail(BFS_ERR_INVALID, "n_edges must be >= 0");
     if (n_edges > 0 && (!src || !dst)) return fail(BFS_ERR_INVALID, "src/dst must not be NULL");
-    if (!(flags & BFS_FLAG_SYMMETRIZE))
-        return fail(BFS_ERR_UNSUPPORTED, "only undirected graphs are supported: pass BFS_FLAG_SYMMETRIZE");
+    const bool directed = !(flags & BFS_FLAG_SYMMETRIZE);
+    if (directed && (flags & (BFS_FLAG_BUILD_DCSC | BFS_FLAG_BUILD_HUB_FIRST)))
+        return fail(BFS_ERR_UNSUPPORTED, "directed graphs: DCSC tiles and hub-first rows are not built");
     bfs_graph* g = nullptr;
     bfs_status st = new_graph(n_vertices, alloc, &g);
     if (st != BFS_OK) return st;
+    g->directed = directed;
     cudaStream_t s = (cudaStream_t)stream;
     st = build_csr_from_edges(g, src, dst, n_edges, (flags & BFS_FLAG_DEVICE_PTRS) != 0, s);
     if (st == BFS_OK && (flags & BFS_FLAG_BUILD_DCSC)) st = build_dcsc_tiles(g, s);
@@ -185,11 +190,13 @@ bfs_status bfs_graph_create_from_edges64(const int64_t* src, const int64_t* dst,
     if (out) *out = nullptr;
     if (n_edges < 0) return fail(BFS_ERR_INVALID, "n_edges must be >= 0");
     if (n_edges > 0 && (!src || !dst)) return fail(BFS_ERR_INVALID, "src/dst must not be NULL");
-    if (!(flags & BFS_FLAG_SYMMETRIZE))
-        return fail(BFS_ERR_UNSUPPORTED, "only undirected graphs are supported: pass BFS_FLAG_SYMMETRIZE");
+    const bool directed = !(flags & BFS_FLAG_SYMMETRIZE);
+    if (directed && (flags & (BFS_FLAG_BUILD_DCSC | BFS_FLAG_BUILD_HUB_FIRST)))
+        return fail(BFS_ERR_UNSUPPORTED, "directed graphs: DCSC tiles and hub-first rows are not built");
     bfs_graph* g = nullptr;
     bfs_status st = new_graph(n_vertices, alloc, &g);
     if (st != BFS_OK) return st;
+    g->directed = directed;
     cudaStream_t s = (cudaStream_t)stream;
     st = build_csr_from_edges64(g, src, dst, n_edges, (flags & BFS_FLAG_DEVICE_PTRS) != 0, s);
     if (st == BFS_OK && (flags & BFS_FLAG_BUILD_DCSC)) st = build_dcsc_tiles(g, s);
@@ -271,6 +278,17 @@ bfs_status bfs_graph_copy_row_heads(const bfs_graph* g, int32_t* heads_out, void
     if (!g->bu_heads) return fail(BFS_ERR_INVALID, "graph was built without BFS_FLAG_BUILD_HUB_FIRST");
     cudaStream_t s = (cudaStream_t)stream;
     BFS_CUDA_TRY(cudaMemcpyAsync(heads_out, g->bu_heads, sizeof(int32_t) * 8 * (size_t)g->n, cudaMemcpyDefault, s));
+    BFS_CUDA_TRY(cudaStreamSynchronize(s));
+    return BFS_OK;
+}
+
+bfs_status bfs_graph_copy_transpose(const bfs_graph* g, int64_t* offsets_out, int32_t* cols_out, void* stream) {
+    if (!g || !offsets_out || !cols_out) return fail(BFS_ERR_INVALID, "NULL argument");
+    if (!g->directed) return fail(BFS_ERR_INVALID, "the graph is undirected: its rows are their own transpose");
+    cudaStream_t s = (cudaStream_t)stream;
+    BFS_CUDA_TRY(cudaMemcpyAsync(offsets_out, g->offsets_in, sizeof(int64_t) * (size_t)(g->n + 1), cudaMemcpyDefault, s));
+    if (g->nnz > 0)
+        BFS_CUDA_TRY(cudaMemcpyAsync(cols_out, g->cols_in, sizeof(int32_t) * (size_t)g->nnz, cudaMemcpyDefault, s));
     BFS_CUDA_TRY(cudaStreamSynchronize(s));
     return BFS_OK;
 }
@@ -365,6 +383,7 @@ bfs_status bfs_run_multiroot(bfs_graph* g, const int32_t* roots_host, int32_t k,
 bfs_status bfs_run_multi(bfs_graph* g, const int32_t* roots_host, int32_t k, int32_t* level_dev, int32_t* parent_dev,
                          const bfs_options* opt, void* stream) {
     if (!g) return fail(BFS_ERR_INVALID, "graph handle is NULL");
+    if (g->directed) return fail(BFS_ERR_UNSUPPORTED, "multi-source search: undirected graphs only");
     if (!roots_host || k < 1) return fail(BFS_ERR_INVALID, "need k >= 1 roots");
     if (!level_dev) return fail(BFS_ERR_INVALID, "level_dev must not be NULL");
     for (int32_t i = 0; i < k; i++)

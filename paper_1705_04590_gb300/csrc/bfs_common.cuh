@@ -46,6 +46,8 @@ struct Ctrl {
     unsigned long long examined[3];  // serial early-exit examinations of that level
     unsigned long long ntask[3];     // top-down edge-chunk tasks of that level
     unsigned long long nmiss[3];     // bottom-up searchers whose first probe missed (miss-list length)
+    unsigned long long dsum_out[3];  // directed graphs: out-degree sum of frontier `slot`
+    unsigned long long dsum_in[3];   // directed graphs: in-degree sum of frontier `slot`
     long long num_levels;
     long long reached;
     unsigned long long t_enter;    // lead CTA's clock at kernel entry

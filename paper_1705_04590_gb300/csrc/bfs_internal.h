@@ -103,7 +103,13 @@ struct bfs_graph {
     int32_t* bu_heads = nullptr;
     // [n + 32] first id of each hub-first row (0 for degree 0), built with the heads
     int32_t* bu_first = nullptr;
-    uint8_t* deg8 = nullptr;        // [n + 32] min(deg(v), 255)
+    uint8_t* deg8 = nullptr;        // [n + 32] min(deg(v), 255) (out-degree of a directed graph)
+    // a directed graph: offsets/cols hold the out-edge rows (top-down), these the
+    // transpose (the in-edge rows a bottom-up step scans); null when undirected
+    bool directed = false;
+    int64_t* offsets_in = nullptr;  // [n+1]
+    int32_t* cols_in = nullptr;     // [nnz + kColPad]
+    uint8_t* deg8_in = nullptr;     // [n + 32] min(in-degree, 255)
     int64_t W = 0;                  // bitmap words
     int64_t n_active = 0;           // vertices with degree > 0
     int32_t debug_barrier_extra = 0;   // testing: arrivals every grid barrier waits for in vain

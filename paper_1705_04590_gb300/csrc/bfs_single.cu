@@ -78,6 +78,11 @@ struct SingleParams {
     // order
     const int* __restrict__ first;
     const unsigned char* __restrict__ deg8;   // min(deg(u), 255); null: degrees from the offsets
+    // the rows bottom-up steps scan: cols_bu with these offsets (off itself, or on a
+    // directed graph the transpose's: the in-edge rows)
+    const long long* __restrict__ off_bu;
+    const unsigned char* __restrict__ deg8_in;   // directed: min(in-degree, 255)
+    int directed;     // 1: off/cols are out-edge rows, off_bu/cols_bu in-edge rows
     const unsigned* __restrict__ isolated;
     long long n, nnz, W;
     int* parent;
@@ -212,9 +217,15 @@ __device__ __forceinline__ void row_of(const SingleParams& p, int u, long long& 
     e = __ldg(p.off + u + 1);
 }
 
-__device__ __forceinline__ void row_of_stream(const SingleParams& p, int u, long long& s, long long& e) {
-    s = ld_stream64(p.off + u);
-    e = ld_stream64(p.off + u + 1);
+// row u of the rows bottom-up steps scan (cols_bu)
+__device__ __forceinline__ void bu_row_of(const SingleParams& p, int u, long long& s, long long& e) {
+    s = __ldg(p.off_bu + u);
+    e = __ldg(p.off_bu + u + 1);
+}
+
+__device__ __forceinline__ void bu_row_of_stream(const SingleParams& p, int u, long long& s, long long& e) {
+    s = ld_stream64(p.off_bu + u);
+    e = ld_stream64(p.off_bu + u + 1);
 }
 
 __device__ __forceinline__ long long deg_of(const SingleParams& p, int u) {
@@ -397,15 +408,20 @@ __device__ void init_phase(const SingleParams& p) {
 // multi-root seeding (after the fill): roots already sit in queue0.
 __device__ void seed_roots_phase(const SingleParams& p) {
     const long long tid = gtid(), nth = gthreads();
-    unsigned long long m = 0;
+    unsigned long long m = 0, mi = 0;
     for (long long i = tid; i < p.nroots; i += nth) {
         const int r = __ldcg(p.queue0 + i);
         atomicOr(p.visited + (r >> 5), 1u << (r & 31));
         if (p.parent) p.parent[r] = r;
         set_level(p, r, 0);
         m += (unsigned long long)deg_of(p, r);
+        if (p.directed) {
+            long long s, e;
+            bu_row_of(p, r, s, e);
+            mi += (unsigned long long)(e - s);
+        }
     }
-    block_add4(m, 0, 0, 0, &p.ctrl->accm[0], nullptr, nullptr, nullptr);
+    block_add4(m, mi, 0, 0, &p.ctrl->accm[0], &p.ctrl->dsum_in[0], nullptr, nullptr);
     if (tid == 0) p.ctrl->tail[0] = (unsigned long long)p.nroots;
 }
 
@@ -639,8 +655,9 @@ __device__ void task_phase(const SingleParams& p, int d, long long ntask, int* q
 
 // parent_mode MIN_ID, after the last level: every reached v other than a root
 // takes the smallest neighbour one level closer, min{u in adj(v) : level(u) =
-// level(v) - 1} (the (select2nd, min) semiring of the top-down local discovery;
-// rows are sorted, so the first such u in the row).  Bottom-up levels over the
+// level(v) - 1} (on a directed graph the smallest u with u -> v; the (select2nd,
+// min) semiring of the top-down local discovery; rows are sorted, so the first
+// such u in the row).  Bottom-up levels over the
 // id-ordered rows already found exactly that parent; top-down claims did not.
 // One pass after the loop instead of one per top-down level keeps the level
 // loop's register budget free of it.
@@ -650,12 +667,51 @@ __device__ void min_parent_pass(const SingleParams& p) {
         const int lv = get_level(p, (int)v);
         if (lv <= 0) continue;
         long long s, e;
-        row_of(p, (int)v, s, e);
+        bu_row_of(p, (int)v, s, e);   // the neighbours (in-neighbours of a directed graph), id order
         for (long long k = s; k < e; k++) {
-            const int u = __ldg(p.cols + k);
+            const int u = __ldg(p.cols_bu + k);
             if (get_level(p, u) == lv - 1) {
                 p.parent[v] = u;
                 break;
+            }
+        }
+    }
+}
+
+// A directed graph's new frontier, after its level: the sum of its out-degrees
+// (m_f of the direction rule) and of its in-degrees (what m_u, the in-degree
+// sum of the unreached vertices, loses).  The frontier is the queue q[0..nq)
+// after a top-down level (q non-null), else the bitmap f.
+__device__ __forceinline__ long long out_degree(const SingleParams& p, int v) {
+    const unsigned d8 = __ldg(p.deg8 + v);
+    return d8 < 255u ? (long long)d8 : deg_of(p, v);
+}
+
+__device__ __forceinline__ long long in_degree(const SingleParams& p, int v) {
+    const unsigned d8 = __ldg(p.deg8_in + v);
+    if (d8 < 255u) return (long long)d8;
+    long long s, e;
+    bu_row_of(p, v, s, e);
+    return e - s;
+}
+
+__device__ void frontier_degree_sums(const SingleParams& p, const int* q, long long nq, const unsigned* f,
+                                     unsigned long long& sum_out, unsigned long long& sum_in) {
+    const long long tid = gtid(), nth = gthreads();
+    if (q) {
+        for (long long i = tid; i < nq; i += nth) {
+            const int v = __ldcg(q + i);
+            sum_out += (unsigned long long)out_degree(p, v);
+            sum_in += (unsigned long long)in_degree(p, v);
+        }
+    } else {
+        for (long long w = tid; w < p.W; w += nth) {
+            unsigned x = __ldcg(f + w);
+            while (x) {
+                const int v = (int)(w * 32 + __ffs(x) - 1);
+                x &= x - 1;
+                sum_out += (unsigned long long)out_degree(p, v);
+                sum_in += (unsigned long long)in_degree(p, v);
             }
         }
     }
@@ -788,7 +844,7 @@ __device__ void bu_phase_a(const SingleParams& p, int d, const unsigned* fcur, u
         int u0 = bu_locate(lane, T, incl, excl, todo, ch);
         long long s0 = 0, e0 = 0;
         if (u0 >= 0) {
-            row_of_stream(p, u0, s0, e0);
+            bu_row_of_stream(p, u0, s0, e0);
         }
         int4 xa0 = z4, xb0 = z4;
         if (u0 >= 0 && e0 > s0) {
@@ -799,14 +855,14 @@ __device__ void bu_phase_a(const SingleParams& p, int d, const unsigned* fcur, u
         int u1 = bu_locate(32 + lane, T, incl, excl, todo, ch);
         long long s1 = 0, e1 = 0;
         if (u1 >= 0) {
-            row_of_stream(p, u1, s1, e1);
+            bu_row_of_stream(p, u1, s1, e1);
         }
         for (int base = 0; base < T; base += 32) {
             // round r+2: offsets
             const int u2 = bu_locate(base + 64 + lane, T, incl, excl, todo, ch);
             long long s2 = 0, e2 = 0;
             if (u2 >= 0) {
-                row_of_stream(p, u2, s2, e2);
+                bu_row_of_stream(p, u2, s2, e2);
             }
             // round r+1: window
             int4 xa1 = z4, xb1 = z4;
@@ -1064,7 +1120,7 @@ __device__ void bu_phase_b(const SingleParams& p, int d, const unsigned* fcur, u
         long long s0 = 0, e0 = 0, pos = 0;
         if (i < nlong) {
             u = __ldcg(longlist + i);
-            row_of(p, u, s0, e0);
+            bu_row_of(p, u, s0, e0);
             pos = ((s0 + skip) & ~3LL) + 4 * gl;
         }
         long long hitpos = -1;
@@ -1137,6 +1193,18 @@ __global__ void __launch_bounds__(kBlock, BFS_MIN_BLOCKS) bfs_single_kernel(Sing
     long long nf = p.nroots;
     long long mf = (long long)ld_relaxed64(&c->accm[0]);
     long long mu = p.nnz - mf;
+    if (p.directed) {
+        // m_u sums in-degrees: the edges a bottom-up step could still examine
+        long long rin = 0;
+        if (p.nroots == 1) {
+            long long s0, e0;
+            bu_row_of(p, p.root0, s0, e0);
+            rin = e0 - s0;
+        } else {
+            rin = (long long)ld_relaxed64(&c->dsum_in[0]);
+        }
+        mu = p.nnz - rin;
+    }
     long long reached = nf;
     int prev = TD, qsel = 0, bsel = 0, d = 0;
     const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
@@ -1152,6 +1220,8 @@ __global__ void __launch_bounds__(kBlock, BFS_MIN_BLOCKS) bfs_single_kernel(Sing
             c->examined[sfree] = 0;
             c->ntask[sfree] = 0;
             c->nmiss[sfree] = 0;
+            c->dsum_out[sfree] = 0;
+            c->dsum_in[sfree] = 0;
         }
         long long nf_next, scanned = 0, examined = mf, aux = 0, misses = 0;
         uint64_t t_mid = 0;
@@ -1225,7 +1295,19 @@ __global__ void __launch_bounds__(kBlock, BFS_MIN_BLOCKS) bfs_single_kernel(Sing
             bsel ^= 1;
         }
         const long long macc = (long long)ld_relaxed64(&c->accm[snext]);
-        const long long mf_next = (dir == BU && p.first) ? mu - macc : macc;
+        long long mf_next = (dir == BU && p.first) ? mu - macc : macc;
+        long long mu_drop = mf_next;   // undirected: in- and out-degree sums coincide
+        if (p.directed) {
+            unsigned long long so = 0, si = 0;
+            if (dir == TD)
+                frontier_degree_sums(p, qsel ? p.queue1 : p.queue0, nf_next, nullptr, so, si);
+            else
+                frontier_degree_sums(p, nullptr, 0, bsel ? p.front1 : p.front0, so, si);
+            block_add4(so, si, 0, 0, &c->dsum_out[snext], &c->dsum_in[snext], nullptr, nullptr);
+            if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
+            mf_next = (long long)ld_relaxed64(&c->dsum_out[snext]);
+            mu_drop = (long long)ld_relaxed64(&c->dsum_in[snext]);
+        }
         if (lead && d < p.rec_cap) {
             bfs_level_record r;
             r.dir = dir;
@@ -1243,7 +1325,7 @@ __global__ void __launch_bounds__(kBlock, BFS_MIN_BLOCKS) bfs_single_kernel(Sing
         }
         if (nf_next == 0) break;
         reached += nf_next;
-        mu -= mf_next;
+        mu -= mu_drop;
         nf = nf_next;
         mf = mf_next;
         prev = dir;
@@ -1644,7 +1726,10 @@ bfs_status single_launch_work(bfs_graph* g, SingleWork& w, const int32_t* roots_
     p.off = reinterpret_cast<const long long*>(g->offsets);
     p.cols = g->cols;
     const bool hub = opt.bu_rows == BFS_BU_ROWS_HUB_FIRST && g->cols_hf;
-    p.cols_bu = hub ? g->cols_hf : g->cols;
+    p.cols_bu = g->directed ? g->cols_in : (hub ? g->cols_hf : g->cols);
+    p.off_bu = reinterpret_cast<const long long*>(g->directed ? g->offsets_in : g->offsets);
+    p.deg8_in = g->deg8_in;
+    p.directed = g->directed ? 1 : 0;
     p.heads = (hub && g->bu_heads && g->bu_first) ? g->bu_heads : nullptr;
     p.first = p.heads ? g->bu_first : nullptr;
     p.deg8 = g->deg8;
@@ -1817,6 +1902,7 @@ extern "C" bfs_status bfs_run_csr_noalloc(const int64_t* row_offsets, const int3
     p.off = reinterpret_cast<const long long*>(row_offsets);
     p.cols = col_ids;
     p.cols_bu = col_ids;
+    p.off_bu = p.off;
     p.isolated = reinterpret_cast<const unsigned*>(b + bfsk::kStaticIsoOff);
     p.n = n;
     p.nnz = nnz;

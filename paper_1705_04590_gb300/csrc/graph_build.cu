@@ -8,8 +8,12 @@
 // Edge list -> CSR: each edge {u, v}, u != v, becomes the 64-bit keys
 // (u << 32 | v) and (v << 32 | u); the keys are radix-sorted (CUB) and
 // de-duplicated; the low halves are the column ids and a degree count plus
-// an exclusive scan gives the row offsets.  Also built here: the bitmap of
-// vertices that never search (degree 0, or ids past n in the last word).
+// an exclusive scan gives the row offsets.  A directed graph ("Data Sets":
+// the method applies to directed graphs) keeps only (u << 32 | v) for the
+// out-edge CSR and builds its transpose the same way from (v << 32 | u): the
+// in-edge rows the bottom-up step scans.  Also built here: the bitmap of
+// vertices that never search (no edge into them, or ids past n in the last
+// word).
 #include <cub/device/device_radix_sort.cuh>
 #include <cub/device/device_scan.cuh>
 #include <cub/device/device_select.cuh>
@@ -19,7 +23,7 @@
 namespace bfsk_build {
 
 __global__ void k_check_and_keys(const int32_t* __restrict__ src, const int32_t* __restrict__ dst, long long m,
-                                 long long n, unsigned long long* __restrict__ keys,
+                                 long long n, int symmetric, unsigned long long* __restrict__ keys,
                                  unsigned long long* __restrict__ count, int* __restrict__ bad) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -42,14 +46,15 @@ __global__ void k_check_and_keys(const int32_t* __restrict__ src, const int32_t*
         if (km) {
             const int leader = __ffs(km) - 1;
             unsigned long long b = 0;
-            if (lane == leader) b = atomicAdd(count, 2ull * __popc(km));
+            const unsigned long long per = symmetric ? 2ull : 1ull;
+            if (lane == leader) b = atomicAdd(count, per * __popc(km));
             b = __shfl_sync(full, b, leader);
             if (keep) {
                 unsigned lt;
                 asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
-                const unsigned long long pos = b + 2ull * __popc(km & lt);
+                const unsigned long long pos = b + per * __popc(km & lt);
                 keys[pos] = k0;
-                keys[pos + 1] = k1;
+                if (symmetric) keys[pos + 1] = k1;
             }
         }
     }
@@ -177,15 +182,15 @@ struct Scratch {
     }
 };
 
-static bfs_status finish_offsets(bfs_graph* g, unsigned long long* deg, cudaStream_t s) {
+static bfs_status finish_offsets(bfs_graph* g, int64_t* offsets, unsigned long long* deg, cudaStream_t s) {
     // offsets[0] = 0, offsets[1..n] = inclusive scan of degrees
     const long long n = g->n;
     size_t tb = 0;
-    BFS_CUDA_TRY(cub::DeviceScan::InclusiveSum(nullptr, tb, deg, (unsigned long long*)g->offsets + 1, n, s));
+    BFS_CUDA_TRY(cub::DeviceScan::InclusiveSum(nullptr, tb, deg, (unsigned long long*)offsets + 1, n, s));
     Scratch tmp(&g->mem, s);
     if (!tmp.get(tb + 16)) return fail(BFS_ERR_OOM, "graph build: scan scratch");
-    BFS_CUDA_TRY(cudaMemsetAsync(g->offsets, 0, sizeof(int64_t), s));
-    BFS_CUDA_TRY(cub::DeviceScan::InclusiveSum(tmp.p, tb, deg, (unsigned long long*)g->offsets + 1, n, s));
+    BFS_CUDA_TRY(cudaMemsetAsync(offsets, 0, sizeof(int64_t), s));
+    BFS_CUDA_TRY(cub::DeviceScan::InclusiveSum(tmp.p, tb, deg, (unsigned long long*)offsets + 1, n, s));
     return BFS_OK;
 }
 
@@ -194,7 +199,9 @@ bfs_status build_isolated_bitmap(bfs_graph* g, cudaStream_t s) {
     g->isolated = (uint32_t*)g->mem.alloc(sizeof(uint32_t) * (size_t)g->W, s);
     if (!g->isolated) return fail(BFS_ERR_OOM, "graph build: isolated bitmap");
     g->graph_bytes += sizeof(uint32_t) * (size_t)g->W;
-    k_isolated<<<grid_for(g->W, 256, g->sm_count), 256, 0, s>>>((const long long*)g->offsets, g->n, g->W,
+    // vertices no edge leads into never search bottom-up and are never reached (but a root)
+    const int64_t* rows_in = g->directed ? g->offsets_in : g->offsets;
+    k_isolated<<<grid_for(g->W, 256, g->sm_count), 256, 0, s>>>((const long long*)rows_in, g->n, g->W,
                                                                 g->isolated);
     BFS_CUDA_TRY(cudaGetLastError());
     {
@@ -214,24 +221,23 @@ bfs_status build_isolated_bitmap(bfs_graph* g, cudaStream_t s) {
     g->graph_bytes += (size_t)g->n + 32;
     k_deg8<<<grid_for(g->n + 32, 256, g->sm_count), 256, 0, s>>>((const long long*)g->offsets, g->n, g->deg8);
     BFS_CUDA_TRY(cudaGetLastError());
+    if (g->directed) {
+        g->deg8_in = (uint8_t*)g->mem.alloc((size_t)g->n + 32, s);
+        if (!g->deg8_in) return fail(BFS_ERR_OOM, "graph build: in-degree bytes");
+        g->graph_bytes += (size_t)g->n + 32;
+        k_deg8<<<grid_for(g->n + 32, 256, g->sm_count), 256, 0, s>>>((const long long*)g->offsets_in, g->n,
+                                                                     g->deg8_in);
+        BFS_CUDA_TRY(cudaGetLastError());
+    }
     return BFS_OK;
 }
 
-bfs_status build_csr_from_edges(bfs_graph* g, const int32_t* src, const int32_t* dst, int64_t m, bool device_ptrs,
-                                cudaStream_t s) {
+// One CSR from device edge arrays: rows of (es[i] -> ed[i]), and of (ed[i] -> es[i])
+// too when symmetric; self-loops dropped, duplicates removed, rows sorted.
+static bfs_status build_rows(bfs_graph* g, const int32_t* es, const int32_t* ed, int64_t m, bool symmetric,
+                             int64_t** off_out, int32_t** cols_out, long long* nnz_out, cudaStream_t s) {
     const long long n = g->n;
-    Scratch dsrc(&g->mem, s), ddst(&g->mem, s);
-    const int32_t* es = src;
-    const int32_t* ed = dst;
-    if (!device_ptrs && m > 0) {
-        if (!dsrc.get(sizeof(int32_t) * (size_t)m) || !ddst.get(sizeof(int32_t) * (size_t)m))
-            return fail(BFS_ERR_OOM, "graph build: edge staging");
-        BFS_CUDA_TRY(cudaMemcpyAsync(dsrc.p, src, sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice, s));
-        BFS_CUDA_TRY(cudaMemcpyAsync(ddst.p, dst, sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice, s));
-        es = (const int32_t*)dsrc.p;
-        ed = (const int32_t*)ddst.p;
-    }
-    const long long cap = 2 * (long long)m;
+    const long long cap = (symmetric ? 2 : 1) * (long long)m;
     Scratch keys_a(&g->mem, s), keys_b(&g->mem, s), small(&g->mem, s);
     if (!small.get(64)) return fail(BFS_ERR_OOM, "graph build: counters");
     unsigned long long* d_count = (unsigned long long*)small.p;
@@ -241,8 +247,8 @@ bfs_status build_csr_from_edges(bfs_graph* g, const int32_t* src, const int32_t*
     if (cap > 0) {
         if (!keys_a.get(sizeof(unsigned long long) * (size_t)cap) || !keys_b.get(sizeof(unsigned long long) * (size_t)cap))
             return fail(BFS_ERR_OOM, "graph build: key buffers");
-        k_check_and_keys<<<grid_for(m, 256, g->sm_count), 256, 0, s>>>(es, ed, m, n, (unsigned long long*)keys_a.p,
-                                                                      d_count, d_bad);
+        k_check_and_keys<<<grid_for(m, 256, g->sm_count), 256, 0, s>>>(es, ed, m, n, symmetric ? 1 : 0,
+                                                                      (unsigned long long*)keys_a.p, d_count, d_bad);
         BFS_CUDA_TRY(cudaGetLastError());
     }
     unsigned long long h[2] = {0, 0};
@@ -273,22 +279,47 @@ bfs_status build_csr_from_edges(bfs_graph* g, const int32_t* src, const int32_t*
         BFS_CUDA_TRY(cudaStreamSynchronize(s));
         nnz = (long long)h[1];
     }
-    g->nnz = nnz;
-    g->offsets = (int64_t*)g->mem.alloc(sizeof(int64_t) * (size_t)(n + 1), s);
-    g->cols = (int32_t*)g->mem.alloc(sizeof(int32_t) * (size_t)(nnz + kColPad), s);
-    if (!g->offsets || !g->cols) return fail(BFS_ERR_OOM, "graph build: CSR arrays");
-    g->graph_bytes = sizeof(int64_t) * (size_t)(n + 1) + sizeof(int32_t) * (size_t)(nnz + kColPad);
+    *nnz_out = nnz;
+    *off_out = (int64_t*)g->mem.alloc(sizeof(int64_t) * (size_t)(n + 1), s);
+    *cols_out = (int32_t*)g->mem.alloc(sizeof(int32_t) * (size_t)(nnz + kColPad), s);
+    if (!*off_out || !*cols_out) return fail(BFS_ERR_OOM, "graph build: CSR arrays");
+    g->graph_bytes += sizeof(int64_t) * (size_t)(n + 1) + sizeof(int32_t) * (size_t)(nnz + kColPad);
     Scratch deg(&g->mem, s);
     if (!deg.get(sizeof(unsigned long long) * (size_t)n)) return fail(BFS_ERR_OOM, "graph build: degrees");
     BFS_CUDA_TRY(cudaMemsetAsync(deg.p, 0, sizeof(unsigned long long) * (size_t)n, s));
-    k_fill_i32<<<1, 32, 0, s>>>(g->cols + nnz, kColPad, 0);
+    k_fill_i32<<<1, 32, 0, s>>>(*cols_out + nnz, kColPad, 0);
     BFS_CUDA_TRY(cudaGetLastError());
     if (nnz > 0) {
-        k_split_keys<<<grid_for(nnz, 256, g->sm_count), 256, 0, s>>>(uniq, nnz, g->cols, (unsigned long long*)deg.p);
+        k_split_keys<<<grid_for(nnz, 256, g->sm_count), 256, 0, s>>>(uniq, nnz, *cols_out, (unsigned long long*)deg.p);
         BFS_CUDA_TRY(cudaGetLastError());
     }
-    bfs_status st = finish_offsets(g, (unsigned long long*)deg.p, s);
+    return finish_offsets(g, *off_out, (unsigned long long*)deg.p, s);
+}
+
+bfs_status build_csr_from_edges(bfs_graph* g, const int32_t* src, const int32_t* dst, int64_t m, bool device_ptrs,
+                                cudaStream_t s) {
+    Scratch dsrc(&g->mem, s), ddst(&g->mem, s);
+    const int32_t* es = src;
+    const int32_t* ed = dst;
+    if (!device_ptrs && m > 0) {
+        if (!dsrc.get(sizeof(int32_t) * (size_t)m) || !ddst.get(sizeof(int32_t) * (size_t)m))
+            return fail(BFS_ERR_OOM, "graph build: edge staging");
+        BFS_CUDA_TRY(cudaMemcpyAsync(dsrc.p, src, sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice, s));
+        BFS_CUDA_TRY(cudaMemcpyAsync(ddst.p, dst, sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice, s));
+        es = (const int32_t*)dsrc.p;
+        ed = (const int32_t*)ddst.p;
+    }
+    g->graph_bytes = 0;
+    long long nnz = 0;
+    bfs_status st = build_rows(g, es, ed, m, !g->directed, &g->offsets, &g->cols, &nnz, s);
     if (st != BFS_OK) return st;
+    g->nnz = nnz;
+    if (g->directed) {
+        long long nnz_in = 0;
+        st = build_rows(g, ed, es, m, false, &g->offsets_in, &g->cols_in, &nnz_in, s);
+        if (st != BFS_OK) return st;
+        if (nnz_in != nnz) return fail(BFS_ERR_CUDA, "graph build: transpose holds a different edge count");
+    }
     st = build_isolated_bitmap(g, s);
     if (st != BFS_OK) return st;
     BFS_CUDA_TRY(cudaStreamSynchronize(s));

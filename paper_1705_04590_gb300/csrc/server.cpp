@@ -484,6 +484,7 @@ bfs_status bfs_server_create_ex(int64_t hbm_budget_bytes, int32_t max_lanes, con
 
 bfs_status bfs_server_add_graph(bfs_server* sv, bfs_graph* g, int32_t* slot) {
     if (!sv || !g) return fail(BFS_ERR_INVALID, "NULL server or graph");
+    if (g->directed) return fail(BFS_ERR_UNSUPPORTED, "server: undirected graphs only");
     std::lock_guard<std::mutex> lk(sv->mu);
     Slot* s = new (std::nothrow) Slot();
     if (!s) return fail(BFS_ERR_OOM, "host allocation of a slot");
