@@ -450,6 +450,41 @@ __device__ __forceinline__ void flush_degree(const SingleParams& p, int v, bool 
     if (pf && re > rs) asm volatile("prefetch.global.L2 [%0];" ::"l"(p.cols + rs));
 }
 
+// Write st.buf[0..cnt) to qnext[base..] and add their degrees (the next
+// frontier's m_f, read here in batches rather than on the claim path) to acc_m:
+// a lane takes up to kFlushBatch entries per step and has all their degree bytes
+// in flight together (one by one they would be a chain of dependent DRAM reads).
+constexpr int kFlushBatch = 8;
+
+__device__ __forceinline__ void flush_entries(const SingleParams& p, const WarpStage& st, int* qnext,
+                                              unsigned long long base, unsigned long long& acc_m) {
+    const int lane = lane_id();
+    if (!p.deg8 || st.pf) {
+        for (int i = lane; i < st.cnt; i += 32) {
+            const int v = st.buf[i];
+            qnext[base + i] = v;
+            flush_degree(p, v, st.pf, acc_m);
+        }
+        return;
+    }
+    for (int i0 = 0; i0 < st.cnt; i0 += 32 * kFlushBatch) {
+        unsigned d8[kFlushBatch];
+        int vs[kFlushBatch];
+#pragma unroll
+        for (int k = 0; k < kFlushBatch; k++) {
+            const int i = i0 + k * 32 + lane;
+            vs[k] = i < st.cnt ? st.buf[i] : -1;
+            d8[k] = vs[k] >= 0 ? (unsigned)__ldg(p.deg8 + vs[k]) : 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < kFlushBatch; k++) {
+            if (vs[k] < 0) continue;
+            qnext[base + i0 + k * 32 + lane] = vs[k];
+            acc_m += d8[k] < 255u ? (unsigned long long)d8[k] : (unsigned long long)deg_of(p, vs[k]);
+        }
+    }
+}
+
 __device__ __forceinline__ void stage_flush(const SingleParams& p, WarpStage& st, int* qnext,
                                             unsigned long long* tail, unsigned long long& acc_m) {
     if (st.cnt == 0) return;
@@ -457,13 +492,7 @@ __device__ __forceinline__ void stage_flush(const SingleParams& p, WarpStage& st
     unsigned long long base = 0;
     if (lane_id() == 0) base = atomicAdd(tail, (unsigned long long)st.cnt);
     base = __shfl_sync(kFull, base, 0);
-    for (int i = lane_id(); i < st.cnt; i += 32) {
-        const int v = st.buf[i];
-        qnext[base + i] = v;
-        // degree sum of the next frontier (the switch rule's m_f), read here in
-        // batches rather than on the claim path
-        flush_degree(p, v, st.pf, acc_m);
-    }
+    flush_entries(p, st, qnext, base, acc_m);
     __syncwarp();
     st.cnt = 0;
 }
@@ -490,11 +519,7 @@ __device__ void block_flush(const SingleParams& p, WarpStage& st, int* qnext, un
     }
     __syncthreads();
     const unsigned long long base = s_bbase + (unsigned long long)s_wcnt[wib];
-    for (int i = lane; i < st.cnt; i += 32) {
-        const int v = st.buf[i];
-        qnext[base + i] = v;
-        flush_degree(p, v, st.pf, acc_m);
-    }
+    flush_entries(p, st, qnext, base, acc_m);
     __syncwarp();
     st.cnt = 0;
 }
@@ -1433,13 +1458,15 @@ __device__ void td_dcsc_phase(const SingleParams& p, int d, const int* qcur, lon
 }
 
 // Bottom-up on tiles (*, b) (Algorithm 4's sub-steps without messages): the
-// CTA owning block b walks the p tiles of its column of the grid, staging the
-// frontier segment of block i in shared memory for tile (i, b); each
+// CTA owning block b walks the p tiles of its column of the grid; each
 // searcher u of block b (a column of the tile: the matrix is symmetric) not
 // yet completed scans its rows in block i and stops at the first one in the
 // frontier.  The completed bits of block b live in shared memory for the whole
-// level; tile order rotates with b (every CTA starts on a different segment),
-// or runs 0..p-1 for minimum-id parents.
+// level.  With minimum-id parents the tiles run 0..p-1 with the frontier
+// segment of block i staged in shared memory and a CTA barrier between tiles
+// (so a searcher stops at its first frontier neighbour in id order); with any
+// parent the tile order rotates with b, the segment is probed in L2, and tiles
+// follow one another without barriers.
 __device__ void bu_dcsc_phase(const SingleParams& p, int d, const unsigned* fcur, unsigned* fnext, unsigned* s_own,
                               unsigned* s_seg, unsigned long long& acc_n, unsigned long long& acc_m,
                               unsigned long long& acc_sc, unsigned long long& acc_ex) {
@@ -1450,8 +1477,45 @@ __device__ void bu_dcsc_phase(const SingleParams& p, int d, const unsigned* fcur
         s_own[w] = x;
         acc_sc += (unsigned long long)__popc(~x);
     }
-    for (int t = 0; t < p.nb; t++) {
-        const int i = (p.parent_mode == BFS_PARENT_MIN_ID) ? t : (b + t) % p.nb;
+    if (p.parent_mode != BFS_PARENT_MIN_ID) {
+        // any parent will do: tiles in rotated order with no staging and no barrier
+        // between them (the frontier segment is probed in L2), four column entries per
+        // thread in flight.  A searcher found in two tiles at once gets either parent.
+        for (int t = 0; t < p.nb; t++) {
+            const int i = (b + t) % p.nb;
+            const unsigned* fseg = fcur + (long long)i * p.Bw;
+            const long long tt = (long long)i * p.nb + b;
+            const long long lo = __ldg(p.tile_ptr + tt), hi = __ldg(p.tile_ptr + tt + 1);
+            for (long long x0 = lo + threadIdx.x; x0 < hi; x0 += 4LL * blockDim.x) {
+                int ul[4];
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const long long x = x0 + (long long)k * blockDim.x;
+                    ul[k] = x < hi ? __ldg(p.jc + x) : -1;
+                }
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    if (ul[k] < 0 || ((s_own[ul[k] >> 5] >> (ul[k] & 31)) & 1u)) continue;
+                    const long long x = x0 + (long long)k * blockDim.x;
+                    const long long e0 = __ldg(p.cp + x), e1 = __ldg(p.cp + x + 1);
+                    for (long long e = e0; e < e1; e++) {
+                        const int vl = __ldg(p.ir + e);
+                        if ((__ldcg(fseg + (vl >> 5)) >> (vl & 31)) & 1u) {
+                            const long long u = (long long)b * p.B + ul[k];
+                            if (p.parent) p.parent[u] = (int)((long long)i * p.B + vl);
+                            if (p.level) p.level[u] = d + 1;
+                            atomicOr(s_own + (ul[k] >> 5), 1u << (ul[k] & 31));
+                            acc_ex += (unsigned long long)(e - e0 + 1);
+                            break;
+                        }
+                        if (e + 1 == e1) acc_ex += (unsigned long long)(e1 - e0);
+                    }
+                }
+            }
+        }
+    }
+    for (int t = 0; t < p.nb && p.parent_mode == BFS_PARENT_MIN_ID; t++) {
+        const int i = t;
         const long long ibw = block_words(p, i), ibase = (long long)i * p.Bw;
         __syncthreads();
         for (long long w = threadIdx.x; w < ibw; w += blockDim.x) s_seg[w] = __ldcg(fcur + ibase + w);
