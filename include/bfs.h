@@ -109,7 +109,7 @@ typedef struct {
                               CSR layout and BFS_PARENT_ANY).  Levels are the same; the bottom-up
                               examination counts and the parents chosen follow the order */
     int32_t td_chunk;      /* top-down: edges per chunk task of a vertex above td_big_degree, 64..4096
-                              (0 = tuned default 256) */
+                              (0 = tuned default 128) */
     int32_t ctas_per_sm;   /* CTAs per SM of the persistent single-source launch, 1 .. the resident
                               maximum (0 = the maximum); fewer means fewer arrivals per grid barrier */
     int32_t reserved;      /* must be 0 */

@@ -47,7 +47,8 @@ namespace bfsk {
 constexpr int kBlock = BFS_BLOCK;  // CSR kernel
 constexpr int kDBlock = 1024;   // DCSC kernel (one CTA per vertex block)
 constexpr int kWarps = 32;      // shared-memory per-warp arrays sized for up to 1024 threads
-constexpr int kChunk = 256;    // default edges per top-down chunk task (options.td_chunk)
+constexpr int kChunk = 256;    // edges per top-down chunk task of the allocation-free entry point
+constexpr int kDefaultChunk = 128;   // default of options.td_chunk (measured best at R-MAT 26)
 constexpr int kMinChunk = 64;  // smallest chunk task: the task lists are sized for it
 constexpr int kStage = 256;    // per-warp shared-memory staging of next-queue entries
 constexpr long long kPrefetchNf = 1 << 16;   // top-down levels below this prefetch the next rows
@@ -753,24 +754,46 @@ __device__ void queue_to_bitmap(const SingleParams& p, const int* q, long long n
 }
 
 // Read-and-clear `f` into queue q (cursor *tail), clear `other` too, so both
-// frontier bitmaps are zero for a later queue -> bitmap conversion.
+// frontier bitmaps are zero for a later queue -> bitmap conversion.  Each
+// thread takes kB2QWords consecutive words per round (two 16-byte loads), so a
+// whole bitmap takes a round or two instead of one round per word per thread.
+constexpr int kB2QWords = 8;
+
 __device__ void bitmap_to_queue(const SingleParams& p, unsigned* f, unsigned* other, int* q,
                                 unsigned long long* tail) {
-    // grid-stride rounds that are uniform across the CTA: per round the CTA
-    // claims its queue range with one atomicAdd (a block scan of its words' counts)
+    // rounds that are uniform across the CTA: per round the CTA claims its queue
+    // range with one atomicAdd (a block scan of its threads' counts)
     __shared__ int s_wtot[kWarps];
     __shared__ unsigned long long s_qb;
     const int lane = lane_id(), wib = threadIdx.x >> 5, nwb = blockDim.x >> 5;
-    const long long nth = gthreads();
-    for (long long r0 = (long long)blockIdx.x * blockDim.x; r0 < p.W; r0 += nth) {
-        const long long w = r0 + threadIdx.x;
-        unsigned x = 0;
-        if (w < p.W) {
-            x = __ldcg(f + w);
-            f[w] = 0u;
-            other[w] = 0u;
+    const long long span = (long long)gthreads() * kB2QWords;
+    const bool vec = (p.W % 4) == 0;   // whole 16-byte groups (bitmaps are 16-byte aligned)
+    for (long long r0 = (long long)blockIdx.x * blockDim.x * kB2QWords; r0 < p.W; r0 += span) {
+        const long long w0 = r0 + (long long)threadIdx.x * kB2QWords;
+        unsigned x[kB2QWords];
+        if (vec && w0 + kB2QWords <= p.W) {
+            const uint4 a = __ldcg(reinterpret_cast<const uint4*>(f + w0));
+            const uint4 b = __ldcg(reinterpret_cast<const uint4*>(f + w0) + 1);
+            x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w; x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+            const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+            reinterpret_cast<uint4*>(f + w0)[0] = z;
+            reinterpret_cast<uint4*>(f + w0)[1] = z;
+            reinterpret_cast<uint4*>(other + w0)[0] = z;
+            reinterpret_cast<uint4*>(other + w0)[1] = z;
+        } else {
+#pragma unroll
+            for (int k = 0; k < kB2QWords; k++) {
+                x[k] = 0u;
+                if (w0 + k < p.W) {
+                    x[k] = __ldcg(f + w0 + k);
+                    f[w0 + k] = 0u;
+                    other[w0 + k] = 0u;
+                }
+            }
         }
-        const int cnt = __popc(x);
+        int cnt = 0;
+#pragma unroll
+        for (int k = 0; k < kB2QWords; k++) cnt += __popc(x[k]);
         const int incl = warp_inclusive_scan(cnt);
         if (lane == 31) s_wtot[wib] = incl;
         __syncthreads();
@@ -785,10 +808,14 @@ __device__ void bitmap_to_queue(const SingleParams& p, unsigned* f, unsigned* ot
         }
         __syncthreads();
         long long pos = (long long)s_qb + s_wtot[wib] + incl - cnt;
-        while (x) {
-            const int bit = __ffs(x) - 1;
-            x &= x - 1;
-            q[pos++] = (int)(w * 32 + bit);
+#pragma unroll
+        for (int k = 0; k < kB2QWords; k++) {
+            unsigned y = x[k];
+            while (y) {
+                const int bit = __ffs(y) - 1;
+                y &= y - 1;
+                q[pos++] = (int)((w0 + k) * 32 + bit);
+            }
         }
         __syncthreads();
     }
@@ -1823,7 +1850,7 @@ bfs_status single_launch_work(bfs_graph* g, SingleWork& w, const int32_t* roots_
     p.beta = opt.beta;
     p.parent_mode = opt.parent_mode;
     p.big_deg = opt.td_big_degree > 0 ? opt.td_big_degree : 96;
-    p.td_chunk = opt.td_chunk > 0 ? opt.td_chunk : bfsk::kChunk;
+    p.td_chunk = opt.td_chunk > 0 ? opt.td_chunk : bfsk::kDefaultChunk;
     p.seed = opt.seed;
     p.timeout_ns = (unsigned long long)(opt.timeout_ms > 0 ? opt.timeout_ms : 10000) * 1000000ull;
     const unsigned extra = (unsigned)(g->debug_barrier_extra > 0 ? g->debug_barrier_extra : 0);
