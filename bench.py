@@ -448,6 +448,12 @@ def configs_section(peak_gbs: float) -> dict:
         line(f"rmat24_csr_{mname}", g, roots, bfs.options(mode=mode, bu_rows=bfs.BU_ROWS_HUB_FIRST), n, m)
         line(f"rmat24_csr_idrows_{mname}", g, roots, bfs.options(mode=mode), n, m)
         line(f"rmat24_dcsc_{mname}", g, roots[:2], bfs.options(mode=mode, layout=bfs.LAYOUT_DCSC_TILED), n, m)
+    # the two layouts' sizes: CSR offsets + ids against the p x p tiles' pointers, JC, CP and IR
+    d = g.dcsc_layout()
+    p2 = d.num_blocks * d.num_blocks
+    out["rmat24_dcsc_do"]["layout_bytes"] = {"csr": 8 * (n + 1) + 4 * g.nnz,
+                                             "dcsc": 8 * (p2 + 1) + 4 * d.nzc + 8 * (d.nzc + 1) + 4 * g.nnz,
+                                             "tiles": p2, "nzc": d.nzc, "nnz": g.nnz}
     g.close()
     # the same R-MAT edges as a directed graph (edge i: src -> dst; top-down over out-rows,
     # bottom-up over their transpose); GTEPS over its directed edge count
@@ -741,14 +747,14 @@ def our_arm(args):
             traffic = tr.get("dram_bytes_per_launch")
 
     # the autotuner's choice (direction thresholds, hub cut-off, top-down chunk, CTAs per
-    # SM) on 4 sample roots, timed over the same steps as the headline
+    # SM, cluster size) on 4 sample roots, timed over the same steps as the headline
     tuned = None
     if rank == 0 and not args.no_tuned and args.layout == "csr":
         from paper_1705_04590_gb300 import autotune
         best, _ = autotune.autotune(g, roots[:4], base=opts)
         t_ms, t_bytes = time_searches(g, [roots[i % len(roots)] for i in range(args.steps)], best, n)
         tuned = {"alpha": best.alpha, "beta": best.beta, "td_big_degree": best.td_big_degree,
-                 "td_chunk": best.td_chunk, "ctas_per_sm": best.ctas_per_sm,
+                 "td_chunk": best.td_chunk, "ctas_per_sm": best.ctas_per_sm, "cluster_size": best.cluster_size,
                  "value": args.steps * m / sum(t_ms) / 1e6, "unit": "GTEPS", "ms_per_step": sum(t_ms) / args.steps,
                  "roofline_frac": sum(t_bytes) / (sum(t_ms) / 1e3) / 1e9 / peaks["hbm_gbs"],
                  "note": "same roots and outputs as the headline, CUDA events per search; the headline keeps "

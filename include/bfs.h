@@ -112,7 +112,14 @@ typedef struct {
                               (0 = tuned default 128) */
     int32_t ctas_per_sm;   /* CTAs per SM of the persistent single-source launch, 1 .. the resident
                               maximum (0 = the maximum); fewer means fewer arrivals per grid barrier */
-    int32_t reserved;      /* must be 0 */
+    int32_t cluster_size;  /* CSR single-source searches of an undirected graph: CTAs per thread-block
+                              cluster (2, 4, 8 or 16), whose first cluster runs top-down levels with
+                              a small frontier alone (frontier in distributed shared memory, one
+                              hardware cluster barrier per level) while the rest of the grid waits;
+                              1 = off; 0 = automatic (16 on graphs of maximum degree <= 32, where
+                              the levels are many and small, else off).  A cluster launch may hold
+                              fewer CTAs than the plain one.  Ignored by DCSC, directed graphs and
+                              the allocation-free entry point */
 } bfs_options;
 
 #define BFS_BU_ROWS_BY_ID     0
@@ -133,8 +140,9 @@ typedef struct {
     int64_t examined;     /* top-down: m_f; bottom-up: sum over searching vertices of the 1-based
                              position of the first frontier neighbour in sorted order, or the degree */
     int64_t t_ns;         /* device time from the end of initialisation to the end of this level */
-    int64_t aux;          /* top-down: edge-chunk tasks; bottom-up: searchers continued past their first
-                             window (id-ordered rows) or row head (hub-first rows): the long list */
+    int64_t aux;          /* top-down: edge-chunk tasks, or -1 for a level thread-block cluster 0 ran
+                             alone (options.cluster_size); bottom-up: searchers continued past their
+                             first window (id-ordered rows) or row head (hub-first rows): the long list */
     int64_t t_mid_ns;     /* device time at the level's first internal barrier (0 if none) */
 } bfs_level_record;
 
@@ -367,7 +375,8 @@ bfs_status bfs_run_csr_noalloc(const int64_t* row_offsets, const int32_t* col_id
  * (roots_host) for a grid of direction thresholds alpha in {6,14,24,32,96},
  * beta in {12,24,64,128} and top-down hub cut-offs td_big_degree in
  * {64,96,256}; then, from the winner, the top-down chunk size td_chunk in
- * {128,256,512,1024} and then ctas_per_sm in {1, the maximum}, one knob at a
+ * {128,256,512,1024}, then ctas_per_sm in {1, the maximum}, then (CSR,
+ * undirected) cluster_size in {1, 8, 16}, one knob at a
  * time.  Each configuration runs once for warm-up, then the k roots timed with
  * CUDA events; the fastest mean goes to *best (other fields from `base`, or
  * the defaults when base is NULL).  Levels do not depend on these choices

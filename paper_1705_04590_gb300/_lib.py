@@ -29,7 +29,7 @@ class Allocator(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("mode", c_i32), ("layout", c_i32), ("alpha", c_i32), ("beta", c_i32), ("parent_mode", c_i32),
                 ("td_big_degree", c_i32), ("timeout_ms", c_i64), ("seed", c_u64),
-                ("bu_rows", c_i32), ("td_chunk", c_i32), ("ctas_per_sm", c_i32), ("reserved", c_i32)]
+                ("bu_rows", c_i32), ("td_chunk", c_i32), ("ctas_per_sm", c_i32), ("cluster_size", c_i32)]
 
 
 class LevelRecord(ctypes.Structure):

@@ -67,12 +67,13 @@ class _TorchAllocator:
 
 def options(mode: int = L.MODE_DO, layout: int = L.LAYOUT_CSR, alpha: int = 14, beta: int = 24,
             parent_mode: int = L.PARENT_ANY, td_big_degree: int = 0, timeout_ms: int = 10000, seed: int = 0,
-            bu_rows: int = L.BU_ROWS_BY_ID, td_chunk: int = 0, ctas_per_sm: int = 0) -> L.Options:
+            bu_rows: int = L.BU_ROWS_BY_ID, td_chunk: int = 0, ctas_per_sm: int = 0,
+            cluster_size: int = 0) -> L.Options:
     o = L.Options()
     L.load().bfs_options_default(ctypes.byref(o))
     o.mode, o.layout, o.alpha, o.beta, o.parent_mode = mode, layout, alpha, beta, parent_mode
     o.td_big_degree, o.timeout_ms, o.seed = td_big_degree, timeout_ms, seed
-    o.bu_rows, o.td_chunk, o.ctas_per_sm = bu_rows, td_chunk, ctas_per_sm
+    o.bu_rows, o.td_chunk, o.ctas_per_sm, o.cluster_size = bu_rows, td_chunk, ctas_per_sm, cluster_size
     return o
 
 

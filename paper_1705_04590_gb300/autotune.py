@@ -2,7 +2,7 @@
 
 `tuned_options(graph, roots)` returns the bfs_options that bfs_autotune (the
 library's native tuner: a grid over alpha, beta and the top-down hub cut-off,
-then the top-down chunk size and the CTAs per SM one at a time, timed with CUDA
+then the top-down chunk size, the CTAs per SM and the cluster size one at a time, timed with CUDA
 events) picked for a graph of this size and degree profile on this device,
 running the tuner once and remembering the result in a JSON file (default
 ~/.cache/gb300_dobfs/autotune.json, or $BFS_AUTOTUNE_CACHE).
@@ -61,10 +61,12 @@ def tuned_options(graph, roots, refresh: bool = False) -> L.Options:
         L.load().bfs_options_default(ctypes.byref(o))
         o.alpha, o.beta, o.td_big_degree = int(c["alpha"]), int(c["beta"]), int(c["td_big_degree"])
         o.td_chunk, o.ctas_per_sm = int(c.get("td_chunk", 0)), int(c.get("ctas_per_sm", 0))
+        o.cluster_size = int(c.get("cluster_size", 0))
         return o
     best, ms = autotune(graph, roots)
     cache[key] = {"alpha": best.alpha, "beta": best.beta, "td_big_degree": best.td_big_degree,
-                  "td_chunk": best.td_chunk, "ctas_per_sm": best.ctas_per_sm, "ms": ms}
+                  "td_chunk": best.td_chunk, "ctas_per_sm": best.ctas_per_sm,
+                  "cluster_size": best.cluster_size, "ms": ms}
     os.makedirs(os.path.dirname(path), exist_ok=True)
     tmp = path + f".tmp{os.getpid()}"
     with open(tmp, "w") as f:

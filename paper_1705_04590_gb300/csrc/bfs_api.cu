@@ -114,7 +114,9 @@ static bfs_status check_options(const bfs_options* in, bfs_options* out, const b
     if (out->td_chunk != 0 && (out->td_chunk < 64 || out->td_chunk > 4096))
         return fail(BFS_ERR_INVALID, "options.td_chunk must be 0 or lie in [64, 4096]");
     if (out->ctas_per_sm < 0) return fail(BFS_ERR_INVALID, "options.ctas_per_sm must be >= 0");
-    if (out->reserved != 0) return fail(BFS_ERR_INVALID, "options.reserved must be 0");
+    if (out->cluster_size != 0 && out->cluster_size != 1 && out->cluster_size != 2 && out->cluster_size != 4 &&
+        out->cluster_size != 8 && out->cluster_size != 16)
+        return fail(BFS_ERR_INVALID, "options.cluster_size must be 0, 1, 2, 4, 8 or 16");
     if (out->bu_rows != BFS_BU_ROWS_BY_ID && out->bu_rows != BFS_BU_ROWS_HUB_FIRST)
         return fail(BFS_ERR_INVALID, "options.bu_rows must be a BFS_BU_ROWS_* value");
     if (out->bu_rows == BFS_BU_ROWS_HUB_FIRST) {
@@ -478,6 +480,17 @@ bfs_status bfs_autotune(bfs_graph* g, const int32_t* roots_host, int32_t k, cons
         bfs_options o = chunk_win;
         o.ctas_per_sm = c;
         consider(o);
+    }
+    // cluster levels (CSR searches of undirected graphs): off, clusters of 8, of 16
+    if (!g->directed && o0.layout == BFS_LAYOUT_CSR) {
+        static const int clus[] = {1, 8, 16};
+        const bfs_options ctas_win = win;
+        for (int c : clus) {
+            if (st != BFS_OK) break;
+            bfs_options o = ctas_win;
+            o.cluster_size = c;
+            consider(o);
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

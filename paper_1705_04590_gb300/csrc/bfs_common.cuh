@@ -48,6 +48,12 @@ struct Ctrl {
     unsigned long long nmiss[3];     // bottom-up searchers whose first probe missed (miss-list length)
     unsigned long long dsum_out[3];  // directed graphs: out-degree sum of frontier `slot`
     unsigned long long dsum_in[3];   // directed graphs: in-degree sum of frontier `slot`
+    unsigned long long heavy[3];     // top-down: vertices of frontier `slot` above the cluster-level degree cap
+    // cluster levels (levels run by thread-block cluster 0 alone while the frontier is small)
+    unsigned long long clu_gen;      // episodes finished: the waiting CTAs resume when it reaches theirs
+    unsigned long long clu_prog;     // last level the cluster started (progress for the waiters' time limit)
+    unsigned long long clu_spill;    // frontier entries that found no room in the cluster's shared memory
+    long long clu_d, clu_nf, clu_mf, clu_mu, clu_reached, clu_done;   // state handed back to the grid
     long long num_levels;
     long long reached;
     unsigned long long t_enter;    // lead CTA's clock at kernel entry

@@ -54,6 +54,7 @@ struct SingleWork {
     long long roots_cap = 0;
     size_t bytes = 0;
     int grid = 0, block = 0;       // cooperative launch shape
+    int clu_grid[5] = {0, 0, 0, 0, 0};   // co-resident CTAs of a launch in clusters of 1, 2, 4, 8, 16 (0 = not asked yet)
 };
 
 // Buffers of one multi-source (64-lane) search state: bfs_run_multi's own,
@@ -112,6 +113,7 @@ struct bfs_graph {
     uint8_t* deg8_in = nullptr;     // [n + 32] min(in-degree, 255)
     int64_t W = 0;                  // bitmap words
     int64_t n_active = 0;           // vertices with degree > 0
+    int64_t max_degree = 0;         // largest degree (largest in- or out-degree of a directed graph)
     int32_t debug_barrier_extra = 0;   // testing: arrivals every grid barrier waits for in vain
     size_t graph_bytes = 0;
     bfsrt::DeviceAlloc mem;

@@ -31,6 +31,7 @@
 // Membership tests read only the current frontier; next is separate and
 // swapped in after the level (the reading of Algorithm 2 that keeps levels
 // exact).
+#include <climits>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -51,6 +52,12 @@ constexpr int kChunk = 256;    // edges per top-down chunk task of the allocatio
 constexpr int kDefaultChunk = 128;   // default of options.td_chunk (measured best at R-MAT 26)
 constexpr int kMinChunk = 64;  // smallest chunk task: the task lists are sized for it
 constexpr int kStage = 256;    // per-warp shared-memory staging of next-queue entries
+
+// Shared memory that phases of the CSR kernel borrow in turn: the top-down
+// staging slices, bottom-up phase A's searcher lists, and the two frontier
+// buffers of the cluster levels.
+__shared__ __align__(16) int g_stage[kWarps][kStage];
+__shared__ __align__(16) unsigned short g_list[kBlock / 32][1024];
 constexpr long long kPrefetchNf = 1 << 16;   // top-down levels below this prefetch the next rows
 #ifndef BFS_TD_CHECK
 #define BFS_TD_CHECK 0   // 1: top-down gather reads the visited word before claiming (hub chunks always do)
@@ -110,6 +117,12 @@ struct SingleParams {
     int nroots;    // > 1: roots already copied into queue0[0..nroots)
     int mode, alpha, beta, parent_mode, big_deg;
     int td_chunk;      // edges per top-down chunk task (>= kMinChunk)
+    // cluster levels: CTAs per thread-block cluster of the launch (1 = none);
+    // cluster 0 runs a top-down level alone while the frontier holds at most
+    // clu_nf vertices and clu_mf edges and no vertex of degree above clu_big
+    // (0 when off: the top-down flushes then count no heavy vertices)
+    int clu_c, clu_big;
+    long long clu_nf, clu_mf;
     unsigned long long seed;
     unsigned long long timeout_ns;
     unsigned expected;
@@ -435,19 +448,23 @@ struct WarpStage {
     int* buf;   // kStage entries of this warp's shared-memory slice
     int cnt;    // warp-uniform fill level
     bool pf;    // prefetch the rows of flushed vertices into L2 (small levels)
+    unsigned hv;   // this lane's flushed vertices of degree above the cluster-level cap
 };
 
 // Degree of a vertex just appended to the next queue, into acc_m.  On small
 // levels the next level is latency-bound: start its column reads now.
-__device__ __forceinline__ void flush_degree(const SingleParams& p, int v, bool pf, unsigned long long& acc_m) {
+__device__ __forceinline__ void flush_degree(const SingleParams& p, int v, bool pf, unsigned long long& acc_m,
+                                             unsigned& hv) {
     const unsigned d8 = p.deg8 ? (unsigned)__ldg(p.deg8 + v) : 255u;
     if (d8 < 255u && !pf) {
         acc_m += d8;
+        hv += (int)d8 > p.clu_big;
         return;
     }
     long long rs, re;
     row_of(p, v, rs, re);
     acc_m += (unsigned long long)(re - rs);
+    hv += re - rs > (long long)p.clu_big;
     if (pf && re > rs) asm volatile("prefetch.global.L2 [%0];" ::"l"(p.cols + rs));
 }
 
@@ -457,14 +474,14 @@ __device__ __forceinline__ void flush_degree(const SingleParams& p, int v, bool 
 // in flight together (one by one they would be a chain of dependent DRAM reads).
 constexpr int kFlushBatch = 8;
 
-__device__ __forceinline__ void flush_entries(const SingleParams& p, const WarpStage& st, int* qnext,
+__device__ __forceinline__ void flush_entries(const SingleParams& p, WarpStage& st, int* qnext,
                                               unsigned long long base, unsigned long long& acc_m) {
     const int lane = lane_id();
     if (!p.deg8 || st.pf) {
         for (int i = lane; i < st.cnt; i += 32) {
             const int v = st.buf[i];
             qnext[base + i] = v;
-            flush_degree(p, v, st.pf, acc_m);
+            flush_degree(p, v, st.pf, acc_m, st.hv);
         }
         return;
     }
@@ -481,7 +498,9 @@ __device__ __forceinline__ void flush_entries(const SingleParams& p, const WarpS
         for (int k = 0; k < kFlushBatch; k++) {
             if (vs[k] < 0) continue;
             qnext[base + i0 + k * 32 + lane] = vs[k];
-            acc_m += d8[k] < 255u ? (unsigned long long)d8[k] : (unsigned long long)deg_of(p, vs[k]);
+            const long long dg = d8[k] < 255u ? (long long)d8[k] : deg_of(p, vs[k]);
+            acc_m += (unsigned long long)dg;
+            st.hv += dg > (long long)p.clu_big;
         }
     }
 }
@@ -562,16 +581,16 @@ __device__ __forceinline__ void td_visit(const SingleParams& p, int d, int u, in
 }
 
 __device__ __forceinline__ WarpStage warp_stage() {
-    __shared__ int s_stage[kWarps][kStage];
     WarpStage st;
-    st.buf = s_stage[threadIdx.x >> 5];
+    st.buf = g_stage[threadIdx.x >> 5];
     st.cnt = 0;
     st.pf = false;
+    st.hv = 0;
     return st;
 }
 
 __device__ void td_phase(const SingleParams& p, int d, const int* qcur, long long nf, int* qnext, int snext,
-                         unsigned long long& acc_m) {
+                         unsigned long long& acc_m, unsigned long long& acc_h) {
     const int lane = lane_id();
     const long long gw = gtid() >> 5, nw = gthreads() >> 5;
     unsigned long long* tail = &p.ctrl->tail[snext];
@@ -636,10 +655,11 @@ __device__ void td_phase(const SingleParams& p, int d, const int* qcur, long lon
         }
     }
     block_flush(p, st, qnext, tail, acc_m);
+    acc_h += st.hv;
 }
 
 __device__ void task_phase(const SingleParams& p, int d, long long ntask, int* qnext, int snext,
-                           unsigned long long& acc_m) {
+                           unsigned long long& acc_m, unsigned long long& acc_h) {
     const int lane = lane_id();
     const long long gw = gtid() >> 5, nw = gthreads() >> 5;
     unsigned long long* tail = &p.ctrl->tail[snext];
@@ -677,6 +697,7 @@ __device__ void task_phase(const SingleParams& p, int d, long long ntask, int* q
         }
     }
     block_flush(p, st, qnext, tail, acc_m);
+    acc_h += st.hv;
 }
 
 // parent_mode MIN_ID, after the last level: every reached v other than a root
@@ -1011,10 +1032,8 @@ __device__ void bu_compact(const SingleParams& p, int d, const unsigned* fcur, u
                            unsigned long long* misscnt, unsigned long long& acc_n, unsigned long long& acc_left,
                            unsigned long long& acc_sc, unsigned long long& acc_ex) {
     __shared__ unsigned s_cnext[kBlock / 32][32];
-    // the chunk's searchers as offsets within the chunk (0..1023), in vertex order
-    __shared__ unsigned short s_list[kBlock / 32][1024];
     const int lane = lane_id(), wib = threadIdx.x >> 5;
-    unsigned short* list = s_list[wib];
+    unsigned short* list = g_list[wib];
     const long long nchunk = (p.W + 31) / 32;
     s_cnext[wib][lane] = 0u;
     WarpStage mst = warp_stage();
@@ -1226,6 +1245,408 @@ __device__ void bu_phase_b(const SingleParams& p, int d, const unsigned* fcur, u
     }
 }
 
+// ------------------------------------------------------------------ cluster levels
+//
+// A top-down level with a small frontier costs the grid a chain of dependent
+// global round trips (queue, offsets, columns, claim, queue tail) and a grid
+// barrier of several hundred CTAs: on a graph of large diameter (a mesh or a
+// torus) that fixed cost is the whole search.  While the frontier stays small,
+// the CTAs of thread-block cluster 0 run the levels alone: the frontier lives
+// in their shared memory, each CTA takes an equal share of it from whichever
+// CTA discovered it (distributed shared memory), a frontier entry carries its
+// row's offset and degree (read once, when the vertex is claimed), and a
+// level ends at the hardware cluster barrier.  The other CTAs wait on a flag
+// until the frontier outgrows the cluster (or the direction rule picks
+// bottom-up), when the cluster writes the frontier back to the global queue
+// and the grid takes over at that level.  Levels, parents, claims and the
+// per-level counters are those of the grid's top-down step.
+
+constexpr int kCluMaxC = 16;
+constexpr int kCluBig = 128;            // largest degree of a vertex in a cluster level's frontier
+constexpr int kCluEdgesPerCta = 4096;   // a cluster level takes at most this many edges per CTA
+constexpr long long kCluAutoMaxDeg = 32;   // automatic: cluster levels on graphs of max degree <= this
+constexpr long long kCluSpecNf = 1024;   // smaller levels read every target's row offsets with its claim
+constexpr long long kCluPfNf = 2048;     // smaller levels prefetch the claimed rows into L2
+constexpr int kCluDegShift = 40;         // a frontier entry's row: offset | degree << 40
+struct CluEntry {
+    unsigned long long row;   // first column index of the row | min(degree, 2^24 - 1) << 40
+    int v;                    // vertex
+    int par;                  // its parent (-1: not known), whose edge the expansion skips
+};
+static_assert(sizeof(CluEntry) == 16, "a frontier entry is one 16-byte load");
+__device__ __forceinline__ unsigned long long clu_row(long long s, long long deg) {
+    return (unsigned long long)s | ((unsigned long long)min(deg, (long long)0xFFFFFF) << kCluDegShift);
+}
+constexpr int kCluCap = (int)((sizeof(g_stage) < sizeof(g_list) ? sizeof(g_stage) : sizeof(g_list)) /
+                              sizeof(CluEntry));   // entries per CTA buffer
+constexpr unsigned long long kCluCntMask = 0x7FFFull;   // entry count field of a summary word
+static_assert(kCluCap <= 0x7FFF, "entry count field");
+
+__device__ __forceinline__ unsigned clu_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ unsigned clu_id() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ unsigned clu_nranks() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+// every thread of every CTA of the cluster, from warp-uniform code; orders
+// shared-memory (local and remote) writes before it against reads after it.
+// The aligned form (the warp executes it together, as after the __syncwarp)
+// keeps the kernel's register allocation intact; the unaligned form does not.
+__device__ __forceinline__ void clu_sync() {
+    __syncwarp();
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// the shared::cluster address of `local` in CTA `rank` of this cluster
+__device__ __forceinline__ unsigned clu_map(const void* local, unsigned rank) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(local);
+    unsigned r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void clu_ld_entry(unsigned addr, long long& s, int& deg, int& v, int& par) {
+    unsigned long long a, b;
+    asm volatile("ld.shared::cluster.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "r"(addr) : "memory");
+    s = (long long)(a & ((1ull << kCluDegShift) - 1ull));
+    deg = (int)(a >> kCluDegShift);
+    v = (int)(unsigned)b;
+    par = (int)(unsigned)(b >> 32);
+}
+__device__ __forceinline__ void clu_st64(unsigned addr, unsigned long long x) {
+    asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(addr), "l"(x) : "memory");
+}
+
+// Per-CTA summaries of a frontier, pushed by each CTA into every CTA of the
+// cluster: [parity][rank] = {entries | heavy << 15 | spilled << 32, degree sum}.
+__shared__ unsigned long long g_csum[2][kCluMaxC][2];
+
+struct CluState {
+    int d;                 // next level for the grid (done: the last level)
+    long long nf, mf, mu, reached;
+    bool done;
+};
+
+// Expand level L of the cluster's frontier (entries in `cur` of every CTA,
+// counts in g_csum[b]) into this CTA's `next` buffer.  Entries past the
+// buffer spill to the front of queue0 (the level after is then the grid's).
+__device__ void clu_expand(const SingleParams& p, int L, int C, int r, int b, long long nf, const CluEntry* cur,
+                           CluEntry* next, int* s_lcnt, unsigned long long& acc_m, unsigned& acc_h) {
+    const int lane = lane_id(), nwb = blockDim.x >> 5, wib = threadIdx.x >> 5;
+    const long long cw = (long long)r * nwb + wib, ncw = (long long)C * nwb;
+    const long long per = nf >= ncw * 32 ? 32 : max(1LL, (nf + ncw - 1) / ncw);
+    for (long long base = cw * per; base < nf; base += ncw * per) {
+        const long long i = base + lane;
+        int u = 0, deg = 0, pu = -1;
+        long long s = 0;
+        if (lane < per && i < nf) {
+            // owner CTA of entry i (the entries are numbered CTA by CTA)
+            int q = 0;
+            long long acc = 0;
+            while (q < C - 1) {
+                const long long c = (long long)(g_csum[b][q][0] & kCluCntMask);
+                if (i < acc + c) break;
+                acc += c;
+                q++;
+            }
+            if (i - acc < kCluCap) clu_ld_entry(clu_map(cur + (i - acc), (unsigned)q), s, deg, u, pu);
+        }
+        const int incl = warp_inclusive_scan(deg);
+        const int total = __shfl_sync(kFull, incl, 31);
+        const int excl = incl - deg;
+        // four edges per lane per round: the column reads, then the claims (on a
+        // small level together with every target's row offsets, else the
+        // claimed rows' offsets after them), each four in flight together; the
+        // edge back to a vertex's parent is known visited and skipped
+        const bool spec = nf < kCluSpecNf;
+        for (int k0 = 0; k0 < total; k0 += 128) {
+            int v[4], uu[4];
+            bool act[4];
+#pragma unroll
+            for (int q4 = 0; q4 < 4; q4++) {
+                const int k = k0 + q4 * 32 + lane;
+                int j = 0;
+#pragma unroll
+                for (int step = 16; step >= 1; step >>= 1) {
+                    const int c = __shfl_sync(kFull, incl, j + step - 1);
+                    if (c <= k) j += step;
+                }
+                const long long sj = __shfl_sync(kFull, s, j);
+                const int exj = __shfl_sync(kFull, excl, j);
+                const int pj = __shfl_sync(kFull, pu, j);
+                uu[q4] = __shfl_sync(kFull, u, j);
+                act[q4] = k < total;
+                v[q4] = act[q4] ? __ldg(p.cols + sj + (k - exj)) : 0;
+                act[q4] = act[q4] && v[q4] != pj;
+            }
+            long long rs[4], re[4];
+#pragma unroll
+            for (int q4 = 0; q4 < 4; q4++) {
+                rs[q4] = 0;
+                re[q4] = 0;
+            }
+            if (spec) {
+#pragma unroll
+                for (int q4 = 0; q4 < 4; q4++)
+                    if (act[q4]) {
+                        rs[q4] = __ldg(p.off + v[q4]);
+                        re[q4] = __ldg(p.off + v[q4] + 1);
+                    }
+            }
+            bool cl[4];
+#pragma unroll
+            for (int q4 = 0; q4 < 4; q4++) {
+                const unsigned bit = 1u << (v[q4] & 31);
+                cl[q4] = act[q4] && !(atomicOr(p.visited + (v[q4] >> 5), bit) & bit);
+            }
+            if (!spec) {
+#pragma unroll
+                for (int q4 = 0; q4 < 4; q4++)
+                    if (cl[q4]) {
+                        rs[q4] = __ldg(p.off + v[q4]);
+                        re[q4] = __ldg(p.off + v[q4] + 1);
+                    }
+            }
+            const int mine = (int)cl[0] + (int)cl[1] + (int)cl[2] + (int)cl[3];
+            const int inc2 = warp_inclusive_scan(mine);
+            const int tot2 = __shfl_sync(kFull, inc2, 31);
+            if (tot2 == 0) continue;
+            int pos = 0;
+            if (lane == 0) pos = atomicAdd(s_lcnt, tot2);
+            pos = __shfl_sync(kFull, pos, 0) + inc2 - mine;
+#pragma unroll
+            for (int q4 = 0; q4 < 4; q4++) {
+                if (!cl[q4]) continue;
+                const int vv = v[q4];
+                if (p.parent) p.parent[vv] = uu[q4];
+                set_level(p, vv, L + 1);
+                const long long dg = re[q4] - rs[q4];
+                acc_m += (unsigned long long)dg;
+                acc_h |= dg > (long long)p.clu_big;
+                if (dg > 0 && nf < kCluPfNf) asm volatile("prefetch.global.L2 [%0];" ::"l"(p.cols + rs[q4]));
+                if (pos < kCluCap) {
+                    CluEntry e;
+                    e.row = clu_row(rs[q4], dg);
+                    e.v = vv;
+                    e.par = uu[q4];
+                    next[pos] = e;
+                } else {
+                    const unsigned long long sp = atomicAdd(&p.ctrl->clu_spill, 1ull);
+                    p.queue0[sp] = vv;
+                }
+                pos++;
+            }
+        }
+    }
+}
+
+// Levels d0, d0+1, ... run by the CTAs of cluster 0 (every thread of them
+// calls).  Enters with the frontier of level d0 in `qcur` (nf0 vertices, mf0
+// edges, none above the degree cap); leaves when the search is done or the
+// grid must take the next level, with the state for it in `out` and, for the
+// waiting CTAs, in the control block.
+__device__ void cluster_levels(const SingleParams& p, const int* qcur, int d0, long long nf0, long long mf0,
+                               long long mu0, long long reached0, unsigned long long epi, uint64_t t_start,
+                               CluState& out) {
+    __shared__ int s_lcnt, s_lh;
+    __shared__ unsigned long long s_lm;
+    Ctrl* c = p.ctrl;
+    const int C = p.clu_c, r = (int)clu_rank(), tid = threadIdx.x, nth = blockDim.x;
+    const int lane = lane_id(), wib = tid >> 5;
+    const bool lead = blockIdx.x == 0 && tid == 0;
+    CluEntry* const buf0 = reinterpret_cast<CluEntry*>(&g_stage[0][0]);
+    CluEntry* const buf1 = reinterpret_cast<CluEntry*>(&g_list[0][0]);
+    // this CTA's share of the entry frontier, with the rows' offsets and degrees
+    {
+        const long long lo = nf0 * r / C, hi = nf0 * (r + 1) / C;
+        for (long long i = lo + tid; i < hi; i += nth) {
+            const int u = __ldcg(qcur + i);
+            long long rs, re;
+            row_of(p, u, rs, re);
+            CluEntry e;
+            e.row = clu_row(rs, re - rs);
+            e.v = u;
+            e.par = -1;
+            buf0[i - lo] = e;
+        }
+        if (tid < C) {
+            const long long cnt = nf0 * (tid + 1) / C - nf0 * tid / C;
+            g_csum[0][tid][0] = (unsigned long long)cnt;
+            g_csum[0][tid][1] = tid == 0 ? (unsigned long long)mf0 : 0ull;
+        }
+        if (tid == 0) {
+            s_lcnt = 0;
+            s_lh = 0;
+            s_lm = 0;
+        }
+    }
+    clu_sync();
+    int L = d0, b = 0;
+    long long mu = mu0, reached = reached0, pnf = 0, pmf = 0;
+    while (true) {
+        long long nf = 0, mf = 0, spill = 0;
+        bool heavy = false;
+        for (int q = 0; q < C; q++) {
+            const unsigned long long w0 = g_csum[b][q][0];
+            nf += (long long)(w0 & kCluCntMask) + (long long)(w0 >> 32);
+            spill += (long long)(w0 >> 32);
+            heavy |= ((w0 >> 15) & 1ull) != 0;
+            mf += (long long)g_csum[b][q][1];
+        }
+        if (L > d0) {
+            if (lead && L - 1 < p.rec_cap) {
+                bfs_level_record rec;
+                rec.dir = TD;
+                rec.misses = 0;
+                rec.nf = pnf;
+                rec.mf = pmf;
+                rec.nnext = nf;
+                rec.mnext = mf;
+                rec.scanned = 0;
+                rec.examined = pmf;
+                rec.t_ns = (long long)(globaltimer_ns() - t_start);
+                rec.aux = -1;   // a cluster level
+                rec.t_mid_ns = 0;
+                p.rec[L - 1] = rec;
+            }
+            if (nf > 0) {
+                reached += nf;
+                mu -= mf;
+            }
+        }
+        const bool done = nf == 0;
+        const bool leave = done || spill > 0 || heavy || nf > p.clu_nf || mf > p.clu_mf ||
+                           decide_dir(p, TD, nf, mf, mu, L) != TD;
+        if (leave) {
+            if (!done) {
+                // the frontier back to queue0: spilled entries first, then CTA by CTA
+                long long pre = spill;
+                for (int q = 0; q < r; q++) pre += (long long)(g_csum[b][q][0] & kCluCntMask);
+                const int mine = (int)(g_csum[b][r][0] & kCluCntMask);
+                const CluEntry* cur = b ? buf1 : buf0;
+                for (int i = tid; i < mine; i += nth) p.queue0[pre + i] = cur[i].v;
+            }
+            out.d = done ? L - 1 : L;
+            out.nf = nf;
+            out.mf = mf;
+            out.mu = mu;
+            out.reached = reached;
+            out.done = done;
+            if (lead) {
+                // the grid resumes at level L with every per-level counter slot clear
+                for (int k = 0; k < 3; k++) {
+                    c->tail[k] = 0;
+                    c->accn[k] = 0;
+                    c->accm[k] = 0;
+                    c->scanned[k] = 0;
+                    c->examined[k] = 0;
+                    c->ntask[k] = 0;
+                    c->nmiss[k] = 0;
+                    c->dsum_out[k] = 0;
+                    c->dsum_in[k] = 0;
+                    c->heavy[k] = 0;
+                }
+                c->clu_spill = 0;
+                c->clu_d = out.d;
+                c->clu_nf = nf;
+                c->clu_mf = mf;
+                c->clu_mu = mu;
+                c->clu_reached = reached;
+                c->clu_done = done ? 1 : 0;
+            }
+            // every CTA's queue, level, parent and claim writes, then the hand-over
+            __threadfence();
+            clu_sync();
+            if (lead) asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(&c->clu_gen), "l"(epi) : "memory");
+            return;
+        }
+        if (lead) asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(&c->clu_prog), "l"((unsigned long long)L)
+                               : "memory");
+        unsigned long long am = 0;
+        unsigned ah = 0;
+        clu_expand(p, L, C, r, b, nf, b ? buf1 : buf0, b ? buf0 : buf1, &s_lcnt, am, ah);
+        am = warp_sum(am);
+        const bool hw = __any_sync(kFull, ah != 0);
+        if (lane == 0) {
+            if (am) atomicAdd(&s_lm, am);
+            if (hw) s_lh = 1;
+        }
+        __syncthreads();
+        if (wib == 0) {
+            const int lc = s_lcnt;
+            const unsigned long long lm = s_lm;
+            const int lh = s_lh;
+            const int cnt = lc < kCluCap ? lc : kCluCap;
+            const unsigned long long w0 = (unsigned long long)cnt | ((unsigned long long)(lh ? 1 : 0) << 15) |
+                                          ((unsigned long long)(lc - cnt) << 32);
+            if (lane < C) {
+                clu_st64(clu_map(&g_csum[b ^ 1][r][0], (unsigned)lane), w0);
+                clu_st64(clu_map(&g_csum[b ^ 1][r][1], (unsigned)lane), lm);
+            }
+            __syncwarp();
+            if (lane == 0) {
+                s_lcnt = 0;
+                s_lh = 0;
+                s_lm = 0;
+            }
+        }
+        clu_sync();
+        pnf = nf;
+        pmf = mf;
+        L++;
+        b ^= 1;
+    }
+}
+
+// A CTA outside cluster 0 during cluster levels: thread 0 waits for episode
+// `epi` to end (giving up only when the cluster makes no progress for the
+// run's time limit); then every thread reads the state the cluster left.
+__device__ bool clu_wait(const SingleParams& p, unsigned long long epi, CluState& out) {
+    __shared__ int s_ok;
+    Ctrl* c = p.ctrl;
+    if (threadIdx.x == 0) {
+        uint64_t t0 = globaltimer_ns();
+        unsigned long long last = ~0ull;
+        int ok = 1;
+        unsigned spins = 0;
+        while (true) {
+            if (ld_acquire64(&c->clu_gen) >= epi) break;
+            if (ld_relaxed64(&c->b.count) & kAbortBit) {
+                ok = 0;
+                break;
+            }
+            const unsigned long long pr = ld_relaxed64(&c->clu_prog);
+            const uint64_t now = globaltimer_ns();
+            if (pr != last) {
+                last = pr;
+                t0 = now;
+            } else if (now - t0 > p.timeout_ns) {
+                raise_status(&c->b, kDevTimeout);
+                ok = 0;
+                break;
+            }
+            __nanosleep(++spins < 16 ? 128 : 512);
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    if (!s_ok) return false;
+    out.d = (int)ld_relaxed64(reinterpret_cast<const unsigned long long*>(&c->clu_d));
+    out.nf = (long long)ld_relaxed64(reinterpret_cast<const unsigned long long*>(&c->clu_nf));
+    out.mf = (long long)ld_relaxed64(reinterpret_cast<const unsigned long long*>(&c->clu_mf));
+    out.mu = (long long)ld_relaxed64(reinterpret_cast<const unsigned long long*>(&c->clu_mu));
+    out.reached = (long long)ld_relaxed64(reinterpret_cast<const unsigned long long*>(&c->clu_reached));
+    out.done = ld_relaxed64(reinterpret_cast<const unsigned long long*>(&c->clu_done)) != 0;
+    return true;
+}
+
 // ------------------------------------------------------------------ kernel
 
 __global__ void __launch_bounds__(kBlock, BFS_MIN_BLOCKS) bfs_single_kernel(SingleParams p) {
@@ -1261,8 +1682,32 @@ __global__ void __launch_bounds__(kBlock, BFS_MIN_BLOCKS) bfs_single_kernel(Sing
     int prev = TD, qsel = 0, bsel = 0, d = 0;
     const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
     const uint64_t t_start = lead ? globaltimer_ns() : 0;
+    // cluster levels only in a launch whose clusters have the size the parameters name
+    const bool clu_on = p.clu_c > 1 && clu_nranks() == (unsigned)p.clu_c;
+    unsigned long long epi = 0;
+    int no_clu = -1;   // the level a cluster episode just handed back (the grid takes it)
     while (true) {
         const int dir = decide_dir(p, prev, nf, mf, mu, d);
+        if (clu_on && dir == TD && prev == TD && d != no_clu && nf <= p.clu_nf && mf <= p.clu_mf &&
+            (d == 0 ? mf <= (long long)p.clu_big : ld_relaxed64(&c->heavy[d % 3]) == 0ull)) {
+            epi++;
+            CluState cs;
+            if (clu_id() == 0) {
+                cluster_levels(p, qsel ? p.queue1 : p.queue0, d, nf, mf, mu, reached, epi, t_start, cs);
+            } else if (!clu_wait(p, epi, cs)) {
+                return;
+            }
+            d = cs.d;
+            reached = cs.reached;
+            if (cs.done) break;
+            nf = cs.nf;
+            mf = cs.mf;
+            mu = cs.mu;
+            prev = TD;
+            qsel = 0;   // the frontier is back in queue0
+            no_clu = d;
+            continue;
+        }
         const int scur = d % 3, snext = (d + 1) % 3, sfree = (d + 2) % 3;
         if (lead) {
             c->tail[sfree] = 0;
@@ -1274,6 +1719,7 @@ __global__ void __launch_bounds__(kBlock, BFS_MIN_BLOCKS) bfs_single_kernel(Sing
             c->nmiss[sfree] = 0;
             c->dsum_out[sfree] = 0;
             c->dsum_in[sfree] = 0;
+            c->heavy[sfree] = 0;
         }
         long long nf_next, scanned = 0, examined = mf, aux = 0, misses = 0;
         uint64_t t_mid = 0;
@@ -1286,17 +1732,18 @@ __global__ void __launch_bounds__(kBlock, BFS_MIN_BLOCKS) bfs_single_kernel(Sing
                 bitmap_to_queue(p, fcur, fnext, qcur, &c->tail[scur]);
                 if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
             }
-            unsigned long long am = 0;
-            td_phase(p, d, qcur, nf, qnext, snext, am);
-            block_add4(0, am, 0, 0, nullptr, &c->accm[snext], nullptr, nullptr);
+            unsigned long long am = 0, ah = 0;
+            unsigned long long* gh = clu_on ? &c->heavy[snext] : nullptr;
+            td_phase(p, d, qcur, nf, qnext, snext, am, ah);
+            block_add4(ah, am, 0, 0, gh, &c->accm[snext], nullptr, nullptr);
             if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
             const long long nt = (long long)ld_relaxed64(&c->ntask[snext]);
             aux = nt;
             if (lead) t_mid = globaltimer_ns();
             if (nt > 0) {
-                unsigned long long am2 = 0;
-                task_phase(p, d, nt, qnext, snext, am2);
-                block_add4(0, am2, 0, 0, nullptr, &c->accm[snext], nullptr, nullptr);
+                unsigned long long am2 = 0, ah2 = 0;
+                task_phase(p, d, nt, qnext, snext, am2, ah2);
+                block_add4(ah2, am2, 0, 0, gh, &c->accm[snext], nullptr, nullptr);
                 if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
             }
             nf_next = (long long)ld_relaxed64(&c->tail[snext]);
@@ -1851,6 +2298,10 @@ bfs_status single_launch_work(bfs_graph* g, SingleWork& w, const int32_t* roots_
     p.parent_mode = opt.parent_mode;
     p.big_deg = opt.td_big_degree > 0 ? opt.td_big_degree : 96;
     p.td_chunk = opt.td_chunk > 0 ? opt.td_chunk : bfsk::kDefaultChunk;
+    p.clu_c = 1;
+    p.clu_big = 0;
+    p.clu_nf = 0;
+    p.clu_mf = 0;
     p.seed = opt.seed;
     p.timeout_ns = (unsigned long long)(opt.timeout_ms > 0 ? opt.timeout_ms : 10000) * 1000000ull;
     const unsigned extra = (unsigned)(g->debug_barrier_extra > 0 ? g->debug_barrier_extra : 0);
@@ -1888,8 +2339,65 @@ bfs_status single_launch_work(bfs_graph* g, SingleWork& w, const int32_t* roots_
         block = bfsk::kDBlock;
         p.expected = (unsigned)grid + extra;
     }
+    // cluster levels (CSR, undirected): the launch in clusters of C CTAs, as many as fit
+    int C = 1;
+    if (!dcsc && !g->directed)
+        C = opt.cluster_size > 0 ? opt.cluster_size : (g->max_degree <= bfsk::kCluAutoMaxDeg ? 16 : 1);
+    while (C > 1 && C > grid) C >>= 1;   // a small grid (a server's executor) is one cluster at most
+    if (C > 1) {
+        int li = 0;
+        while ((1 << li) < C) li++;
+        if (w.clu_grid[li] == 0) {
+            BFS_CUDA_TRY(cudaFuncSetAttribute(bfsk::bfs_single_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = (unsigned)C;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3((unsigned)C);
+            cfg.blockDim = dim3((unsigned)block);
+            cfg.dynamicSmemBytes = dyn;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            int ncl = 0;
+            BFS_CUDA_TRY(cudaOccupancyMaxActiveClusters(&ncl, bfsk::bfs_single_kernel, &cfg));
+            w.clu_grid[li] = ncl > 0 ? ncl * C : -1;
+        }
+        const int g2 = (grid < w.clu_grid[li] ? grid : w.clu_grid[li]) / C * C;
+        if (g2 < C) {
+            C = 1;   // clusters of this size cannot be resident, or the grid is smaller: plain launch
+        } else {
+            grid = g2;
+            p.expected = (unsigned)grid + extra;
+        }
+    }
+    if (C > 1) {
+        p.clu_c = C;
+        p.clu_big = bfsk::kCluBig;
+        p.clu_nf = (long long)C * (bfsk::kCluCap / 2);
+        p.clu_mf = (long long)C * bfsk::kCluEdgesPerCta;
+    }
     BFS_CUDA_TRY(cudaMemsetAsync(w.ctrl, 0, sizeof(Ctrl), s));
     if (k > 1) BFS_CUDA_TRY(cudaMemcpyAsync(w.queue0, roots_host, sizeof(int32_t) * (size_t)k, cudaMemcpyHostToDevice, s));
+    if (C > 1) {
+        cudaLaunchAttribute at[2];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)C;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        at[1].id = cudaLaunchAttributeCooperative;
+        at[1].val.cooperative = 1;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)grid);
+        cfg.blockDim = dim3((unsigned)block);
+        cfg.dynamicSmemBytes = dyn;
+        cfg.stream = s;
+        cfg.attrs = at;
+        cfg.numAttrs = 2;
+        BFS_CUDA_TRY(cudaLaunchKernelEx(&cfg, bfsk::bfs_single_kernel, p));
+        return BFS_OK;
+    }
     void* args[] = {&p};
     const void* fn = dcsc ? (const void*)bfsk::bfs_dcsc_kernel : (const void*)bfsk::bfs_single_kernel;
     BFS_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, dyn, s));
@@ -2019,6 +2527,10 @@ extern "C" bfs_status bfs_run_csr_noalloc(const int64_t* row_offsets, const int3
     p.parent_mode = BFS_PARENT_ANY;
     p.big_deg = 96;
     p.td_chunk = bfsk::kChunk;
+    p.clu_c = 1;
+    p.clu_big = 0;
+    p.clu_nf = 0;
+    p.clu_mf = 0;
     p.timeout_ns = 10000ull * 1000000ull;
     p.expected = (unsigned)grid;
     const int ig = (int)std::min<long long>((W + 255) / 256, (long long)g_noalloc_sms[dev] * 4);

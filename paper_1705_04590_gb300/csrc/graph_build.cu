@@ -113,13 +113,22 @@ __global__ void k_count_active(const uint32_t* __restrict__ iso, long long W, un
 }
 
 // deg8[v] = min(deg(v), 255): the degree as bottom-up and top-down steps need it
-// (a coalesced byte stream instead of two int64 offsets per vertex)
-__global__ void k_deg8(const long long* __restrict__ off, long long n, uint8_t* __restrict__ deg8) {
+// (a coalesced byte stream instead of two int64 offsets per vertex); and the
+// largest degree into *dmax
+__global__ void k_deg8(const long long* __restrict__ off, long long n, uint8_t* __restrict__ deg8,
+                       unsigned long long* dmax) {
     const long long nth = (long long)gridDim.x * blockDim.x;
+    unsigned long long mx = 0;
     for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n + 32; v += nth) {
         const long long dg = v < n ? off[v + 1] - off[v] : 0;
         deg8[v] = (uint8_t)(dg < 255 ? dg : 255);
+        mx = dg > (long long)mx ? (unsigned long long)dg : mx;
     }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long t = __shfl_xor_sync(0xffffffffu, mx, o);
+        mx = t > mx ? t : mx;
+    }
+    if ((threadIdx.x & 31) == 0 && mx) atomicMax(dmax, mx);
 }
 
 // CSR validation: warp per row.  bad codes: 1 offsets, 2 id range, 3 order/duplicate, 4 self-loop, 5 asymmetric
@@ -219,16 +228,25 @@ bfs_status build_isolated_bitmap(bfs_graph* g, cudaStream_t s) {
     g->deg8 = (uint8_t*)g->mem.alloc((size_t)g->n + 32, s);
     if (!g->deg8) return fail(BFS_ERR_OOM, "graph build: degree bytes");
     g->graph_bytes += (size_t)g->n + 32;
-    k_deg8<<<grid_for(g->n + 32, 256, g->sm_count), 256, 0, s>>>((const long long*)g->offsets, g->n, g->deg8);
+    Scratch dm(&g->mem, s);
+    if (!dm.get(16)) return fail(BFS_ERR_OOM, "graph build: counter");
+    BFS_CUDA_TRY(cudaMemsetAsync(dm.p, 0, 16, s));
+    unsigned long long* dmax = (unsigned long long*)dm.p;
+    k_deg8<<<grid_for(g->n + 32, 256, g->sm_count), 256, 0, s>>>((const long long*)g->offsets, g->n, g->deg8,
+                                                                 dmax);
     BFS_CUDA_TRY(cudaGetLastError());
     if (g->directed) {
         g->deg8_in = (uint8_t*)g->mem.alloc((size_t)g->n + 32, s);
         if (!g->deg8_in) return fail(BFS_ERR_OOM, "graph build: in-degree bytes");
         g->graph_bytes += (size_t)g->n + 32;
         k_deg8<<<grid_for(g->n + 32, 256, g->sm_count), 256, 0, s>>>((const long long*)g->offsets_in, g->n,
-                                                                     g->deg8_in);
+                                                                     g->deg8_in, dmax + 1);
         BFS_CUDA_TRY(cudaGetLastError());
     }
+    unsigned long long h[2] = {0, 0};
+    BFS_CUDA_TRY(cudaMemcpyAsync(h, dmax, sizeof h, cudaMemcpyDeviceToHost, s));
+    BFS_CUDA_TRY(cudaStreamSynchronize(s));
+    g->max_degree = (int64_t)(h[0] > h[1] ? h[0] : h[1]);
     return BFS_OK;
 }
 

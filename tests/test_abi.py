@@ -60,9 +60,9 @@ def test_struct_layouts_match_header(tmp_path):
 #include <stddef.h>
 #include "bfs.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(bfs_options), sizeof(bfs_level_record), sizeof(bfs_stats),
-         sizeof(bfs_allocator), sizeof(bfs_dcsc_layout), offsetof(bfs_options, timeout_ms),
-         offsetof(bfs_options, ctas_per_sm), offsetof(bfs_stats, vertices_reached));
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(bfs_options), sizeof(bfs_level_record),
+         sizeof(bfs_stats), sizeof(bfs_allocator), sizeof(bfs_dcsc_layout), offsetof(bfs_options, timeout_ms),
+         offsetof(bfs_options, ctas_per_sm), offsetof(bfs_options, cluster_size), offsetof(bfs_stats, vertices_reached));
   return 0;
 }
 """)
@@ -71,5 +71,5 @@ int main(void) {
     got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
     want = [ctypes.sizeof(L.Options), ctypes.sizeof(L.LevelRecord), ctypes.sizeof(L.Stats),
             ctypes.sizeof(L.Allocator), ctypes.sizeof(L.DcscLayout), L.Options.timeout_ms.offset,
-            L.Options.ctas_per_sm.offset, L.Stats.vertices_reached.offset]
+            L.Options.ctas_per_sm.offset, L.Options.cluster_size.offset, L.Stats.vertices_reached.offset]
     assert got == want

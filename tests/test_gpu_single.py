@@ -432,12 +432,12 @@ def test_autotune_picks_a_grid_point_and_levels_do_not_change(gpu_lib, tmp_path,
     best, ms = autotune.autotune(case.g, roots)
     assert best.alpha in (6, 14, 24, 32, 96) and best.beta in (12, 24, 64, 128)
     assert best.td_big_degree in (64, 96, 256) and best.td_chunk in (0, 128, 256, 512, 1024)
-    assert best.ctas_per_sm in (0, 1)
+    assert best.ctas_per_sm in (0, 1) and best.cluster_size in (0, 1, 8, 16)
     assert ms > 0
     monkeypatch.setenv("BFS_AUTOTUNE_CACHE", str(tmp_path / "cache.json"))
     o1 = autotune.tuned_options(case.g, roots)
     o2 = autotune.tuned_options(case.g, roots)        # served from the cache file
-    knobs = ("alpha", "beta", "td_big_degree", "td_chunk", "ctas_per_sm")
+    knobs = ("alpha", "beta", "td_big_degree", "td_chunk", "ctas_per_sm", "cluster_size")
     assert [getattr(o1, k) for k in knobs] == [getattr(o2, k) for k in knobs]
     for root in roots:
         lv, pa, _ = case.run(root, o1)
