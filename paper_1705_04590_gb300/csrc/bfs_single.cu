@@ -448,6 +448,7 @@ struct WarpStage {
     int* buf;   // kStage entries of this warp's shared-memory slice
     int cnt;    // warp-uniform fill level
     bool pf;    // prefetch the rows of flushed vertices into L2 (small levels)
+    bool nodeg;    // no degrees at the flush (a directed graph sums them after the level)
     unsigned hv;   // this lane's flushed vertices of degree above the cluster-level cap
 };
 
@@ -477,6 +478,10 @@ constexpr int kFlushBatch = 8;
 __device__ __forceinline__ void flush_entries(const SingleParams& p, WarpStage& st, int* qnext,
                                               unsigned long long base, unsigned long long& acc_m) {
     const int lane = lane_id();
+    if (st.nodeg) {
+        for (int i = lane; i < st.cnt; i += 32) qnext[base + i] = st.buf[i];
+        return;
+    }
     if (!p.deg8 || st.pf) {
         for (int i = lane; i < st.cnt; i += 32) {
             const int v = st.buf[i];
@@ -585,17 +590,19 @@ __device__ __forceinline__ WarpStage warp_stage() {
     st.buf = g_stage[threadIdx.x >> 5];
     st.cnt = 0;
     st.pf = false;
+    st.nodeg = false;
     st.hv = 0;
     return st;
 }
 
 __device__ void td_phase(const SingleParams& p, int d, const int* qcur, long long nf, int* qnext, int snext,
-                         unsigned long long& acc_m, unsigned long long& acc_h) {
+                         bool nodeg, unsigned long long& acc_m, unsigned long long& acc_h) {
     const int lane = lane_id();
     const long long gw = gtid() >> 5, nw = gthreads() >> 5;
     unsigned long long* tail = &p.ctrl->tail[snext];
     WarpStage st = warp_stage();
-    st.pf = nf < kPrefetchNf;
+    st.nodeg = nodeg;
+    st.pf = !nodeg && nf < kPrefetchNf;
     // A small frontier is spread over every warp (fewer vertices per warp, so
     // each warp's edges take one gather round instead of several dependent ones).
     const long long per = nf >= nw * 32 ? 32 : max(1LL, (nf + nw - 1) / nw);
@@ -658,12 +665,13 @@ __device__ void td_phase(const SingleParams& p, int d, const int* qcur, long lon
     acc_h += st.hv;
 }
 
-__device__ void task_phase(const SingleParams& p, int d, long long ntask, int* qnext, int snext,
+__device__ void task_phase(const SingleParams& p, int d, long long ntask, int* qnext, int snext, bool nodeg,
                            unsigned long long& acc_m, unsigned long long& acc_h) {
     const int lane = lane_id();
     const long long gw = gtid() >> 5, nw = gthreads() >> 5;
     unsigned long long* tail = &p.ctrl->tail[snext];
     WarpStage st = warp_stage();
+    st.nodeg = nodeg;
     const long long nt = ntask < p.task_cap ? ntask : p.task_cap;
     for (long long t = gw; t < nt; t += nw) {
         const int4 raw = __ldcg(reinterpret_cast<const int4*>(p.tasks + t));
@@ -1265,8 +1273,6 @@ constexpr int kCluMaxC = 16;
 constexpr int kCluBig = 128;            // largest degree of a vertex in a cluster level's frontier
 constexpr int kCluEdgesPerCta = 4096;   // a cluster level takes at most this many edges per CTA
 constexpr long long kCluAutoMaxDeg = 32;   // automatic: cluster levels on graphs of max degree <= this
-constexpr long long kCluSpecNf = 1024;   // smaller levels read every target's row offsets with its claim
-constexpr long long kCluPfNf = 2048;     // smaller levels prefetch the claimed rows into L2
 constexpr int kCluDegShift = 40;         // a frontier entry's row: offset | degree << 40
 struct CluEntry {
     unsigned long long row;   // first column index of the row | min(degree, 2^24 - 1) << 40
@@ -1361,11 +1367,9 @@ __device__ void clu_expand(const SingleParams& p, int L, int C, int r, int b, lo
         const int incl = warp_inclusive_scan(deg);
         const int total = __shfl_sync(kFull, incl, 31);
         const int excl = incl - deg;
-        // four edges per lane per round: the column reads, then the claims (on a
-        // small level together with every target's row offsets, else the
-        // claimed rows' offsets after them), each four in flight together; the
-        // edge back to a vertex's parent is known visited and skipped
-        const bool spec = nf < kCluSpecNf;
+        // four edges per lane per round: the column reads, then the claims, then
+        // the claimed rows' offsets, each four in flight together; the edge back
+        // to a vertex's parent is known visited and skipped
         for (int k0 = 0; k0 < total; k0 += 128) {
             int v[4], uu[4];
             bool act[4];
@@ -1386,33 +1390,18 @@ __device__ void clu_expand(const SingleParams& p, int L, int C, int r, int b, lo
                 v[q4] = act[q4] ? __ldg(p.cols + sj + (k - exj)) : 0;
                 act[q4] = act[q4] && v[q4] != pj;
             }
-            long long rs[4], re[4];
-#pragma unroll
-            for (int q4 = 0; q4 < 4; q4++) {
-                rs[q4] = 0;
-                re[q4] = 0;
-            }
-            if (spec) {
-#pragma unroll
-                for (int q4 = 0; q4 < 4; q4++)
-                    if (act[q4]) {
-                        rs[q4] = __ldg(p.off + v[q4]);
-                        re[q4] = __ldg(p.off + v[q4] + 1);
-                    }
-            }
             bool cl[4];
 #pragma unroll
             for (int q4 = 0; q4 < 4; q4++) {
                 const unsigned bit = 1u << (v[q4] & 31);
                 cl[q4] = act[q4] && !(atomicOr(p.visited + (v[q4] >> 5), bit) & bit);
             }
-            if (!spec) {
+            long long rs[4], re[4];
 #pragma unroll
-                for (int q4 = 0; q4 < 4; q4++)
-                    if (cl[q4]) {
-                        rs[q4] = __ldg(p.off + v[q4]);
-                        re[q4] = __ldg(p.off + v[q4] + 1);
-                    }
+            for (int q4 = 0; q4 < 4; q4++) {
+                rs[q4] = 0;
+                re[q4] = 0;
+                if (cl[q4]) row_of(p, v[q4], rs[q4], re[q4]);
             }
             const int mine = (int)cl[0] + (int)cl[1] + (int)cl[2] + (int)cl[3];
             const int inc2 = warp_inclusive_scan(mine);
@@ -1430,7 +1419,7 @@ __device__ void clu_expand(const SingleParams& p, int L, int C, int r, int b, lo
                 const long long dg = re[q4] - rs[q4];
                 acc_m += (unsigned long long)dg;
                 acc_h |= dg > (long long)p.clu_big;
-                if (dg > 0 && nf < kCluPfNf) asm volatile("prefetch.global.L2 [%0];" ::"l"(p.cols + rs[q4]));
+                if (dg > 0) asm volatile("prefetch.global.L2 [%0];" ::"l"(p.cols + rs[q4]));
                 if (pos < kCluCap) {
                     CluEntry e;
                     e.row = clu_row(rs[q4], dg);
@@ -1734,7 +1723,9 @@ __global__ void __launch_bounds__(kBlock, BFS_MIN_BLOCKS) bfs_single_kernel(Sing
             }
             unsigned long long am = 0, ah = 0;
             unsigned long long* gh = clu_on ? &c->heavy[snext] : nullptr;
-            td_phase(p, d, qcur, nf, qnext, snext, am, ah);
+            // a directed graph sums the new frontier's degrees after the level
+            const bool nodeg = p.directed != 0;
+            td_phase(p, d, qcur, nf, qnext, snext, nodeg, am, ah);
             block_add4(ah, am, 0, 0, gh, &c->accm[snext], nullptr, nullptr);
             if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
             const long long nt = (long long)ld_relaxed64(&c->ntask[snext]);
@@ -1742,7 +1733,7 @@ __global__ void __launch_bounds__(kBlock, BFS_MIN_BLOCKS) bfs_single_kernel(Sing
             if (lead) t_mid = globaltimer_ns();
             if (nt > 0) {
                 unsigned long long am2 = 0, ah2 = 0;
-                task_phase(p, d, nt, qnext, snext, am2, ah2);
+                task_phase(p, d, nt, qnext, snext, nodeg, am2, ah2);
                 block_add4(ah2, am2, 0, 0, gh, &c->accm[snext], nullptr, nullptr);
                 if (!grid_sync(&c->b, p.expected, p.timeout_ns)) return;
             }
