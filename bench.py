@@ -537,7 +537,7 @@ def served_section(g26, roots26, n_queries: int = 2000, seed: int = 5151) -> dic
     def run_server(tr, arrivals):
         free = [list(range(len(pl))) for pl in pools]
         inflight = []    # (ticket, graph, buffer index)
-        lat, done_m = [], 0
+        lat, lat_g, done_m = [], [], 0
         submitted = 0
         t0 = time.perf_counter()
         for (gi, root), at in zip(tr, arrivals):
@@ -550,6 +550,7 @@ def served_section(g26, roots26, n_queries: int = 2000, seed: int = 5151) -> dic
                         if not srv.wait(tk, 300_000):
                             raise RuntimeError("served query did not complete within 300 s")
                         lat.append(srv.latency_us(tk))
+                        lat_g.append(gj)
                         done_m += ms[gj]
                         free[gj].append(bi)
                         inflight.pop(idx)
@@ -564,6 +565,7 @@ def served_section(g26, roots26, n_queries: int = 2000, seed: int = 5151) -> dic
                 for tk, gj, bj in inflight:
                     if srv.poll(tk):
                         lat.append(srv.latency_us(tk))
+                        lat_g.append(gj)
                         done_m += ms[gj]
                         free[gj].append(bj)
                     else:
@@ -573,11 +575,16 @@ def served_section(g26, roots26, n_queries: int = 2000, seed: int = 5151) -> dic
             if not srv.wait(tk, 300_000):
                 raise RuntimeError("served query did not complete within 300 s")
             lat.append(srv.latency_us(tk))
+            lat_g.append(gj)
             done_m += ms[gj]
         wall = time.perf_counter() - t0
         lat = np.array(lat) / 1e3
+        lat_g = np.array(lat_g)
+        by_graph = {specs[i][0]: round(float(np.percentile(lat[lat_g == i], 99)), 2)
+                    for i in range(len(graphs)) if (lat_g == i).any()}
         return {"wall_s": wall, "qps": len(tr) / wall, "gteps": done_m / wall / 1e9,
-                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))}
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "p99_ms_by_graph": by_graph}
 
     def run_fifo(tr, arrivals):
         lvs = [torch.empty(g.n, dtype=torch.int32, device="cuda") for g in graphs]

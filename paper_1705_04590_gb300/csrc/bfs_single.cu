@@ -56,7 +56,8 @@ constexpr int kStage = 256;    // per-warp shared-memory staging of next-queue e
 // Shared memory that phases of the CSR kernel borrow in turn: the top-down
 // staging slices, bottom-up phase A's searcher lists, and the two frontier
 // buffers of the cluster levels.
-__shared__ __align__(16) int g_stage[kWarps][kStage];
+__shared__ __align__(16) int g_stage[kBlock / 32][kStage];
+__shared__ __align__(16) int g_stage_d[kDBlock / 32][kStage];   // the DCSC kernel's (more warps per CTA)
 __shared__ __align__(16) unsigned short g_list[kBlock / 32][1024];
 constexpr long long kPrefetchNf = 1 << 16;   // top-down levels below this prefetch the next rows
 #ifndef BFS_TD_CHECK
@@ -585,15 +586,18 @@ __device__ __forceinline__ void td_visit(const SingleParams& p, int d, int u, in
     td_stage(p, d, u, v, claimed, st, qnext, tail, acc_m);
 }
 
-__device__ __forceinline__ WarpStage warp_stage() {
+__device__ __forceinline__ WarpStage warp_stage_in(int* buf) {
     WarpStage st;
-    st.buf = g_stage[threadIdx.x >> 5];
+    st.buf = buf;
     st.cnt = 0;
     st.pf = false;
     st.nodeg = false;
     st.hv = 0;
     return st;
 }
+// the CSR kernel's phases (kBlock threads) and the DCSC kernel's (kDBlock threads)
+__device__ __forceinline__ WarpStage warp_stage() { return warp_stage_in(g_stage[threadIdx.x >> 5]); }
+__device__ __forceinline__ WarpStage warp_stage_dcsc() { return warp_stage_in(g_stage_d[threadIdx.x >> 5]); }
 
 __device__ void td_phase(const SingleParams& p, int d, const int* qcur, long long nf, int* qnext, int snext,
                          bool nodeg, unsigned long long& acc_m, unsigned long long& acc_h) {
@@ -905,7 +909,7 @@ __device__ __forceinline__ int bu_locate(int k, int T, int incl, int excl, unsig
 __device__ void bu_phase_a(const SingleParams& p, int d, const unsigned* fcur, unsigned* fnext, int* longlist,
                            unsigned long long* longcnt, unsigned long long& acc_n, unsigned long long& acc_m,
                            unsigned long long& acc_sc, unsigned long long& acc_ex) {
-    __shared__ unsigned s_next[kWarps][32];
+    __shared__ unsigned s_next[kBlock / 32][32];
     const int lane = lane_id(), wib = threadIdx.x >> 5;
     const long long nchunk = (p.W + 31) / 32;
     const int4 z4 = make_int4(0, 0, 0, 0);
@@ -1861,7 +1865,7 @@ __device__ void td_dcsc_phase(const SingleParams& p, int d, const int* qcur, lon
     for (long long w = threadIdx.x; w < nbw; w += blockDim.x) s_own[w] = __ldcg(p.visited + wbase + w);
     __syncthreads();
     unsigned long long* tail = &p.ctrl->tail[snext];
-    WarpStage st = warp_stage();
+    WarpStage st = warp_stage_dcsc();
     const int wib = threadIdx.x >> 5, nwb = blockDim.x >> 5;
     for (long long base = (long long)wib * 32; base < nf; base += (long long)nwb * 32) {
         const long long i = base + lane;
