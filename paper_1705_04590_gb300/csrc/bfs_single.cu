@@ -54,8 +54,8 @@ constexpr int kMinChunk = 64;  // smallest chunk task: the task lists are sized 
 constexpr int kStage = 256;    // per-warp shared-memory staging of next-queue entries
 
 // Shared memory that phases of the CSR kernel borrow in turn: the top-down
-// staging slices, bottom-up phase A's searcher lists, and the two frontier
-// buffers of the cluster levels.
+// staging slices, and bottom-up phase A's searcher lists, whose two halves are
+// the frontier buffers of the cluster levels.
 __shared__ __align__(16) int g_stage[kBlock / 32][kStage];
 __shared__ __align__(16) int g_stage_d[kDBlock / 32][kStage];   // the DCSC kernel's (more warps per CTA)
 __shared__ __align__(16) unsigned short g_list[kBlock / 32][1024];
@@ -1287,8 +1287,7 @@ static_assert(sizeof(CluEntry) == 16, "a frontier entry is one 16-byte load");
 __device__ __forceinline__ unsigned long long clu_row(long long s, long long deg) {
     return (unsigned long long)s | ((unsigned long long)min(deg, (long long)0xFFFFFF) << kCluDegShift);
 }
-constexpr int kCluCap = (int)((sizeof(g_stage) < sizeof(g_list) ? sizeof(g_stage) : sizeof(g_list)) /
-                              sizeof(CluEntry));   // entries per CTA buffer
+constexpr int kCluCap = (int)(sizeof(g_list) / 2 / sizeof(CluEntry));   // entries per CTA buffer (half of g_list)
 constexpr unsigned long long kCluCntMask = 0x7FFFull;   // entry count field of a summary word
 static_assert(kCluCap <= 0x7FFF, "entry count field");
 
@@ -1454,8 +1453,8 @@ __device__ void cluster_levels(const SingleParams& p, const int* qcur, int d0, l
     const int C = p.clu_c, r = (int)clu_rank(), tid = threadIdx.x, nth = blockDim.x;
     const int lane = lane_id(), wib = tid >> 5;
     const bool lead = blockIdx.x == 0 && tid == 0;
-    CluEntry* const buf0 = reinterpret_cast<CluEntry*>(&g_stage[0][0]);
-    CluEntry* const buf1 = reinterpret_cast<CluEntry*>(&g_list[0][0]);
+    CluEntry* const buf0 = reinterpret_cast<CluEntry*>(&g_list[0][0]);
+    CluEntry* const buf1 = buf0 + kCluCap;
     // this CTA's share of the entry frontier, with the rows' offsets and degrees
     {
         const long long lo = nf0 * r / C, hi = nf0 * (r + 1) / C;
