@@ -25,7 +25,10 @@
 // gain nothing from lanes -- their levels are short and many, and every lane
 // pays every level -- so their slots use kDeepExecs executors with small grids
 // only; those cooperative launches run side by side, each bound by its own
-// level latency rather than by the device's throughput.
+// level latency rather than by the device's throughput.  A deep executor's grid
+// is one thread-block cluster (kDeepGrid CTAs): its small levels run as cluster
+// levels whatever the grid, and the CTAs it does not hold stay free for the
+// other slots' launches.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -49,6 +52,7 @@ enum TicketState { kQueued = 0, kRunning = 1, kDone = 2, kFailed = 3 };
 constexpr int kMinCtas = 8;   // smallest grid of a slot's launch
 constexpr int kDeepLevels = 128;   // probe levels above which a slot runs concurrent single searches
 constexpr int kDeepExecs = 8;      // concurrent single-source searches of such a slot
+constexpr int kDeepGrid = 16;      // CTAs of each (one cluster of 16)
 constexpr int kExecs = 2;          // executors of every other slot
 constexpr size_t kLaneBatch = 8;   // a queue this long (or busy lanes) sends queries to lanes
 
@@ -497,7 +501,7 @@ bfs_status bfs_server_add_graph(bfs_server* sv, bfs_graph* g, int32_t* slot) {
     }
     if (deep_levels > kDeepLevels) {
         s->deep = true;
-        bfs_status r = add_execs(sv, s, kDeepExecs, std::max(kMinCtas, 2 * g->sm_count / kDeepExecs), 1);
+        bfs_status r = add_execs(sv, s, kDeepExecs, kDeepGrid, 1);
         if (r != BFS_OK) {
             std::string msg = bfs_last_error();
             free_execs(sv, s);
