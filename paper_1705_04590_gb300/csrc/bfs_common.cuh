@@ -45,7 +45,8 @@ struct Ctrl {
     unsigned long long scanned[3];   // bottom-up searchers of the level producing frontier `slot`
     unsigned long long examined[3];  // serial early-exit examinations of that level
     unsigned long long ntask[3];     // top-down edge-chunk tasks of that level
-    unsigned long long nmiss[3];     // bottom-up searchers whose first probe missed (miss-list length)
+    unsigned long long nmiss[3];     // bottom-up first-probe misses left to phase B (miss-list length)
+    unsigned long long nmiss_in[3];  // ... resolved by their chunk's warp in phase A
     unsigned long long dsum_out[3];  // directed graphs: out-degree sum of frontier `slot`
     unsigned long long dsum_in[3];   // directed graphs: in-degree sum of frontier `slot`
     unsigned long long heavy[3];     // top-down: vertices of frontier `slot` above the cluster-level degree cap

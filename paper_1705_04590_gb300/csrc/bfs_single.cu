@@ -1040,15 +1040,90 @@ constexpr unsigned kMore = 0x80000000u;
 
 __device__ __forceinline__ unsigned frontier_word(const unsigned* f, int v) { return __ldcg(f + (v >> 5)); }
 
+constexpr int kMissPerLane = 2;   // misses whose row heads a lane reads together
+#ifndef BFS_INLINE_MISSES
+#define BFS_INLINE_MISSES 128
+#endif
+// A chunk with at most this many first-probe misses resolves them in its own
+// warp at the end of the chunk (two steps of kMissPerLane per lane at most: no miss-list
+// round trip, no global atomics, and the random head reads overlap other warps'
+// first probes); a chunk with more sends them to the miss list, which phase B
+// spreads over every warp.
+constexpr int kInlineMisses = BFS_INLINE_MISSES;
+
+// The first-probe misses of a warp's current chunk (staged in st.buf[0..cnt)):
+// each lane takes kMissPerLane of them per step and reads their 32-byte row
+// heads together (degree and the first seven ids), then probes ids 1..6 in row
+// order.  A hit goes into `cmiss`, the chunk's words of such hits in shared
+// memory (merged into the chunk's next-frontier words when they are written,
+// so no global atomics, and kept out of `pfirst`: these parents are stored); a
+// row that goes on is appended to the long list (phase C resumes it at 7).
+__device__ __forceinline__ void chunk_misses(const SingleParams& p, int d, const unsigned* fcur, WarpStage& st,
+                                             unsigned* cmiss, long long ch, int* longlist, unsigned long long* longcnt,
+                                             unsigned long long& acc_left, unsigned long long& acc_ex) {
+    const int lane = lane_id();
+    __syncwarp();
+    for (int i0 = 0; i0 < st.cnt; i0 += 32 * kMissPerLane) {
+        int u[kMissPerLane];
+        int4 a[kMissPerLane], b[kMissPerLane];
+#pragma unroll
+        for (int r = 0; r < kMissPerLane; r++) {
+            const int i = i0 + r * 32 + lane;
+            u[r] = i < st.cnt ? st.buf[i] : -1;
+            a[r] = b[r] = make_int4(0, 0, 0, 0);
+            if (u[r] >= 0) ld_stream8(p.heads + 8 * (long long)u[r], a[r], b[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < kMissPerLane; r++) {
+            bool to_long = false;
+            if (u[r] >= 0) {
+                const int deg = a[r].x;
+                const int ids[kHead] = {a[r].y, a[r].z, a[r].w, b[r].x, b[r].y, b[r].z, b[r].w};
+                unsigned hit = 0;
+#pragma unroll
+                for (int t = 1; t < kHead; t++)
+                    if (t < deg && in_frontier(fcur, ids[t])) hit |= 1u << t;
+                if (hit) {
+                    const int t = __ffs(hit) - 1;
+                    const int v = u[r];
+                    acc_ex += (unsigned long long)(t + 1);
+                    if (p.parent) p.parent[v] = pick(ids, t);
+                    set_level(p, v, d + 1);
+                    atomicOr(cmiss + ((v >> 5) - ch * 32), 1u << (v & 31));
+                } else if (deg > kHead) {
+                    to_long = true;       // examinations counted by phase C
+                } else {
+                    acc_ex += (unsigned long long)deg;
+                    acc_left += (unsigned long long)deg;
+                }
+            }
+            const unsigned lm = __ballot_sync(kFull, to_long);
+            if (lm) {
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(longcnt, (unsigned long long)__popc(lm));
+                base = __shfl_sync(kFull, base, 0);
+                if (to_long) longlist[base + __popc(lm & lanemask_lt())] = u[r];
+            }
+        }
+    }
+    __syncwarp();
+    st.cnt = 0;
+}
+
 __device__ void bu_compact(const SingleParams& p, int d, const unsigned* fcur, unsigned* fnext, int* misslist,
-                           unsigned long long* misscnt, unsigned long long& acc_n, unsigned long long& acc_left,
-                           unsigned long long& acc_sc, unsigned long long& acc_ex) {
+                           unsigned long long* misscnt, unsigned long long* misscnt_inline, int* longlist,
+                           unsigned long long* longcnt,
+                           unsigned long long& acc_n, unsigned long long& acc_left, unsigned long long& acc_sc,
+                           unsigned long long& acc_ex) {
     __shared__ unsigned s_cnext[kBlock / 32][32];
+    __shared__ unsigned s_cmiss[kBlock / 32][32];   // the chunk's hits among misses it resolved itself
+    s_cmiss[threadIdx.x >> 5][lane_id()] = 0u;
     const int lane = lane_id(), wib = threadIdx.x >> 5;
     unsigned short* list = g_list[wib];
     const long long nchunk = (p.W + 31) / 32;
     s_cnext[wib][lane] = 0u;
     WarpStage mst = warp_stage();
+    unsigned long long nmiss_w = 0;   // warp-uniform
     __syncwarp();
     const long long gw = gtid() >> 5, nw = gthreads() >> 5;
     for (long long ch = gw; ch < nchunk; ch += nw) {
@@ -1102,20 +1177,29 @@ __device__ void bu_compact(const SingleParams& p, int d, const unsigned* fcur, u
             f2 = f3;
             pw0 = pw1;
         }
+        if (mst.cnt > kInlineMisses) {
+            long_flush(mst, misslist, misscnt);
+        } else if (mst.cnt > 0) {
+            nmiss_w += (unsigned long long)mst.cnt;
+            chunk_misses(p, d, fcur, mst, s_cmiss[wib], ch, longlist, longcnt, acc_left, acc_ex);
+        }
         __syncwarp();
-        const unsigned nx = s_cnext[wib][lane];
+        const unsigned nf = s_cnext[wib][lane];   // first-probe hits: parent = the plane entry
+        const unsigned nx = nf | s_cmiss[wib][lane];
+        s_cmiss[wib][lane] = 0u;
         if (w < p.W) {
             fnext[w] = nx;
             if (nx) {
                 p.visited[w] = cw | nx;
-                if (p.pfirst) atomicOr(p.pfirst + w, nx);
+                if (p.pfirst && nf) atomicOr(p.pfirst + w, nf);
             }
         }
         acc_n += (unsigned long long)__popc(nx);
         s_cnext[wib][lane] = 0u;
         __syncwarp();
     }
-    long_flush(mst, misslist, misscnt);
+    // misses resolved here, for the level's record
+    if (lane == 0 && nmiss_w) atomicAdd(misscnt_inline, nmiss_w);
 }
 
 // Bottom-up over the hub-first rows, phase B: the miss list.  Each lane takes
@@ -1125,8 +1209,6 @@ __device__ void bu_compact(const SingleParams& p, int d, const unsigned* fcur, u
 // frontier and completed words are shared with other warps here, hence
 // atomicOr.  A searcher with more than seven neighbours and no hit among them
 // goes on the long list (phase C resumes its row at position 7).
-constexpr int kMissPerLane = 2;
-
 __device__ void bu_misses(const SingleParams& p, int d, const unsigned* fcur, unsigned* fnext, const int* misslist,
                           long long nmiss, int* longlist, unsigned long long* longcnt, unsigned long long& acc_n,
                           unsigned long long& acc_left, unsigned long long& acc_ex) {
@@ -1541,6 +1623,7 @@ __device__ void cluster_levels(const SingleParams& p, const int* qcur, int d0, l
                     c->examined[k] = 0;
                     c->ntask[k] = 0;
                     c->nmiss[k] = 0;
+                    c->nmiss_in[k] = 0;
                     c->dsum_out[k] = 0;
                     c->dsum_in[k] = 0;
                     c->heavy[k] = 0;
@@ -1709,6 +1792,7 @@ __global__ void __launch_bounds__(kBlock, BFS_MIN_BLOCKS) bfs_single_kernel(Sing
             c->examined[sfree] = 0;
             c->ntask[sfree] = 0;
             c->nmiss[sfree] = 0;
+            c->nmiss_in[sfree] = 0;
             c->dsum_out[sfree] = 0;
             c->dsum_in[sfree] = 0;
             c->heavy[sfree] = 0;
@@ -1756,7 +1840,8 @@ __global__ void __launch_bounds__(kBlock, BFS_MIN_BLOCKS) bfs_single_kernel(Sing
             int* longlist = qnext;
             int* misslist = qcur;
             if (p.first)
-                bu_compact(p, d, fcur, fnext, misslist, &c->nmiss[snext], an, am, asc, aex);
+                bu_compact(p, d, fcur, fnext, misslist, &c->nmiss[snext], &c->nmiss_in[snext], longlist,
+                           &c->ntask[snext], an, am, asc, aex);
             else
                 bu_phase_a(p, d, fcur, fnext, longlist, &c->ntask[snext], an, am, asc, aex);
             block_add4(an, am, asc, aex, &c->accn[snext], &c->accm[snext], &c->scanned[snext],
@@ -1765,7 +1850,7 @@ __global__ void __launch_bounds__(kBlock, BFS_MIN_BLOCKS) bfs_single_kernel(Sing
             if (lead) t_mid = globaltimer_ns();
             if (p.first) {
                 const long long nmiss = (long long)ld_relaxed64(&c->nmiss[snext]);
-                misses = nmiss;
+                misses = nmiss + (long long)ld_relaxed64(&c->nmiss_in[snext]);
                 if (nmiss > 0) {
                     unsigned long long bn = 0, bm = 0, bex = 0;
                     bu_misses(p, d, fcur, fnext, misslist, nmiss, longlist, &c->ntask[snext], bn, bm, bex);
