@@ -25,14 +25,15 @@ cpu_baseline: the serial CPU oracle (Algorithm 1) on 4 roots of the headline gra
           multithreaded direction-optimizing CPU BFS (the paper's in-node
           algorithm, OpenMP) on the same roots with every host thread.
 tuned:   the autotuner's options (alpha, beta, hub cut-off, top-down chunk,
-          CTAs per SM) on 4 sample roots, timed over the same steps.
+          CTAs per SM, cluster size) on 4 sample roots, timed over the same steps.
 batched: 64-lane multi-source search (R-MAT 22, 64 roots, one launch) and an
           uneven batch of 256 graphs (one multi-root launch over their union),
           each against looping the plain single-source search.
 served:  continuous-batching server over 8 resident graphs; the sustained
           capacity is the highest Poisson rate it keeps up with (>= 97 % served,
-          p99 under 100 ms); Poisson arrivals at 0.25/0.5/0.9 of it, p50/p99
-          latency and GTEPS, against a one-at-a-time plain FIFO on the same trace.
+          p99 under half the 100 ms target over 1000 queries); Poisson arrivals at
+          0.25/0.5/0.9 of it, p50/p99 latency (also per graph) and GTEPS, against a
+          one-at-a-time plain FIFO on the same trace.
 configs: R-MAT 24 over CSR (hub-first and id-ordered rows) and DCSC tiles, each
           direction-optimizing / top-down only / bottom-up only, and as a directed
           graph (out-rows top-down, their transpose bottom-up); Erdos-Renyi
@@ -609,16 +610,20 @@ def served_section(g26, roots26, n_queries: int = 2000, seed: int = 5151) -> dic
     sat = run_server(trace(1024), np.zeros(1024))
     # the sustained capacity: the highest Poisson rate (searched from below the burst's) at
     # which the server keeps up, i.e. serves >= 97 % of the offered rate with a p99 under
-    # the target; the offered loads are fractions of it
+    # half the target over 1000 queries (the margin keeps the longer runs at the offered
+    # loads under the target); the offered loads are fractions of it
     p99_target_ms = 100.0
     probes = []
 
-    def keeps_up(rate, k=600):
+    def keeps_up(rate, k=1000):
         tr = trace(k)
         arr = np.cumsum(rng.exponential(1.0 / rate, k))
         arr -= arr[0]
         r = run_server(tr, arr)
-        ok = r["qps"] >= 0.97 * rate and r["p99_ms"] <= p99_target_ms
+        # against the trace's own arrival rate (a Poisson trace of k queries spans
+        # k / rate only on average)
+        realized = (k - 1) / max(float(arr[-1]), 1e-9)
+        ok = r["qps"] >= 0.97 * realized and r["p99_ms"] <= 0.5 * p99_target_ms
         probes.append({"offered_qps": rate, "served_qps": r["qps"], "p99_ms": r["p99_ms"], "keeps_up": ok})
         return ok
 
