@@ -53,7 +53,7 @@ constexpr int kMinCtas = 8;   // smallest grid of a slot's launch
 constexpr int kDeepLevels = 128;   // probe levels above which a slot runs concurrent single searches
 constexpr int kDeepExecs = 8;      // concurrent single-source searches of such a slot
 constexpr int kDeepGrid = 16;      // CTAs of each (one cluster of 16)
-constexpr int kExecs = 2;          // executors of every other slot
+constexpr int kExecs = 4;          // executors of every other slot
 constexpr size_t kLaneBatch = 8;   // a queue this long (or busy lanes) sends queries to lanes
 
 struct Ticket {
