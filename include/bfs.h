@@ -408,13 +408,13 @@ bfs_status bfs_debug_set_barrier_extra(bfs_graph* g, int32_t extra);
  * running multi-source search; a query is admitted into a free slot at the
  * next level boundary (its lane starts at the current iteration, and its
  * levels count from there), so queries that arrive while others run share
- * the device work.  Each graph also keeps up to two plain single-source
+ * the device work.  Each graph also keeps up to four plain single-source
  * search states that take queued queries first (plain searches); lanes open
  * for the overflow once 8 or more queries wait, and keep admitting while they
  * run.  A graph whose probe search at
  * add time needs more than 128 levels (large diameter, e.g. a torus) is served
- * by up to 8 plain searches running side by side with small grids instead of
- * lanes.  Levels are the same on every path.  Admission is bounded by
+ * by up to 8 plain searches running side by side, each on one 16-CTA
+ * thread-block cluster (cluster levels), instead of lanes.  Levels are the same on every path.  Admission is bounded by
  * hbm_budget_bytes for per-query state and search states.  A host thread
  * drives the device; outputs land in caller memory.
  */
