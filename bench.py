@@ -329,7 +329,9 @@ def batched_section(seed: int = 4242, hub: bool = True) -> dict:
     """Batched multi-source BFS against looping the plain search.
 
     (i)  R-MAT scale 22, 64 roots: one bfs_run_multi (64 lanes, one persistent
-         launch) vs 64 bfs_run, levels only, CUDA events, best of 3.
+         launch) vs 64 bfs_run, levels only, CUDA events, best of 3; again with
+         both arms tuned (the autotuner for the plain arm, a grid over the
+         direction thresholds for the multi-source launch).
     (ii) 256 R-MAT graphs with scales drawn uniformly from 10..20 (seeded), one
          root each: one bfs_run_multiroot over their disjoint union (one
          launch) vs a loop of 256 plain searches on the separate graphs.
@@ -372,6 +374,24 @@ def batched_section(seed: int = 4242, hub: bool = True) -> dict:
     out["rmat22_64roots"] = {"multi_ms": t_multi, "plain_ms": t_plain, "multi_gteps": 64 * m / t_multi / 1e6,
                              "plain_gteps": 64 * m / t_plain / 1e6, "speedup": t_plain / t_multi,
                              "launches_multi": 1, "launches_plain": 64}
+    # both arms tuned: the plain arm with the autotuner's choice on 4 of the roots (every
+    # plain-search knob), the multi-source launch with the direction thresholds that time
+    # best for it over the same grid (its levels count 64 lanes, so its best thresholds differ)
+    from paper_1705_04590_gb300 import autotune
+    ot, _ = autotune.autotune(g, roots[:4], base=o)
+    t_plain_t = best_ms(lambda: [g.run(r, level=lv1, opts=ot) for r in roots])
+    grid_ab = [(a_, b_) for a_ in (6, 14, 24, 32, 96) for b_ in (12, 24, 64, 128)]
+    tm = {ab: best_ms(lambda ab=ab: g.run_multi(roots, lvk, opts=bfs.options(bu_rows=o.bu_rows, alpha=ab[0],
+                                                                              beta=ab[1])), reps=1)
+          for ab in grid_ab}
+    am, bm = min(tm, key=tm.get)
+    t_multi_t = best_ms(lambda: g.run_multi(roots, lvk, opts=bfs.options(bu_rows=o.bu_rows, alpha=am, beta=bm)))
+    g.sync()
+    out["rmat22_64roots_tuned"] = {"plain": {"alpha": ot.alpha, "beta": ot.beta, "td_big_degree": ot.td_big_degree,
+                                             "td_chunk": ot.td_chunk, "ctas_per_sm": ot.ctas_per_sm,
+                                             "cluster_size": ot.cluster_size},
+                                   "multi": {"alpha": am, "beta": bm}, "multi_ms": t_multi_t, "plain_ms": t_plain_t,
+                                   "speedup": t_plain_t / t_multi_t}
     g.close()
     del lvk
     rng = np.random.default_rng(seed)
