@@ -63,3 +63,23 @@ def test_reference_arm_off_rank0_does_nothing(monkeypatch, capsys):
                           "scale": 26, "cpu_scale": 22})()
     assert bench.reference_arm(args) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_served_capacity_criterion_uses_the_traces_own_rate():
+    """A Poisson trace of k queries at nominal rate r spans (k-1)/r only on average: a server
+    that kept pace with a trace that ran long must not be judged slow against r."""
+    import numpy as np
+    rng = np.random.default_rng(3)
+    rate, k = 400.0, 1000
+    arr = np.cumsum(rng.exponential(1.0 / rate, k))
+    arr -= arr[0]
+    realized = (k - 1) / arr[-1]
+    # served exactly at the trace's pace, p99 well under half the target: keeps pace
+    assert bench.keeps_pace(arr, realized, 30.0, 100.0)
+    # a trace that happened to span 5 % longer than average is still kept pace with
+    long_arr = arr * 1.05
+    assert bench.keeps_pace(long_arr, (k - 1) / long_arr[-1], 30.0, 100.0)
+    assert not (k - 1) / long_arr[-1] >= 0.97 * rate   # the nominal-rate test would have failed it
+    # falling behind the trace, or a tail over half the target, does not keep pace
+    assert not bench.keeps_pace(arr, 0.9 * realized, 30.0, 100.0)
+    assert not bench.keeps_pace(arr, realized, 60.0, 100.0)
